@@ -1,0 +1,211 @@
+/*
+ * sss.h -- C ABI of the GB300 string sorter (libsss.so).
+ *
+ * The library sorts a string array S = [s_0, ..., s_{n-1}] as defined in the
+ * paper's Section 2 ("String Properties and Input Format"): strings are views
+ * (offset, length) into one character array, the output is the sorted order
+ * ("where to find the i-th smallest string", Section 4) plus the LCP array, and
+ * optionally the distinguishing-prefix lengths.  The p "PEs" of the paper's
+ * distributed algorithm are p partitions of the input held in one GPU's memory:
+ * partition i owns input indices [floor(i*n/p), floor((i+1)*n/p)).
+ *
+ * Conventions for every call below:
+ *  - Pointers named chars/offsets/lengths/... and every out_* pointer are DEVICE
+ *    pointers owned by the caller; the library never frees them.
+ *      chars    : uint8_t[n_chars]   character data; no string contains 0x00
+ *                 (the sentinel of Section 2 is implicit at the string end)
+ *      offsets  : uint64_t[n]        string i starts at chars[offsets[i]]
+ *      lengths  : uint32_t[n]        string i has lengths[i] chars (no terminator)
+ *    Strings may overlap (e.g. suffixes of one text).
+ *  - Calls are asynchronous on the context's CUDA stream.  A call returns after
+ *    enqueueing its work; some calls synchronise the stream internally to read
+ *    small counters (documented per call).  Outputs are valid once the stream has
+ *    been synchronised.
+ *  - The return value reports argument, allocation and launch errors.  Errors
+ *    detected on the device (SSS_CHECKED validation, bounded waits that ran out)
+ *    are sticky in the context and returned by sss_sync().
+ *  - Work memory is owned by the context: it is allocated with cudaMalloc on
+ *    first use and grown when a larger problem arrives, or supplied by the caller
+ *    with sss_set_workspace().
+ *  - A context is not thread-safe; use one context per host thread.
+ *  - Limits: n < 2^32 - 1, p <= 4096, string lengths < 2^31.
+ */
+#ifndef SSS_H
+#define SSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sss_status {
+    SSS_OK = 0,
+    SSS_ERR_INVALID_ARG = 1,   /* bad pointer/size/parameter; nothing was enqueued */
+    SSS_ERR_OOM = 2,           /* device or pinned host allocation failed */
+    SSS_ERR_CUDA = 3,          /* a CUDA runtime call failed (see sss_last_error) */
+    SSS_ERR_TIMEOUT = 4,       /* a bounded device-side wait ran out */
+    SSS_ERR_DEVICE_CHECK = 5,  /* SSS_CHECKED validation found bad input */
+    SSS_ERR_UNIMPLEMENTED = 6, /* the requested mode is not built */
+    SSS_ERR_WORKSPACE = 7      /* caller-supplied workspace is too small */
+} sss_status;
+
+/* sss_params.flags */
+#define SSS_FLAG_MS 0x1u       /* p > 1: merge full strings, skip prefix doubling */
+#define SSS_FLAG_CHECKED 0x2u  /* validate offsets/lengths against n_chars and
+                                  scan strings for 0x00 bytes; errors are sticky */
+#define SSS_FLAG_NO_LOCAL_LCP_SKIP 0x4u /* doubling: hash every active string
+                                  instead of one per locally-equal prefix group */
+
+typedef struct sss_params {
+    uint32_t kmin;      /* first doubling round: prefix length 2^kmin (default 0) */
+    uint32_t kmax;      /* last doubling round; SSS_KMAX_AUTO = ceil(log2(max len)) */
+    uint32_t v;         /* regular-sampling factor (default 2, Section 5) */
+    uint32_t flags;     /* SSS_FLAG_* */
+    uint64_t hash_seed; /* seed of the prefix hash (default 0) */
+    uint32_t cta_cap;   /* tuning: largest segment sorted inside one CTA (0 = default) */
+    uint32_t reserved[5];
+} sss_params;
+
+#define SSS_KMAX_AUTO 0xFFFFFFFFu
+
+typedef struct sss_ctx sss_ctx;
+
+/* Fill *p with the defaults (kmin 0, kmax auto, v 2, flags 0, seed 0). */
+void sss_params_default(sss_params* p);
+
+/* Create a context on CUDA device `device` that enqueues on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  *out is set on success. */
+sss_status sss_create(sss_ctx** out, int device, void* cuda_stream);
+
+/* Destroy a context (synchronises its stream, frees its memory).  NULL is a no-op. */
+sss_status sss_destroy(sss_ctx* ctx);
+
+/* Change the stream subsequent calls enqueue on. */
+sss_status sss_set_stream(sss_ctx* ctx, void* cuda_stream);
+
+/* Hand the context a caller-owned device buffer to use as work memory instead of
+ * its own allocations (NULL/0 returns to library-owned memory).  The buffer must
+ * stay valid while calls that use it run; sss_workspace_bytes() gives the size. */
+sss_status sss_set_workspace(sss_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Upper bound on the work memory a call with these sizes needs (bytes). */
+size_t sss_workspace_bytes(uint32_t n, uint32_t p, const sss_params* params);
+
+/* Synchronise the context's stream and return the sticky device status
+ * (SSS_OK, SSS_ERR_DEVICE_CHECK, SSS_ERR_TIMEOUT or SSS_ERR_CUDA); clears it. */
+sss_status sss_sync(sss_ctx* ctx);
+
+const char* sss_status_string(sss_status s);
+
+/* Human-readable text of the last error raised by this context (never NULL). */
+const char* sss_last_error(sss_ctx* ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Stage A -- local string sort with LCP output (Section 3, "Initialization":
+ * each PE sorts its local array; the LCP array is a by-product of sorting).
+ * MSD radix sort over 8-byte big-endian character words with an equal-prefix
+ * skip, finished inside one CTA for segments of up to cta_cap strings.
+ *
+ * out_run_perm : uint32_t[n]; positions [lo_i, hi_i) hold partition i's input
+ *                indices in sorted order (equal strings by index).
+ * out_run_lcp  : uint32_t[n]; out_run_lcp[q] = lcp(run[q-1], run[q]) within a
+ *                partition, 0 at every partition start.
+ * Synchronises the stream once per radix round of segments larger than cta_cap. */
+sss_status sss_local_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars,
+                          const uint64_t* offsets, const uint32_t* lengths, uint32_t n,
+                          uint32_t p, const sss_params* params,
+                          uint32_t* out_run_perm, uint32_t* out_run_lcp);
+
+/* Stage A6 -- exact distinguishing prefixes (Section 2: the characters needed to
+ * rank a string): out_dist[perm[r]] = min(len, 1 + max(lcp[r], lcp[r+1])) for a
+ * GLOBAL sorted order perm/lcp of all n strings (missing neighbours count 0). */
+sss_status sss_dist(sss_ctx* ctx, const uint32_t* lengths, uint32_t n,
+                    const uint32_t* perm, const uint32_t* lcp, uint32_t* out_dist);
+
+/* Stage B -- prefix doubling (Section 4): for k = kmin..kmax the prefixes of
+ * length L = 2^k of the still-active strings are hashed to 64-bit keys; keys
+ * that occur once (or strings with length <= L) retire with
+ * approx = min(L, len); duplicate detection sorts the keys (appendix,
+ * "Duplicate Detection with Atomic Hypercube Quicksort").  Survivors of round
+ * kmax get approx = len.  approx >= dist always.
+ * run_perm/run_lcp (nullable together): the local sorted runs of p partitions
+ * (as from sss_local_sort); when given, strings whose L-prefix equals a local
+ * neighbour's are known duplicates and one key per such group is hashed -- the
+ * result is identical.  out_approx: uint32_t[n] by input index.
+ * Synchronises the stream once per round. */
+sss_status sss_dist_prefix(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars,
+                           const uint64_t* offsets, const uint32_t* lengths, uint32_t n,
+                           const uint32_t* run_perm, const uint32_t* run_lcp, uint32_t p,
+                           const sss_params* params, uint32_t* out_approx);
+
+/* Stage C -- string-based regular sampling and splitters (Section 3.1.1) and
+ * bucket bounds (Section 3, step 1).  Partition i draws v+1 samples at local
+ * ranks ceil(t*n_i/(v+1)) - 1 (t = 1..v+1); the samples are sorted (truncated
+ * strings, then index) and f_j = V[floor(j*|V|/p) - 1] for 0 < j < p
+ * (UINT32_MAX = minus infinity when the index is negative).
+ * trunc        : uint32_t[n] or NULL; string i is compared as its first
+ *                trunc[i] chars (trunc[i] <= lengths[i]).
+ * out_splitters: uint32_t[p-1] input indices of f_1..f_{p-1} (may be NULL if p==1)
+ * out_bounds   : uint32_t[p*(p+1)]; out_bounds[i*(p+1)+j] = number of strings of
+ *                run i that are <= f_j (0 for j = 0, n_i for j = p). */
+sss_status sss_partition(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars,
+                         const uint64_t* offsets, const uint32_t* lengths,
+                         const uint32_t* trunc, const uint32_t* run_perm, uint32_t n, uint32_t p,
+                         const sss_params* params, uint32_t* out_splitters, uint32_t* out_bounds);
+
+/* Stage D -- LCP-compressed exchange and LCP-aware merge (Section 3, steps 2-3;
+ * LCP compression and LCP merging of Section 2 "Algorithmic Building Blocks").
+ * Merges the p sorted runs run_perm/run_lcp (partition layout) into the global
+ * order: stage C picks splitters, every run piece is copied LCP-compressed into
+ * its bucket (index, LCP with predecessor, chars [lcp, trunc)), and each bucket
+ * is merged with LCPs.  Equal (truncated) strings keep run order.
+ * trunc: as for sss_partition (NULL = full strings).  Truncation lengths must not
+ * change the order (true for approx from sss_dist_prefix).
+ * out_perm/out_lcp: uint32_t[n] global sorted order and full LCP array. */
+sss_status sss_lcp_merge(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars,
+                         const uint64_t* offsets, const uint32_t* lengths,
+                         const uint32_t* trunc, const uint32_t* run_perm, const uint32_t* run_lcp,
+                         uint32_t n, uint32_t p, const sss_params* params,
+                         uint32_t* out_perm, uint32_t* out_lcp);
+
+/* The whole path.  p == 1: local sort (stage A) of all strings.  p > 1: the
+ * prefix-doubling merge sort (PDMS, Section 4) collapsed onto one GPU: stage A on
+ * every partition, stage B, then stages C and D on the approx-truncated strings
+ * (SSS_FLAG_MS: no stage B, full strings are merged).
+ * out_perm, out_lcp  : uint32_t[n] global order and LCP array (required)
+ * out_dist, out_approx: uint32_t[n] by input index, or NULL to skip (out_approx
+ *                       is approx for p > 1 without SSS_FLAG_MS, else lengths). */
+sss_status sss_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars,
+                    const uint64_t* offsets, const uint32_t* lengths, uint32_t n, uint32_t p,
+                    const sss_params* params, uint32_t* out_perm, uint32_t* out_lcp,
+                    uint32_t* out_dist, uint32_t* out_approx);
+
+/* ------------------------------------------------------------------------ */
+/* Instrumentation: per-kernel launch counts and (when timing is enabled) device
+ * time measured with CUDA events on the context's stream around each launch. */
+#define SSS_MAX_KERNELS 64
+
+typedef struct sss_kernel_stat {
+    const char* name;   /* static string */
+    uint64_t launches;  /* launches since the last reset */
+    double total_ms;    /* summed device time (timing enabled only) */
+    uint64_t timed;     /* launches that were timed */
+} sss_kernel_stat;
+
+/* Enable (1) / disable (0) event timing of launches whose kernel name contains
+ * `name_filter` (NULL or "" = all kernels). */
+sss_status sss_set_timing(sss_ctx* ctx, int enable, const char* name_filter);
+
+/* Synchronise, then copy up to `cap` entries (one per kernel that launched since
+ * the last reset) into out; *count receives the number written. */
+sss_status sss_kernel_stats(sss_ctx* ctx, sss_kernel_stat* out, uint32_t cap, uint32_t* count);
+
+/* Zero all launch counts and times. */
+sss_status sss_reset_stats(sss_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSS_H */

@@ -1,0 +1,317 @@
+// C ABI entry points: context, work memory, instrumentation and the stage calls.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "sss_internal.cuh"
+
+sss_status sss_fail(sss_ctx* c, sss_status s, const std::string& msg) {
+    if (c) c->last_error = msg;
+    return s;
+}
+
+sss_status sss_workspace(sss_ctx* ctx, size_t bytes, char** out) {
+    if (ctx->ws_user) {
+        if (bytes > ctx->ws_user_bytes)
+            return sss_fail(ctx, SSS_ERR_WORKSPACE,
+                            "caller workspace too small: need " + std::to_string(bytes) + " bytes");
+        *out = static_cast<char*>(ctx->ws_user);
+        return SSS_OK;
+    }
+    if (bytes > ctx->ws_own_bytes) {
+        if (ctx->ws_own) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->ws_own);
+            ctx->ws_own = nullptr;
+            ctx->ws_own_bytes = 0;
+        }
+        size_t want = bytes + bytes / 8;
+        if (cudaMalloc(&ctx->ws_own, want) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->ws_own = nullptr;
+            return sss_fail(ctx, SSS_ERR_OOM, "cudaMalloc of " + std::to_string(want) + " bytes failed");
+        }
+        ctx->ws_own_bytes = want;
+    }
+    *out = static_cast<char*>(ctx->ws_own);
+    return SSS_OK;
+}
+
+sss_status sss_pinned(sss_ctx* ctx, size_t bytes, void** out) {
+    if (bytes > ctx->h_pin_bytes) {
+        if (ctx->h_pin) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFreeHost(ctx->h_pin);
+            ctx->h_pin = nullptr;
+            ctx->h_pin_bytes = 0;
+        }
+        if (cudaMallocHost(&ctx->h_pin, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->h_pin = nullptr;
+            return sss_fail(ctx, SSS_ERR_OOM, "cudaMallocHost failed");
+        }
+        ctx->h_pin_bytes = bytes;
+    }
+    *out = ctx->h_pin;
+    return SSS_OK;
+}
+
+int sss_stat_index(sss_ctx* ctx, const char* name) {
+    for (int i = 0; i < ctx->nstats; ++i)
+        if (ctx->stats[i].name == name || std::strcmp(ctx->stats[i].name, name) == 0) return i;
+    if (ctx->nstats >= SSS_MAX_KERNELS) return -1;
+    ctx->stats[ctx->nstats] = KStat{name, 0, 0.0, 0};
+    return ctx->nstats++;
+}
+
+bool sss_timing_on(sss_ctx* ctx, int stat) {
+    if (!ctx->timing || stat < 0) return false;
+    if (ctx->timing_filter.empty()) return true;
+    return std::strstr(ctx->stats[stat].name, ctx->timing_filter.c_str()) != nullptr;
+}
+
+cudaEvent_t sss_event(sss_ctx* ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+static void collect_timings(sss_ctx* ctx) {
+    for (auto& p : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            ctx->stats[p.stat].ms += ms;
+            ctx->stats[p.stat].timed++;
+        }
+        ctx->event_pool.push_back(p.a);
+        ctx->event_pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+    cudaGetLastError();
+}
+
+extern "C" {
+
+void sss_params_default(sss_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->kmin = 0;
+    p->kmax = SSS_KMAX_AUTO;
+    p->v = 2;
+}
+
+const char* sss_status_string(sss_status s) {
+    switch (s) {
+        case SSS_OK: return "ok";
+        case SSS_ERR_INVALID_ARG: return "invalid argument";
+        case SSS_ERR_OOM: return "out of memory";
+        case SSS_ERR_CUDA: return "CUDA error";
+        case SSS_ERR_TIMEOUT: return "device wait timed out";
+        case SSS_ERR_DEVICE_CHECK: return "input validation failed on the device";
+        case SSS_ERR_UNIMPLEMENTED: return "not implemented";
+        case SSS_ERR_WORKSPACE: return "workspace too small";
+    }
+    return "unknown status";
+}
+
+const char* sss_last_error(sss_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+sss_status sss_create(sss_ctx** out, int device, void* stream) {
+    if (!out) return SSS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return SSS_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return SSS_ERR_CUDA;
+    sss_ctx* ctx = new (std::nothrow) sss_ctx();
+    if (!ctx) return SSS_ERR_OOM;
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&ctx->d_err, sizeof(unsigned) * 4) != cudaSuccess) {
+        delete ctx;
+        return SSS_ERR_OOM;
+    }
+    cudaMemset(ctx->d_err, 0, sizeof(unsigned) * 4);
+    cudaDeviceSynchronize();
+    *out = ctx;
+    return SSS_OK;
+}
+
+sss_status sss_destroy(sss_ctx* ctx) {
+    if (!ctx) return SSS_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    collect_timings(ctx);
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->ws_own) cudaFree(ctx->ws_own);
+    if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    delete ctx;
+    return SSS_OK;
+}
+
+sss_status sss_set_stream(sss_ctx* ctx, void* stream) {
+    if (!ctx) return SSS_ERR_INVALID_ARG;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return SSS_OK;
+}
+
+sss_status sss_set_workspace(sss_ctx* ctx, void* dev_ptr, size_t bytes) {
+    if (!ctx) return SSS_ERR_INVALID_ARG;
+    if (dev_ptr == nullptr || bytes == 0) {
+        ctx->ws_user = nullptr;
+        ctx->ws_user_bytes = 0;
+    } else {
+        ctx->ws_user = dev_ptr;
+        ctx->ws_user_bytes = bytes;
+    }
+    return SSS_OK;
+}
+
+sss_status sss_sync(sss_ctx* ctx) {
+    if (!ctx) return SSS_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    SSS_CUDA(cudaStreamSynchronize(ctx->stream));
+    unsigned h = 0;
+    SSS_CUDA(cudaMemcpy(&h, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (h) SSS_CUDA(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+    if (h & ERRBIT_CHECK) return sss_fail(ctx, SSS_ERR_DEVICE_CHECK, "input validation failed (offset/length/0x00)");
+    if (h & ERRBIT_TIMEOUT) return sss_fail(ctx, SSS_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (h & ERRBIT_OVERFLOW) return sss_fail(ctx, SSS_ERR_CUDA, "internal capacity exceeded on the device");
+    return SSS_OK;
+}
+
+sss_status sss_set_timing(sss_ctx* ctx, int enable, const char* filter) {
+    if (!ctx) return SSS_ERR_INVALID_ARG;
+    ctx->timing = enable != 0;
+    ctx->timing_filter = filter ? filter : "";
+    return SSS_OK;
+}
+
+sss_status sss_kernel_stats(sss_ctx* ctx, sss_kernel_stat* out, uint32_t cap, uint32_t* count) {
+    if (!ctx || (!out && cap) || !count) return SSS_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    SSS_CUDA(cudaStreamSynchronize(ctx->stream));
+    collect_timings(ctx);
+    uint32_t k = 0;
+    for (int i = 0; i < ctx->nstats && k < cap; ++i) {
+        if (ctx->stats[i].launches == 0) continue;
+        out[k].name = ctx->stats[i].name;
+        out[k].launches = ctx->stats[i].launches;
+        out[k].total_ms = ctx->stats[i].ms;
+        out[k].timed = ctx->stats[i].timed;
+        ++k;
+    }
+    *count = k;
+    return SSS_OK;
+}
+
+sss_status sss_reset_stats(sss_ctx* ctx) {
+    if (!ctx) return SSS_ERR_INVALID_ARG;
+    cudaStreamSynchronize(ctx->stream);
+    collect_timings(ctx);
+    for (int i = 0; i < ctx->nstats; ++i) {
+        ctx->stats[i].launches = 0;
+        ctx->stats[i].ms = 0.0;
+        ctx->stats[i].timed = 0;
+    }
+    return SSS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// argument checks shared by the entry points
+static sss_status check_common(sss_ctx* ctx, const uint8_t* chars, const uint64_t* offs, const uint32_t* lens,
+                               uint32_t n, uint32_t p) {
+    if (!ctx) return SSS_ERR_INVALID_ARG;
+    if (n == 0xFFFFFFFFu) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "n must be < 2^32 - 1");
+    if (p == 0 || p > 4096) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "p must be in 1..4096");
+    if (n > 0 && (!offs || !lens)) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "offsets/lengths must be non-NULL");
+    if (n > 0 && !chars) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "chars must be non-NULL");
+    return SSS_OK;
+}
+
+static sss_params resolve_params(const sss_params* p) {
+    sss_params r;
+    sss_params_default(&r);
+    if (p) r = *p;
+    if (r.v == 0) r.v = 2;
+    return r;
+}
+
+extern "C" {
+
+size_t sss_workspace_bytes(uint32_t n, uint32_t p, const sss_params* params) {
+    sss_params prm = resolve_params(params);
+    if (p == 0) p = 1;
+    return need_local_sort(n, p, prm);
+}
+
+sss_status sss_local_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,
+                          const uint32_t* lengths, uint32_t n, uint32_t p, const sss_params* params,
+                          uint32_t* out_run_perm, uint32_t* out_run_lcp) {
+    SSS_TRY(check_common(ctx, chars, offsets, lengths, n, p));
+    if (n > 0 && (!out_run_perm || !out_run_lcp)) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "outputs must be non-NULL");
+    if (n == 0) return SSS_OK;
+    cudaSetDevice(ctx->device);
+    sss_params prm = resolve_params(params);
+    StrIn in{chars, n_chars, offsets, lengths, n};
+    if (prm.flags & SSS_FLAG_CHECKED) {
+        SSS_TRY(impl_check_input(ctx, in));
+        SSS_TRY(sss_sync(ctx));
+    }
+    char* ws;
+    SSS_TRY(sss_workspace(ctx, need_local_sort(n, p, prm), &ws));
+    Arena ar{ws, 0, 0};
+    return impl_local_sort(ctx, ar, in, p, prm, out_run_perm, out_run_lcp);
+}
+
+sss_status sss_dist(sss_ctx* ctx, const uint32_t* lengths, uint32_t n, const uint32_t* perm, const uint32_t* lcp,
+                    uint32_t* out_dist) {
+    if (!ctx) return SSS_ERR_INVALID_ARG;
+    if (n == 0) return SSS_OK;
+    if (!lengths || !perm || !lcp || !out_dist) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "NULL pointer");
+    cudaSetDevice(ctx->device);
+    return impl_dist(ctx, lengths, n, perm, lcp, out_dist);
+}
+
+sss_status sss_dist_prefix(sss_ctx* ctx, const uint8_t*, uint64_t, const uint64_t*, const uint32_t*, uint32_t,
+                           const uint32_t*, const uint32_t*, uint32_t, const sss_params*, uint32_t*) {
+    return sss_fail(ctx, SSS_ERR_UNIMPLEMENTED, "sss_dist_prefix not built yet");
+}
+
+sss_status sss_partition(sss_ctx* ctx, const uint8_t*, uint64_t, const uint64_t*, const uint32_t*, const uint32_t*,
+                         const uint32_t*, uint32_t, uint32_t, const sss_params*, uint32_t*, uint32_t*) {
+    return sss_fail(ctx, SSS_ERR_UNIMPLEMENTED, "sss_partition not built yet");
+}
+
+sss_status sss_lcp_merge(sss_ctx* ctx, const uint8_t*, uint64_t, const uint64_t*, const uint32_t*, const uint32_t*,
+                         const uint32_t*, const uint32_t*, uint32_t, uint32_t, const sss_params*, uint32_t*,
+                         uint32_t*) {
+    return sss_fail(ctx, SSS_ERR_UNIMPLEMENTED, "sss_lcp_merge not built yet");
+}
+
+sss_status sss_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,
+                    const uint32_t* lengths, uint32_t n, uint32_t p, const sss_params* params, uint32_t* out_perm,
+                    uint32_t* out_lcp, uint32_t* out_dist, uint32_t* out_approx) {
+    SSS_TRY(check_common(ctx, chars, offsets, lengths, n, p));
+    if (n > 0 && (!out_perm || !out_lcp)) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "outputs must be non-NULL");
+    if (n == 0) return SSS_OK;
+    if (p > 1) return sss_fail(ctx, SSS_ERR_UNIMPLEMENTED, "p > 1 not built yet");
+    SSS_TRY(sss_local_sort(ctx, chars, n_chars, offsets, lengths, n, 1, params, out_perm, out_lcp));
+    if (out_dist) SSS_TRY(impl_dist(ctx, lengths, n, out_perm, out_lcp, out_dist));
+    if (out_approx) SSS_CUDA(cudaMemcpyAsync(out_approx, lengths, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice,
+                                             ctx->stream));
+    return SSS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,229 @@
+// Device-side helpers: character words, LCP extension, block scans, bitonic sort.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define SSS_FULL 0xFFFFFFFFu
+
+__device__ __forceinline__ uint64_t bswap64(uint64_t x) {
+    uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+    return ((uint64_t)__byte_perm(lo, 0, 0x0123) << 32) | (uint64_t)__byte_perm(hi, 0, 0x0123);
+}
+
+// The 8 characters s[d .. d+8) as a big-endian word, bytes at or past `len` zero
+// (the implicit sentinel sorts below every character, so word order == string
+// order on these 8 characters).  Reads only 8-byte-aligned words that contain at
+// least one character of the string, so it never touches a page the string does
+// not touch.
+__device__ __forceinline__ uint64_t load_word_be(const uint8_t* __restrict__ s, uint32_t len, uint32_t d) {
+    if (d >= len) return 0;
+    uintptr_t ai = (uintptr_t)(s + d);
+    const uint64_t* base = reinterpret_cast<const uint64_t*>(ai & ~uintptr_t(7));
+    uint32_t sh = (uint32_t)(ai & 7);
+    uint32_t rem = len - d;
+    uint64_t x = bswap64(__ldg(base)) << (8 * sh);
+    if (sh != 0 && rem > 8 - sh) x |= bswap64(__ldg(base + 1)) >> (64 - 8 * sh);
+    if (rem < 8) x &= ~0ull << (8 * (8 - rem));
+    return x;
+}
+
+// Number of equal characters of a[d..] and b[d..], capped at min(la, lb) - d.
+// Stops early (returning some value >= *runmin) once it has passed *runmin: the
+// caller only needs the minimum over a group, and runmin only decreases.
+__device__ __forceinline__ uint32_t lcp_extend(const uint8_t* __restrict__ a, uint32_t la,
+                                               const uint8_t* __restrict__ b, uint32_t lb, uint32_t d,
+                                               const volatile uint32_t* runmin) {
+    uint32_t m = la < lb ? la : lb;
+    if (d >= m) return 0;
+    uint32_t cap = m - d;
+    for (uint32_t k = 0; k < cap; k += 8) {
+        if (runmin != nullptr && k >= *runmin) return k;
+        uint64_t x = load_word_be(a, la, d + k) ^ load_word_be(b, lb, d + k);
+        if (x) {
+            uint32_t r = k + ((uint32_t)__clzll((long long)x) >> 3);
+            return r < cap ? r : cap;
+        }
+    }
+    return cap;
+}
+
+// First differing character of two distinct words, counted from the word start.
+__device__ __forceinline__ uint32_t word_lcp(uint64_t a, uint64_t b) {
+    uint64_t x = a ^ b;
+    return x ? ((uint32_t)__clzll((long long)x) >> 3) : 8u;
+}
+
+// True if the word contains a zero byte, i.e. the string ended inside it.
+__device__ __forceinline__ bool word_has_zero(uint64_t k) {
+    return ((k - 0x0101010101010101ull) & ~k & 0x8080808080808080ull) != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide scans over THREADS threads, each owning one value.
+template <int THREADS>
+struct BlockScan {
+    static constexpr int WARPS = (THREADS + 31) / 32;
+    // exclusive sum; *total receives the block sum (all threads)
+    __device__ static uint32_t exclusive_sum(uint32_t v, uint32_t* sh_warp, uint32_t* total) {
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(SSS_FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sh_warp[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t t = lane < WARPS ? sh_warp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(SSS_FULL, t, o);
+                if (lane >= o) t += y;
+            }
+            if (lane < WARPS) sh_warp[lane] = t;  // inclusive warp prefix
+        }
+        __syncthreads();
+        uint32_t base = w > 0 ? sh_warp[w - 1] : 0;
+        uint32_t tot = sh_warp[WARPS - 1];
+        __syncthreads();
+        if (total) *total = tot;
+        return base + x - v;
+    }
+    // inclusive max
+    __device__ static uint32_t inclusive_max(uint32_t v, uint32_t* sh_warp) {
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(SSS_FULL, x, o);
+            if (lane >= o) x = x > y ? x : y;
+        }
+        if (lane == 31) sh_warp[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t t = lane < WARPS ? sh_warp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(SSS_FULL, t, o);
+                if (lane >= o) t = t > y ? t : y;
+            }
+            if (lane < WARPS) sh_warp[lane] = t;
+        }
+        __syncthreads();
+        uint32_t base = w > 0 ? sh_warp[w - 1] : 0;
+        __syncthreads();
+        return x > base ? x : base;
+    }
+};
+
+// Exclusive sum over `count` items held ITEMS-per-thread in a contiguous blocked
+// layout of an smem array (in place); returns the total.
+template <int THREADS, int ITEMS>
+__device__ uint32_t block_exclusive_sum_inplace(uint32_t* a, uint32_t count, uint32_t* sh_warp) {
+    uint32_t loc[ITEMS];
+    uint32_t sum = 0;
+    int b = threadIdx.x * ITEMS;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t v = (uint32_t)(b + i) < count ? a[b + i] : 0;
+        loc[i] = sum;
+        sum += v;
+    }
+    uint32_t total;
+    uint32_t off = BlockScan<THREADS>::exclusive_sum(sum, sh_warp, &total);
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i)
+        if ((uint32_t)(b + i) < count) a[b + i] = off + loc[i];
+    __syncthreads();
+    return total;
+}
+
+// Inclusive max over a blocked smem array (in place).
+template <int THREADS, int ITEMS>
+__device__ void block_inclusive_max_inplace(uint32_t* a, uint32_t count, uint32_t* sh_warp) {
+    uint32_t loc[ITEMS];
+    uint32_t m = 0;
+    int b = threadIdx.x * ITEMS;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t v = (uint32_t)(b + i) < count ? a[b + i] : 0;
+        m = v > m ? v : m;
+        loc[i] = m;
+    }
+    // exclusive max of thread totals = inclusive max of previous threads
+    uint32_t incl = BlockScan<THREADS>::inclusive_max(m, sh_warp);
+    uint32_t prev = __shfl_up_sync(SSS_FULL, incl, 1);
+    // thread 0 of each warp needs the previous warp's inclusive value
+    __shared__ uint32_t sh_last[(THREADS + 31) / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 31) sh_last[w] = incl;
+    __syncthreads();
+    if (lane == 0) prev = w > 0 ? sh_last[w - 1] : 0;
+    if (threadIdx.x == 0) prev = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i)
+        if ((uint32_t)(b + i) < count) a[b + i] = loc[i] > prev ? loc[i] : prev;
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// In-shared-memory bitonic sort of `count` 128-bit keys (hi, lo), ascending,
+// padded to the next power of two with all-ones keys (count <= CAP).
+__device__ __forceinline__ bool key128_less(uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl) {
+    return ah < bh || (ah == bh && al < bl);
+}
+
+template <int THREADS>
+__device__ void bitonic_sort128(uint64_t* hi, uint64_t* lo, uint32_t count) {
+    uint32_t P = 1;
+    while (P < count) P <<= 1;
+    for (uint32_t i = count + threadIdx.x; i < P; i += THREADS) {
+        hi[i] = ~0ull;
+        lo[i] = ~0ull;
+    }
+    __syncthreads();
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t t = threadIdx.x; t < P / 2; t += THREADS) {
+                // t-th compare-exchange pair of this stage
+                uint32_t i = 2 * j * (t / j) + (t % j);
+                uint32_t ixj = i + j;
+                bool up = (i & k) == 0;
+                uint64_t ah = hi[i], al = lo[i], bh = hi[ixj], bl = lo[ixj];
+                bool sw = up ? key128_less(bh, bl, ah, al) : key128_less(ah, al, bh, bl);
+                if (sw) {
+                    hi[i] = bh;
+                    lo[i] = bl;
+                    hi[ixj] = ah;
+                    lo[ixj] = al;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int THREADS>
+__device__ void bitonic_sort64(uint64_t* a, uint32_t count) {
+    uint32_t P = 1;
+    while (P < count) P <<= 1;
+    for (uint32_t i = count + threadIdx.x; i < P; i += THREADS) a[i] = ~0ull;
+    __syncthreads();
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t t = threadIdx.x; t < P / 2; t += THREADS) {
+                uint32_t i = 2 * j * (t / j) + (t % j);
+                uint32_t ixj = i + j;
+                bool up = (i & k) == 0;
+                uint64_t x = a[i], y = a[ixj];
+                if (up ? (y < x) : (x < y)) {
+                    a[i] = y;
+                    a[ixj] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}

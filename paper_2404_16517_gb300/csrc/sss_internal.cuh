@@ -1,0 +1,155 @@
+// Internal host/device declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sss.h"
+
+// ---------------------------------------------------------------------------
+// Device error word bits (sticky until sss_sync).
+enum : unsigned {
+    ERRBIT_CHECK = 1u,     // SSS_CHECKED validation failed
+    ERRBIT_TIMEOUT = 2u,   // a bounded wait ran out
+    ERRBIT_OVERFLOW = 4u,  // an internal capacity was exceeded (library bug)
+};
+
+// A segment of consecutive positions whose strings share their first `depth`
+// characters (and are still to be ordered by the characters from `depth` on).
+struct Seg {
+    uint32_t start;
+    uint32_t size;
+    uint32_t depth;
+    uint32_t aux;
+};
+
+// ---------------------------------------------------------------------------
+// Bump allocator over one device buffer.  With base == nullptr it only counts,
+// so the same carving code gives the workspace size.
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+struct KStat {
+    const char* name;
+    uint64_t launches;
+    double ms;
+    uint64_t timed;
+};
+
+struct PendingTiming {
+    int stat;
+    cudaEvent_t a, b;
+};
+
+struct sss_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    // library-owned work memory
+    void* ws_own = nullptr;
+    size_t ws_own_bytes = 0;
+    // caller-supplied work memory
+    void* ws_user = nullptr;
+    size_t ws_user_bytes = 0;
+    // pinned host staging for small counters and segment lists
+    void* h_pin = nullptr;
+    size_t h_pin_bytes = 0;
+    // sticky device error word
+    unsigned* d_err = nullptr;
+    std::string last_error;
+    // instrumentation
+    KStat stats[SSS_MAX_KERNELS];
+    int nstats = 0;
+    bool timing = false;
+    std::string timing_filter;
+    std::vector<PendingTiming> pending;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+// Set ctx->last_error and return the status.
+sss_status sss_fail(sss_ctx* c, sss_status s, const std::string& msg);
+
+// Check a CUDA runtime result; on failure record it and return SSS_ERR_CUDA.
+#define SSS_CUDA(call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return sss_fail(ctx, SSS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define SSS_TRY(expr)                 \
+    do {                              \
+        sss_status s_ = (expr);       \
+        if (s_ != SSS_OK) return s_;  \
+    } while (0)
+
+// Work memory of at least `bytes`; grows library-owned memory when needed.
+sss_status sss_workspace(sss_ctx* ctx, size_t bytes, char** out);
+// Pinned host staging of at least `bytes`.
+sss_status sss_pinned(sss_ctx* ctx, size_t bytes, void** out);
+
+// Instrumentation hooks used by the launch wrapper.
+int sss_stat_index(sss_ctx* ctx, const char* name);
+bool sss_timing_on(sss_ctx* ctx, int stat);
+cudaEvent_t sss_event(sss_ctx* ctx);
+
+// Launch a kernel on the context stream, counting it (and timing it with CUDA
+// events when enabled).  Grids with zero blocks launch nothing.
+template <typename... KArgs, typename... Args>
+sss_status sss_launch(sss_ctx* ctx, const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                      size_t smem, Args... args) {
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0) return SSS_OK;
+    int st = sss_stat_index(ctx, name);
+    bool timed = sss_timing_on(ctx, st);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (timed) {
+        a = sss_event(ctx);
+        b = sss_event(ctx);
+        cudaEventRecord(a, ctx->stream);
+    }
+    kernel<<<grid, block, smem, ctx->stream>>>(static_cast<KArgs>(args)...);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return sss_fail(ctx, SSS_ERR_CUDA, std::string("launch ") + name + ": " + cudaGetErrorString(e));
+    if (timed) {
+        cudaEventRecord(b, ctx->stream);
+        ctx->pending.push_back({st, a, b});
+    }
+    if (st >= 0) ctx->stats[st].launches++;
+    return SSS_OK;
+}
+
+inline uint32_t part_lo(uint32_t n, uint32_t p, uint32_t i) {
+    return (uint32_t)(((uint64_t)i * n) / p);
+}
+
+// Stage implementations (one per translation unit).  They enqueue on ctx->stream
+// and carve their work memory from `ar` (which may be a counting arena).
+struct StrIn {
+    const uint8_t* chars;
+    uint64_t n_chars;
+    const uint64_t* offs;
+    const uint32_t* lens;
+    uint32_t n;
+};
+
+sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p, const sss_params& prm,
+                           uint32_t* perm, uint32_t* lcp);
+size_t need_local_sort(uint32_t n, uint32_t p, const sss_params& prm);
+
+sss_status impl_dist(sss_ctx* ctx, const uint32_t* lens, uint32_t n, const uint32_t* perm, const uint32_t* lcp,
+                     uint32_t* dist);
+
+sss_status impl_check_input(sss_ctx* ctx, const StrIn& in);

@@ -1,0 +1,714 @@
+// Stage A: local string sort of every partition with LCP-array output
+// (Section 3, "Initialization": each PE sorts its local strings; the LCP array
+// is a by-product of sorting).  A6: exact distinguishing prefixes (Section 2).
+//
+// Design (GB300): MSD radix sort over 8-byte big-endian character words.
+//  * A segment is a run of positions whose strings share their first `depth`
+//    characters.  Before a segment is split, its common prefix beyond `depth` is
+//    found by comparing every member with the segment's first member (running
+//    minimum, early exit) and the depth jumps by that amount ("equal-word skip").
+//  * Segments of <= 2048 strings are finished inside one CTA: keys are gathered,
+//    sorted in shared memory as (group, word, index) and split, until every group
+//    is a single string or a run of equal strings.
+//  * Larger segments take a multi-CTA round: gather the word at the new depth,
+//    sample splitters, classify into range and equality buckets (equal words
+//    always share a bucket), stable scatter, sort each range bucket in shared
+//    memory, and emit the groups of equal words as new segments.
+//  * LCP values fall out at every split: depth + first differing byte of the
+//    two words; equal strings get lcp = their length.
+#include <algorithm>
+#include <vector>
+
+#include "sss_device.cuh"
+#include "sss_internal.cuh"
+
+namespace {
+
+constexpr uint32_t DONE = 0xFFFFFFFFu;
+constexpr uint32_t INF32 = 0xFFFFFFFFu;
+
+// size classes
+constexpr int TINY_T = 64, TINY_CAP = 64;       // segments of 2..64 strings
+constexpr int MED_T = 256, MED_CAP = 2048;      // segments of 65..2048 strings
+constexpr int LG_TILE = 1024, LG_T = 256;       // large path tile / threads
+constexpr int LG_OVS = 16;                      // samples per range bucket
+constexpr int LG_BMAX = 256;                    // max range buckets per segment
+constexpr int LG_NBMAX = 2 * LG_BMAX - 1;       // range + equality buckets
+constexpr int BK_T = 512, BK_CAP = 4096;        // bucket sort CTA
+constexpr int LG_TARGET = BK_CAP / 2;           // target range-bucket size
+
+struct SegLists {
+    Seg* tiny;
+    Seg* med;
+    Seg* large;
+    uint32_t* cnt;  // [0] tiny, [1] med, [2] large
+    uint32_t cap_tiny, cap_med, cap_large;
+};
+
+__device__ __forceinline__ void push_seg(const SegLists& L, uint32_t start, uint32_t size, uint32_t depth,
+                                         unsigned* err) {
+    Seg s{start, size, depth, 0};
+    if (size <= (uint32_t)TINY_CAP) {
+        uint32_t i = atomicAdd(&L.cnt[0], 1u);
+        if (i < L.cap_tiny) L.tiny[i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
+    } else if (size <= (uint32_t)MED_CAP) {
+        uint32_t i = atomicAdd(&L.cnt[1], 1u);
+        if (i < L.cap_med) L.med[i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
+    } else {
+        uint32_t i = atomicAdd(&L.cnt[2], 1u);
+        if (i < L.cap_large) L.large[i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
+    }
+}
+
+__global__ void k_init_perm(uint32_t* perm, uint32_t* lcp, uint32_t n) {
+    uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) {
+        perm[q] = q;
+        lcp[q] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CTA finisher: completely sorts one segment of <= CAP strings.
+template <int THREADS, int CAP>
+__global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs, const uint8_t* __restrict__ chars,
+                                                    const uint64_t* __restrict__ offs,
+                                                    const uint32_t* __restrict__ lens, uint32_t* __restrict__ perm,
+                                                    uint32_t* __restrict__ lcp, unsigned* err) {
+    constexpr int ITEMS = CAP / THREADS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* sHi = reinterpret_cast<uint64_t*>(smem);  // sort keys (group:16 | word>>16)
+    uint64_t* sLo = sHi + CAP;                           // (word<<48 | string index)
+    uint32_t* sV = reinterpret_cast<uint32_t*>(sLo + CAP);  // string index at local position
+    uint32_t* sG = sV + CAP;                             // group start of element, DONE when final
+    uint32_t* sGD = sG + CAP;                            // depth of group (at its start)
+    uint32_t* sGM = sGD + CAP;                           // running min / member count (at group start)
+    uint32_t* sA = sGM + CAP;                            // scan buffer
+    uint32_t* sC = sA + CAP;                             // compacted active positions
+    __shared__ uint32_t sh_warp[32];
+
+    const Seg sg = segs[blockIdx.x];
+    const uint32_t m = sg.size;
+    const int tid = threadIdx.x;
+    for (uint32_t i = tid; i < m; i += THREADS) {
+        sV[i] = perm[sg.start + i];
+        sG[i] = 0;
+    }
+    if (tid == 0) sGD[0] = sg.depth;
+    __syncthreads();
+
+    // every iteration splits a group or finishes it, so a segment of m strings
+    // needs at most about 2m iterations; the bound only guards against bugs
+    for (uint32_t iter = 0;; ++iter) {
+        if (iter > 4u * (uint32_t)CAP + 64u) {
+            if (tid == 0) atomicOr(err, ERRBIT_OVERFLOW);
+            break;
+        }
+        // 1. compact the positions of unfinished elements
+        for (uint32_t i = tid; i < (uint32_t)CAP; i += THREADS) sA[i] = (i < m && sG[i] != DONE) ? 1u : 0u;
+        __syncthreads();
+        uint32_t nact = block_exclusive_sum_inplace<THREADS, ITEMS>(sA, CAP, sh_warp);
+        if (nact == 0) break;
+        for (uint32_t i = tid; i < m; i += THREADS)
+            if (sG[i] != DONE) sC[sA[i]] = i;
+        for (uint32_t i = tid; i < m; i += THREADS)
+            if (sG[i] == i) sGM[i] = INF32;
+        __syncthreads();
+
+        // 2. common prefix of each group beyond its depth (compare with the group's first member)
+        for (uint32_t j = tid; j < nact; j += THREADS) {
+            uint32_t pos = sC[j];
+            uint32_t g = sG[pos];
+            if (pos == g) continue;
+            uint32_t e = sV[pos], r = sV[g];
+            uint32_t v = lcp_extend(chars + offs[e], lens[e], chars + offs[r], lens[r], sGD[g], &sGM[g]);
+            atomicMin(&sGM[g], v);
+        }
+        __syncthreads();
+
+        // 3. gather the word at the new depth; pack (group, word, index)
+        for (uint32_t j = tid; j < nact; j += THREADS) {
+            uint32_t pos = sC[j];
+            uint32_t g = sG[pos];
+            uint32_t d = sGD[g] + sGM[g];
+            uint32_t e = sV[pos];
+            uint64_t k = load_word_be(chars + offs[e], lens[e], d);
+            sHi[j] = ((uint64_t)g << 48) | (k >> 16);
+            sLo[j] = (k << 48) | (uint64_t)e;
+        }
+        __syncthreads();
+        for (uint32_t j = tid; j < nact; j += THREADS) {
+            uint32_t pos = sC[j];
+            if (sG[pos] == pos) sGD[pos] += sGM[pos];
+        }
+        __syncthreads();
+
+        // 4. sort (group, word, index)
+        bitonic_sort128<THREADS>(sHi, sLo, nact);
+
+        // 5. write back, find new group boundaries, LCP at new boundaries
+        for (uint32_t j = tid; j < nact; j += THREADS) {
+            uint32_t pos = sC[j];
+            uint64_t hi = sHi[j], lo = sLo[j];
+            uint32_t g = (uint32_t)(hi >> 48);
+            uint64_t k = (hi << 16) | (lo >> 48);
+            sV[pos] = (uint32_t)lo;
+            bool bnd = true;
+            if (j > 0) {
+                uint64_t hp = sHi[j - 1], lp = sLo[j - 1];
+                uint32_t gp = (uint32_t)(hp >> 48);
+                uint64_t kp = (hp << 16) | (lp >> 48);
+                if (gp == g) {
+                    bnd = (kp != k);
+                    if (bnd) lcp[sg.start + pos] = sGD[g] + word_lcp(kp, k);
+                }
+            }
+            sA[j] = bnd ? pos : 0u;
+        }
+        __syncthreads();
+        block_inclusive_max_inplace<THREADS, ITEMS>(sA, nact, sh_warp);
+
+        // 6. member count of every new group
+        for (uint32_t j = tid; j < nact; j += THREADS)
+            if (sA[j] == sC[j]) sGM[sC[j]] = 0;
+        __syncthreads();
+        for (uint32_t j = tid; j < nact; j += THREADS) atomicAdd(&sGM[sA[j]], 1u);
+        __syncthreads();
+
+        // 7. classify: single strings and runs of equal strings are final
+        uint32_t dnew[ITEMS];
+#pragma unroll
+        for (int t = 0; t < ITEMS; ++t) {
+            uint32_t j = tid + t * THREADS;
+            if (j < nact) dnew[t] = sGD[(uint32_t)(sHi[j] >> 48)];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < ITEMS; ++t) {
+            uint32_t j = tid + t * THREADS;
+            if (j >= nact) continue;
+            uint32_t pos = sC[j];
+            uint32_t ng = sA[j];
+            uint64_t k = (sHi[j] << 16) | (sLo[j] >> 48);
+            uint32_t cnt = sGM[ng];
+            if (cnt == 1) {
+                sG[pos] = DONE;
+            } else if (word_has_zero(k)) {
+                sG[pos] = DONE;
+                if (pos != ng) lcp[sg.start + pos] = lens[(uint32_t)sLo[j]];
+            } else {
+                sG[pos] = ng;
+                if (pos == ng) sGD[ng] = dnew[t] + 8;
+            }
+        }
+        __syncthreads();
+    }
+    for (uint32_t i = tid; i < m; i += THREADS) perm[sg.start + i] = sV[i];
+}
+
+constexpr size_t finish_smem(int cap) { return (size_t)cap * (8 + 8 + 4 * 6); }
+
+// ---------------------------------------------------------------------------
+// Large path.
+struct LgSegInfo {
+    Seg seg;            // start, size, depth
+    uint32_t tiles;     // number of tiles
+    uint32_t tile0;     // first tile index
+    uint32_t nb;        // range buckets B (splitters B-1, buckets 2B-1)
+    uint32_t hist_base; // offset into hist (bucket-major: b*tiles + t)
+    uint32_t bst_base;  // offset into bucket starts (2B entries)
+    uint32_t pad[3];
+};
+
+struct LgTile {
+    uint32_t s;      // segment index
+    uint32_t begin;  // absolute first position
+    uint32_t end;    // absolute end position
+    uint32_t t;      // tile index within segment
+};
+
+__global__ void __launch_bounds__(LG_T) k_lg_ext(const LgTile* __restrict__ tiles, const LgSegInfo* __restrict__ info,
+                                                 const uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
+                                                 const uint32_t* __restrict__ lens, const uint32_t* __restrict__ perm,
+                                                 uint32_t* segmin) {
+    LgTile tl = tiles[blockIdx.x];
+    LgSegInfo si = info[tl.s];
+    uint32_t r = perm[si.seg.start];
+    const uint8_t* rs = chars + offs[r];
+    uint32_t rl = lens[r];
+    uint32_t best = INF32;
+    for (uint32_t q = tl.begin + threadIdx.x; q < tl.end; q += LG_T) {
+        if (q == si.seg.start) continue;
+        uint32_t e = perm[q];
+        uint32_t v = lcp_extend(chars + offs[e], lens[e], rs, rl, si.seg.depth, &segmin[tl.s]);
+        best = v < best ? v : best;
+    }
+    best = __reduce_min_sync(SSS_FULL, best);
+    if ((threadIdx.x & 31) == 0 && best < *((volatile uint32_t*)&segmin[tl.s])) atomicMin(&segmin[tl.s], best);
+}
+
+__global__ void __launch_bounds__(LG_T) k_lg_keys(const LgTile* __restrict__ tiles, const LgSegInfo* __restrict__ info,
+                                                  const uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
+                                                  const uint32_t* __restrict__ lens, const uint32_t* __restrict__ perm,
+                                                  const uint32_t* __restrict__ segmin, uint64_t* __restrict__ K) {
+    LgTile tl = tiles[blockIdx.x];
+    uint32_t d = info[tl.s].seg.depth + segmin[tl.s];
+    for (uint32_t q = tl.begin + threadIdx.x; q < tl.end; q += LG_T) {
+        uint32_t e = perm[q];
+        K[q] = load_word_be(chars + offs[e], lens[e], d);
+    }
+}
+
+// One CTA per segment: evenly spaced samples, sorted; splitter b = sample (b+1)*OVS-1.
+__global__ void __launch_bounds__(512) k_lg_samples(const LgSegInfo* __restrict__ info, const uint64_t* __restrict__ K,
+                                                    uint64_t* __restrict__ spl) {
+    __shared__ uint64_t sh[LG_BMAX * LG_OVS];
+    LgSegInfo si = info[blockIdx.x];
+    uint32_t S = si.nb * LG_OVS;
+    for (uint32_t i = threadIdx.x; i < S; i += 512) {
+        uint64_t q = si.seg.start + ((2 * (uint64_t)i + 1) * si.seg.size) / (2 * (uint64_t)S);
+        sh[i] = K[q];
+    }
+    __syncthreads();
+    bitonic_sort64<512>(sh, S);
+    for (uint32_t b = threadIdx.x; b + 1 < si.nb; b += 512)
+        spl[(size_t)blockIdx.x * (LG_BMAX - 1) + b] = sh[(b + 1) * LG_OVS - 1];
+}
+
+// first splitter >= k (lower bound) among nsp sorted splitters
+__device__ __forceinline__ uint32_t lower_bound64(const uint64_t* s, uint32_t nsp, uint64_t k) {
+    uint32_t lo = 0, hi = nsp;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (s[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(LG_T) k_lg_classify(const LgTile* __restrict__ tiles,
+                                                      const LgSegInfo* __restrict__ info,
+                                                      const uint64_t* __restrict__ K, const uint64_t* __restrict__ spl,
+                                                      uint32_t* __restrict__ hist, uint32_t* __restrict__ rankinfo) {
+    constexpr int W = LG_T / 32;
+    constexpr int PER_WARP = LG_TILE / W;  // contiguous positions per warp
+    __shared__ uint64_t ssp[LG_BMAX];
+    __shared__ uint32_t cnt[W][LG_NBMAX];
+    LgTile tl = tiles[blockIdx.x];
+    LgSegInfo si = info[tl.s];
+    uint32_t nsp = si.nb - 1, nbk = 2 * si.nb - 1;
+    for (uint32_t i = threadIdx.x; i < nsp; i += LG_T) ssp[i] = spl[(size_t)tl.s * (LG_BMAX - 1) + i];
+    for (uint32_t i = threadIdx.x; i < (uint32_t)(W * LG_NBMAX); i += LG_T) (&cnt[0][0])[i] = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t lt = (1u << lane) - 1u;
+    uint32_t myb[PER_WARP / 32], myr[PER_WARP / 32];
+#pragma unroll
+    for (int it = 0; it < PER_WARP / 32; ++it) {
+        uint32_t q = tl.begin + w * PER_WARP + it * 32 + lane;
+        bool valid = q < tl.end;
+        uint32_t b = 0xFFFFu;
+        if (valid) {
+            uint64_t k = K[q];
+            uint32_t lb = lower_bound64(ssp, nsp, k);
+            b = 2 * lb + ((lb < nsp && ssp[lb] == k) ? 1u : 0u);
+        }
+        uint32_t peers = __match_any_sync(SSS_FULL, b);
+        uint32_t leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (valid && lane == (int)leader) {
+            base = cnt[w][b];
+            cnt[w][b] = base + __popc(peers);
+        }
+        base = __shfl_sync(SSS_FULL, base, leader);
+        myb[it] = b;
+        myr[it] = base + __popc(peers & lt);
+    }
+    __syncthreads();
+    // exclusive prefix over warps for every bucket; tile total into hist
+    for (uint32_t b = threadIdx.x; b < nbk; b += LG_T) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int ww = 0; ww < W; ++ww) {
+            uint32_t t = cnt[ww][b];
+            cnt[ww][b] = run;
+            run += t;
+        }
+        hist[si.hist_base + b * si.tiles + tl.t] = run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < PER_WARP / 32; ++it) {
+        uint32_t q = tl.begin + w * PER_WARP + it * 32 + lane;
+        if (q < tl.end) rankinfo[q] = (myb[it] << 16) | (cnt[w][myb[it]] + myr[it]);
+    }
+}
+
+// Per segment: prefix of every bucket over the tiles, then bucket starts.
+__global__ void __launch_bounds__(512) k_lg_offsets(const LgSegInfo* __restrict__ info, uint32_t* __restrict__ hist,
+                                                    uint32_t* __restrict__ bst) {
+    __shared__ uint32_t sh_warp[32];
+    LgSegInfo si = info[blockIdx.x];
+    uint32_t nbk = 2 * si.nb - 1;
+    uint32_t b = threadIdx.x;
+    uint32_t tot = 0;
+    if (b < nbk) {
+        uint32_t* h = hist + si.hist_base + b * si.tiles;
+        for (uint32_t t = 0; t < si.tiles; ++t) {
+            uint32_t v = h[t];
+            h[t] = tot;
+            tot += v;
+        }
+    }
+    uint32_t total;
+    uint32_t ex = BlockScan<512>::exclusive_sum(tot, sh_warp, &total);
+    if (b < nbk) bst[si.bst_base + b] = si.seg.start + ex;
+    if (b == 0) bst[si.bst_base + nbk] = si.seg.start + si.seg.size;
+}
+
+__global__ void __launch_bounds__(LG_T) k_lg_scatter(const LgTile* __restrict__ tiles, const LgSegInfo* __restrict__ info,
+                                                     const uint32_t* __restrict__ hist, const uint32_t* __restrict__ bst,
+                                                     const uint32_t* __restrict__ rankinfo,
+                                                     const uint64_t* __restrict__ K, const uint32_t* __restrict__ perm,
+                                                     uint64_t* __restrict__ tK, uint32_t* __restrict__ tV,
+                                                     unsigned* err) {
+    LgTile tl = tiles[blockIdx.x];
+    LgSegInfo si = info[tl.s];
+    for (uint32_t q = tl.begin + threadIdx.x; q < tl.end; q += LG_T) {
+        uint32_t ri = rankinfo[q];
+        uint32_t b = ri >> 16;
+        uint32_t dst = bst[si.bst_base + b] + hist[si.hist_base + b * si.tiles + tl.t] + (ri & 0xFFFFu);
+        if (dst < si.seg.start || dst >= si.seg.start + si.seg.size) {
+            atomicOr(err, ERRBIT_OVERFLOW);
+            continue;
+        }
+        tK[dst] = K[q];
+        tV[dst] = perm[q];
+    }
+}
+
+// One CTA per (segment, bucket).  Range buckets are sorted in shared memory;
+// groups of equal words become new segments one word deeper.
+__global__ void __launch_bounds__(BK_T) k_lg_buckets(const LgSegInfo* __restrict__ info,
+                                                     const uint32_t* __restrict__ bst,
+                                                     const uint32_t* __restrict__ segmin,
+                                                     const uint64_t* __restrict__ tK, const uint32_t* __restrict__ tV,
+                                                     const uint32_t* __restrict__ lens, uint64_t* __restrict__ K,
+                                                     uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
+                                                     SegLists L, unsigned* err) {
+    constexpr int ITEMS = BK_CAP / BK_T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* sHi = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* sLo = sHi + BK_CAP;
+    uint32_t* sA = reinterpret_cast<uint32_t*>(sLo + BK_CAP);
+    uint32_t* sN = sA + BK_CAP;
+    __shared__ uint32_t sh_warp[32];
+    LgSegInfo si = info[blockIdx.y];
+    uint32_t b = blockIdx.x;
+    uint32_t nbk = 2 * si.nb - 1;
+    if (b >= nbk) return;
+    uint32_t bs = bst[si.bst_base + b], be = bst[si.bst_base + b + 1];
+    if (bs < si.seg.start || be > si.seg.start + si.seg.size || be < bs) {
+        if (threadIdx.x == 0) atomicOr(err, ERRBIT_OVERFLOW);
+        return;
+    }
+    uint32_t m = be - bs;
+    if (m == 0) return;
+    uint32_t d = si.seg.depth + segmin[blockIdx.y];
+    bool eq = (b & 1u) != 0;
+    if (eq || m > (uint32_t)BK_CAP) {
+        for (uint32_t q = bs + threadIdx.x; q < be; q += BK_T) {
+            K[q] = tK[q];
+            perm[q] = tV[q];
+        }
+        if (threadIdx.x == 0) {
+            if (eq) {
+                uint64_t k = tK[bs];
+                if (m >= 2 && !word_has_zero(k)) push_seg(L, bs, m, d + 8, err);
+            } else {
+                push_seg(L, bs, m, d, err);  // oversized range bucket: another round at this depth
+            }
+        }
+        if (eq && m >= 2 && word_has_zero(tK[bs])) {
+            // a run of equal strings: lcp = length inside the run
+            for (uint32_t q = bs + 1 + threadIdx.x; q < be; q += BK_T) lcp[q] = lens[tV[q]];
+        }
+        return;
+    }
+    for (uint32_t i = threadIdx.x; i < m; i += BK_T) {
+        sHi[i] = tK[bs + i];
+        sLo[i] = tV[bs + i];
+    }
+    __syncthreads();
+    bitonic_sort128<BK_T>(sHi, sLo, m);
+    for (uint32_t i = threadIdx.x; i < BK_CAP; i += BK_T) {
+        uint32_t v = 0;
+        if (i < m) {
+            uint64_t k = sHi[i];
+            K[bs + i] = k;
+            perm[bs + i] = (uint32_t)sLo[i];
+            bool bnd = (i == 0) || (sHi[i - 1] != k);
+            if (bnd && i > 0) lcp[bs + i] = d + word_lcp(sHi[i - 1], k);
+            v = bnd ? i : 0u;
+        }
+        sA[i] = v;
+    }
+    __syncthreads();
+    block_inclusive_max_inplace<BK_T, ITEMS>(sA, m, sh_warp);
+    for (uint32_t i = threadIdx.x; i < m; i += BK_T)
+        if (sA[i] == i) sN[i] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < m; i += BK_T) atomicAdd(&sN[sA[i]], 1u);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < m; i += BK_T) {
+        uint32_t g = sA[i];
+        uint32_t c = sN[g];
+        if (c < 2) continue;
+        uint64_t k = sHi[i];
+        if (word_has_zero(k)) {
+            if (i != g) lcp[bs + i] = lens[(uint32_t)sLo[i]];
+        } else if (i == g) {
+            push_seg(L, bs + g, c, d + 8, err);
+        }
+    }
+}
+
+// LCP at the first position of every non-first, non-empty bucket.
+__global__ void __launch_bounds__(512) k_lg_seams(const LgSegInfo* __restrict__ info, const uint32_t* __restrict__ bst,
+                                                  const uint32_t* __restrict__ segmin, const uint64_t* __restrict__ K,
+                                                  uint32_t* __restrict__ lcp) {
+    LgSegInfo si = info[blockIdx.x];
+    uint32_t nbk = 2 * si.nb - 1;
+    uint32_t d = si.seg.depth + segmin[blockIdx.x];
+    for (uint32_t b = threadIdx.x; b < nbk; b += 512) {
+        uint32_t bs = bst[si.bst_base + b], be = bst[si.bst_base + b + 1];
+        if (be > bs && bs > si.seg.start && be <= si.seg.start + si.seg.size)
+            lcp[bs] = d + word_lcp(K[bs - 1], K[bs]);
+    }
+}
+
+__global__ void k_dist(const uint32_t* __restrict__ lens, uint32_t n, const uint32_t* __restrict__ perm,
+                       const uint32_t* __restrict__ lcp, uint32_t* __restrict__ dist) {
+    uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    uint32_t left = r > 0 ? lcp[r] : 0;
+    uint32_t right = r + 1 < n ? lcp[r + 1] : 0;
+    uint32_t m = left > right ? left : right;
+    uint32_t i = perm[r];
+    uint64_t d = (uint64_t)m + 1;
+    dist[i] = d < lens[i] ? (uint32_t)d : lens[i];
+}
+
+__global__ void k_check_input(const uint8_t* __restrict__ chars, uint64_t n_chars, const uint64_t* __restrict__ offs,
+                              const uint32_t* __restrict__ lens, uint32_t n, unsigned* err) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t o = offs[i];
+    uint32_t l = lens[i];
+    if (o > n_chars || (uint64_t)l > n_chars - o || l >= 0x80000000u) {
+        atomicOr(err, ERRBIT_CHECK);
+        return;
+    }
+    for (uint32_t k = 0; k < l; ++k)
+        if (chars[o + k] == 0) {
+            atomicOr(err, ERRBIT_CHECK);
+            return;
+        }
+}
+
+// Work memory layout of the local sort.
+struct LsBufs {
+    uint64_t* K;
+    uint64_t* tK;
+    uint32_t* tV;
+    uint32_t* rankinfo;
+    Seg* tiny;
+    Seg* med;
+    Seg* large;
+    uint32_t* cnt;
+    uint32_t* segmin;
+    uint64_t* spl;
+    uint32_t* hist;
+    uint32_t* bst;
+    LgSegInfo* info;
+    LgTile* tiles;
+    uint32_t cap_tiny, cap_med, cap_large, cap_tiles, cap_hist;
+};
+
+void carve_ls(Arena& ar, uint32_t n, uint32_t p, LsBufs& b) {
+    b.cap_tiny = n / 2 + 2;
+    b.cap_med = n / (TINY_CAP + 1) + 2;
+    b.cap_large = n / (MED_CAP + 1) + p + 2;
+    b.cap_tiles = n / LG_TILE + b.cap_large + 2;
+    b.cap_hist = LG_NBMAX * b.cap_tiles;
+    b.K = ar.take<uint64_t>(n);
+    b.tK = ar.take<uint64_t>(n);
+    b.tV = ar.take<uint32_t>(n);
+    b.rankinfo = ar.take<uint32_t>(n);
+    b.tiny = ar.take<Seg>(b.cap_tiny);
+    b.med = ar.take<Seg>(b.cap_med);
+    b.large = ar.take<Seg>(b.cap_large);
+    b.cnt = ar.take<uint32_t>(4);
+    b.segmin = ar.take<uint32_t>(b.cap_large);
+    b.spl = ar.take<uint64_t>((size_t)b.cap_large * (LG_BMAX - 1));
+    b.hist = ar.take<uint32_t>(b.cap_hist);
+    b.bst = ar.take<uint32_t>((size_t)b.cap_large * (LG_NBMAX + 1));
+    b.info = ar.take<LgSegInfo>(b.cap_large);
+    b.tiles = ar.take<LgTile>(b.cap_tiles);
+}
+
+sss_status run_finishers(sss_ctx* ctx, const LsBufs& B, uint32_t ntiny, uint32_t nmed, const StrIn& in,
+                         uint32_t* perm, uint32_t* lcp) {
+    SSS_TRY(sss_launch(ctx, "ls_finish_tiny", k_finish<TINY_T, TINY_CAP>, dim3(ntiny), dim3(TINY_T),
+                       finish_smem(TINY_CAP), (const Seg*)B.tiny, in.chars, in.offs, in.lens, perm, lcp,
+                       ctx->d_err));
+    SSS_TRY(sss_launch(ctx, "ls_finish_cta", k_finish<MED_T, MED_CAP>, dim3(nmed), dim3(MED_T),
+                       finish_smem(MED_CAP), (const Seg*)B.med, in.chars, in.offs, in.lens, perm, lcp,
+                       ctx->d_err));
+    return SSS_OK;
+}
+
+}  // namespace
+
+size_t need_local_sort(uint32_t n, uint32_t p, const sss_params& prm) {
+    (void)prm;
+    Arena ar;
+    LsBufs b;
+    carve_ls(ar, n, p, b);
+    return ar.off + 256;
+}
+
+static bool g_attr_done[64];
+
+sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p, const sss_params& prm,
+                           uint32_t* perm, uint32_t* lcp) {
+    (void)prm;
+    const uint32_t n = in.n;
+    if (n == 0) return SSS_OK;
+    LsBufs B;
+    carve_ls(ar, n, p, B);
+    if (!g_attr_done[ctx->device & 63]) {
+        SSS_CUDA(cudaFuncSetAttribute(k_finish<MED_T, MED_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)finish_smem(MED_CAP)));
+        SSS_CUDA(cudaFuncSetAttribute(k_finish<TINY_T, TINY_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)finish_smem(TINY_CAP)));
+        SSS_CUDA(cudaFuncSetAttribute(k_lg_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(BK_CAP * (8 + 8 + 4 + 4))));
+        g_attr_done[ctx->device & 63] = true;
+    }
+    SSS_TRY(sss_launch(ctx, "ls_init", k_init_perm, dim3((n + 255) / 256), dim3(256), 0, perm, lcp, n));
+
+    // initial segments: the partitions
+    std::vector<Seg> tiny, med, large;
+    for (uint32_t i = 0; i < p; ++i) {
+        uint32_t lo = part_lo(n, p, i), hi = part_lo(n, p, i + 1);
+        uint32_t sz = hi - lo;
+        if (sz < 2) continue;
+        Seg s{lo, sz, 0, 0};
+        if (sz <= (uint32_t)TINY_CAP) tiny.push_back(s);
+        else if (sz <= (uint32_t)MED_CAP) med.push_back(s);
+        else large.push_back(s);
+    }
+    // pinned staging: segment info + tiles + counters
+    size_t pin_bytes = sizeof(uint32_t) * 4 + sizeof(Seg) * (size_t)(B.cap_large + B.cap_med + B.cap_tiny) +
+                       sizeof(LgSegInfo) * B.cap_large + sizeof(LgTile) * B.cap_tiles + 1024;
+    void* pin;
+    SSS_TRY(sss_pinned(ctx, pin_bytes, &pin));
+    uint32_t* h_cnt = reinterpret_cast<uint32_t*>(pin);
+    Seg* h_seg = reinterpret_cast<Seg*>(reinterpret_cast<char*>(pin) + 64);
+    LgSegInfo* h_info = reinterpret_cast<LgSegInfo*>(h_seg + (B.cap_large + B.cap_med + B.cap_tiny));
+    LgTile* h_tiles = reinterpret_cast<LgTile*>(h_info + B.cap_large);
+
+    if (!tiny.empty() || !med.empty()) {
+        std::copy(tiny.begin(), tiny.end(), h_seg);
+        std::copy(med.begin(), med.end(), h_seg + tiny.size());
+        SSS_CUDA(cudaMemcpyAsync(B.tiny, h_seg, sizeof(Seg) * tiny.size(), cudaMemcpyHostToDevice, ctx->stream));
+        SSS_CUDA(cudaMemcpyAsync(B.med, h_seg + tiny.size(), sizeof(Seg) * med.size(), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+        SSS_TRY(run_finishers(ctx, B, (uint32_t)tiny.size(), (uint32_t)med.size(), in, perm, lcp));
+        // staging is reused below: wait for the uploads
+        SSS_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+
+    SegLists L{B.tiny, B.med, B.large, B.cnt, B.cap_tiny, B.cap_med, B.cap_large};
+    uint32_t rounds = 0;
+    while (!large.empty()) {
+        if (++rounds > 100000u) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: round limit exceeded");
+        uint32_t ns = (uint32_t)large.size();
+        uint32_t ntiles = 0, hist_off = 0;
+        for (uint32_t s = 0; s < ns; ++s) {
+            const Seg& sg = large[s];
+            uint32_t tiles = (sg.size + LG_TILE - 1) / LG_TILE;
+            uint32_t nb = (sg.size + LG_TARGET - 1) / LG_TARGET;
+            nb = std::max(2u, std::min((uint32_t)LG_BMAX, nb));
+            LgSegInfo si{};
+            si.seg = sg;
+            si.tiles = tiles;
+            si.tile0 = ntiles;
+            si.nb = nb;
+            si.hist_base = hist_off;
+            si.bst_base = s * (LG_NBMAX + 1);
+            h_info[s] = si;
+            for (uint32_t t = 0; t < tiles; ++t) {
+                uint32_t b0 = sg.start + t * LG_TILE;
+                h_tiles[ntiles + t] = LgTile{s, b0, std::min(b0 + (uint32_t)LG_TILE, sg.start + sg.size), t};
+            }
+            ntiles += tiles;
+            hist_off += (2 * nb - 1) * tiles;
+        }
+        if (ntiles > B.cap_tiles || hist_off > B.cap_hist || ns > B.cap_large)
+            return sss_fail(ctx, SSS_ERR_CUDA, "local sort: internal capacity exceeded");
+        SSS_CUDA(cudaMemcpyAsync(B.info, h_info, sizeof(LgSegInfo) * ns, cudaMemcpyHostToDevice, ctx->stream));
+        SSS_CUDA(cudaMemcpyAsync(B.tiles, h_tiles, sizeof(LgTile) * ntiles, cudaMemcpyHostToDevice, ctx->stream));
+        SSS_CUDA(cudaMemsetAsync(B.segmin, 0xFF, sizeof(uint32_t) * ns, ctx->stream));
+        SSS_CUDA(cudaMemsetAsync(B.cnt, 0, sizeof(uint32_t) * 4, ctx->stream));
+        SSS_TRY(sss_launch(ctx, "ls_lg_ext", k_lg_ext, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.tiles,
+                           (const LgSegInfo*)B.info, in.chars, in.offs, in.lens, (const uint32_t*)perm, B.segmin));
+        SSS_TRY(sss_launch(ctx, "ls_lg_keys", k_lg_keys, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.tiles,
+                           (const LgSegInfo*)B.info, in.chars, in.offs, in.lens, (const uint32_t*)perm,
+                           (const uint32_t*)B.segmin, B.K));
+        SSS_TRY(sss_launch(ctx, "ls_lg_samples", k_lg_samples, dim3(ns), dim3(512), 0, (const LgSegInfo*)B.info,
+                           (const uint64_t*)B.K, B.spl));
+        SSS_TRY(sss_launch(ctx, "ls_lg_classify", k_lg_classify, dim3(ntiles), dim3(LG_T), 0,
+                           (const LgTile*)B.tiles, (const LgSegInfo*)B.info, (const uint64_t*)B.K,
+                           (const uint64_t*)B.spl, B.hist, B.rankinfo));
+        SSS_TRY(sss_launch(ctx, "ls_lg_offsets", k_lg_offsets, dim3(ns), dim3(512), 0, (const LgSegInfo*)B.info,
+                           B.hist, B.bst));
+        SSS_TRY(sss_launch(ctx, "ls_lg_scatter", k_lg_scatter, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.tiles,
+                           (const LgSegInfo*)B.info, (const uint32_t*)B.hist, (const uint32_t*)B.bst,
+                           (const uint32_t*)B.rankinfo, (const uint64_t*)B.K, (const uint32_t*)perm, B.tK, B.tV,
+                           ctx->d_err));
+        SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets, dim3(LG_NBMAX, ns), dim3(BK_T),
+                           (size_t)BK_CAP * (8 + 8 + 4 + 4), (const LgSegInfo*)B.info, (const uint32_t*)B.bst,
+                           (const uint32_t*)B.segmin, (const uint64_t*)B.tK, (const uint32_t*)B.tV, in.lens, B.K, perm,
+                           lcp, L, ctx->d_err));
+        SSS_TRY(sss_launch(ctx, "ls_lg_seams", k_lg_seams, dim3(ns), dim3(512), 0, (const LgSegInfo*)B.info,
+                           (const uint32_t*)B.bst, (const uint32_t*)B.segmin, (const uint64_t*)B.K, lcp));
+        SSS_CUDA(cudaMemcpyAsync(h_cnt, B.cnt, sizeof(uint32_t) * 3, cudaMemcpyDeviceToHost, ctx->stream));
+        SSS_CUDA(cudaMemcpyAsync(h_cnt + 3, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+        SSS_CUDA(cudaStreamSynchronize(ctx->stream));
+        if (h_cnt[3] & ERRBIT_OVERFLOW) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: device capacity check failed");
+        uint32_t ct = std::min(h_cnt[0], B.cap_tiny), cm = std::min(h_cnt[1], B.cap_med),
+                 cl = std::min(h_cnt[2], B.cap_large);
+        SSS_TRY(run_finishers(ctx, B, ct, cm, in, perm, lcp));
+        large.clear();
+        if (cl > 0) {
+            SSS_CUDA(cudaMemcpyAsync(h_seg, B.large, sizeof(Seg) * cl, cudaMemcpyDeviceToHost, ctx->stream));
+            SSS_CUDA(cudaStreamSynchronize(ctx->stream));
+            large.assign(h_seg, h_seg + cl);
+        } else {
+            // the finishers read the lists before the next round resets the counters
+            SSS_CUDA(cudaStreamSynchronize(ctx->stream));
+        }
+    }
+    return SSS_OK;
+}
+
+sss_status impl_dist(sss_ctx* ctx, const uint32_t* lens, uint32_t n, const uint32_t* perm, const uint32_t* lcp,
+                     uint32_t* dist) {
+    return sss_launch(ctx, "dist", k_dist, dim3((n + 255) / 256), dim3(256), 0, lens, n, perm, lcp, dist);
+}
+
+sss_status impl_check_input(sss_ctx* ctx, const StrIn& in) {
+    return sss_launch(ctx, "check_input", k_check_input, dim3((in.n + 255) / 256), dim3(256), 0, in.chars,
+                      in.n_chars, in.offs, in.lens, in.n, ctx->d_err);
+}
