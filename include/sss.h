@@ -90,8 +90,9 @@ sss_status sss_set_stream(sss_ctx* ctx, void* cuda_stream);
  * stay valid while calls that use it run; sss_workspace_bytes() gives the size. */
 sss_status sss_set_workspace(sss_ctx* ctx, void* dev_ptr, size_t bytes);
 
-/* Upper bound on the work memory a call with these sizes needs (bytes). */
-size_t sss_workspace_bytes(uint32_t n, uint32_t p, const sss_params* params);
+/* Upper bound on the work memory any call with these sizes needs (bytes):
+ * n strings with total_len = sum of lengths (an upper bound is fine), p partitions. */
+size_t sss_workspace_bytes(uint32_t n, uint64_t total_len, uint32_t p, const sss_params* params);
 
 /* Synchronise the context's stream and return the sticky device status
  * (SSS_OK, SSS_ERR_DEVICE_CHECK, SSS_ERR_TIMEOUT or SSS_ERR_CUDA); clears it. */

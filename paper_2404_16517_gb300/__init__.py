@@ -70,7 +70,7 @@ def lib():
             "sss_destroy": (st, [vp]),
             "sss_set_stream": (st, [vp, vp]),
             "sss_set_workspace": (st, [vp, vp, C.c_size_t]),
-            "sss_workspace_bytes": (C.c_size_t, [u32, u32, P]),
+            "sss_workspace_bytes": (C.c_size_t, [u32, u64, u32, P]),
             "sss_sync": (st, [vp]),
             "sss_status_string": (C.c_char_p, [st]),
             "sss_last_error": (C.c_char_p, [vp]),
@@ -277,9 +277,9 @@ def sss_sort(chars, offs, lens, p: int = 1, prm: sss_params | None = None, out_p
     return op, ol, d, a
 
 
-def workspace_bytes(n: int, p: int = 1, prm: sss_params | None = None) -> int:
+def workspace_bytes(n: int, total_len: int, p: int = 1, prm: sss_params | None = None) -> int:
     prm = prm or params()
-    return int(lib().sss_workspace_bytes(n, p, C.byref(prm)))
+    return int(lib().sss_workspace_bytes(n, total_len, p, C.byref(prm)))
 
 
 def to_device(ss, device="cuda"):

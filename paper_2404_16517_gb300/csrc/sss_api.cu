@@ -1,4 +1,5 @@
 // C ABI entry points: context, work memory, instrumentation and the stage calls.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -140,6 +141,11 @@ sss_status sss_create(sss_ctx** out, int device, void* stream) {
         return SSS_ERR_OOM;
     }
     cudaMemset(ctx->d_err, 0, sizeof(unsigned) * 4);
+    if (cudaMalloc(&ctx->d_small, 4096) != cudaSuccess) {
+        cudaFree(ctx->d_err);
+        delete ctx;
+        return SSS_ERR_OOM;
+    }
     cudaDeviceSynchronize();
     *out = ctx;
     return SSS_OK;
@@ -154,6 +160,7 @@ sss_status sss_destroy(sss_ctx* ctx) {
     if (ctx->ws_own) cudaFree(ctx->ws_own);
     if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_small) cudaFree(ctx->d_small);
     delete ctx;
     return SSS_OK;
 }
@@ -240,6 +247,11 @@ static sss_status check_common(sss_ctx* ctx, const uint8_t* chars, const uint64_
     return SSS_OK;
 }
 
+static sss_status checked_input(sss_ctx* ctx, const StrIn& in) {
+    SSS_TRY(impl_check_input(ctx, in));
+    return sss_sync(ctx);
+}
+
 static sss_params resolve_params(const sss_params* p) {
     sss_params r;
     sss_params_default(&r);
@@ -250,10 +262,26 @@ static sss_params resolve_params(const sss_params* p) {
 
 extern "C" {
 
-size_t sss_workspace_bytes(uint32_t n, uint32_t p, const sss_params* params) {
+// Work memory of the whole path: the runs, LCPs and approx of the partitions
+// followed by the largest stage scratch (stages run one after the other).
+static size_t need_pipeline(uint32_t n, uint64_t total_len, uint32_t p, const sss_params& prm) {
+    size_t stage = need_local_sort(n, p, prm);
+    if (p > 1) {
+        stage = std::max(stage, need_dist_prefix(n));
+        stage = std::max(stage, need_merge(n, p, prm.v, total_len));
+    }
+    Arena ar;
+    ar.take<uint32_t>(n);
+    ar.take<uint32_t>(n);
+    ar.take<uint32_t>(n);
+    ar.take<char>(stage);
+    return ar.off + 256;
+}
+
+size_t sss_workspace_bytes(uint32_t n, uint64_t total_len, uint32_t p, const sss_params* params) {
     sss_params prm = resolve_params(params);
     if (p == 0) p = 1;
-    return need_local_sort(n, p, prm);
+    return need_pipeline(n, total_len, p, prm);
 }
 
 sss_status sss_local_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,
@@ -265,10 +293,7 @@ sss_status sss_local_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, 
     cudaSetDevice(ctx->device);
     sss_params prm = resolve_params(params);
     StrIn in{chars, n_chars, offsets, lengths, n};
-    if (prm.flags & SSS_FLAG_CHECKED) {
-        SSS_TRY(impl_check_input(ctx, in));
-        SSS_TRY(sss_sync(ctx));
-    }
+    if (prm.flags & SSS_FLAG_CHECKED) SSS_TRY(checked_input(ctx, in));
     char* ws;
     SSS_TRY(sss_workspace(ctx, need_local_sort(n, p, prm), &ws));
     Arena ar{ws, 0, 0};
@@ -284,20 +309,59 @@ sss_status sss_dist(sss_ctx* ctx, const uint32_t* lengths, uint32_t n, const uin
     return impl_dist(ctx, lengths, n, perm, lcp, out_dist);
 }
 
-sss_status sss_dist_prefix(sss_ctx* ctx, const uint8_t*, uint64_t, const uint64_t*, const uint32_t*, uint32_t,
-                           const uint32_t*, const uint32_t*, uint32_t, const sss_params*, uint32_t*) {
-    return sss_fail(ctx, SSS_ERR_UNIMPLEMENTED, "sss_dist_prefix not built yet");
+sss_status sss_dist_prefix(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,
+                           const uint32_t* lengths, uint32_t n, const uint32_t* run_perm, const uint32_t* run_lcp,
+                           uint32_t p, const sss_params* params, uint32_t* out_approx) {
+    SSS_TRY(check_common(ctx, chars, offsets, lengths, n, p));
+    if ((run_perm == nullptr) != (run_lcp == nullptr))
+        return sss_fail(ctx, SSS_ERR_INVALID_ARG, "run_perm and run_lcp must both be given or both be NULL");
+    if (n > 0 && !out_approx) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "out_approx must be non-NULL");
+    if (n == 0) return SSS_OK;
+    cudaSetDevice(ctx->device);
+    sss_params prm = resolve_params(params);
+    StrIn in{chars, n_chars, offsets, lengths, n};
+    if (prm.flags & SSS_FLAG_CHECKED) SSS_TRY(checked_input(ctx, in));
+    char* ws;
+    SSS_TRY(sss_workspace(ctx, need_dist_prefix(n), &ws));
+    Arena ar{ws, 0, 0};
+    const uint32_t* rp = (prm.flags & SSS_FLAG_NO_LOCAL_LCP_SKIP) ? nullptr : run_perm;
+    const uint32_t* rl = (prm.flags & SSS_FLAG_NO_LOCAL_LCP_SKIP) ? nullptr : run_lcp;
+    return impl_dist_prefix(ctx, ar, in, rp, rl, p, prm, out_approx);
 }
 
-sss_status sss_partition(sss_ctx* ctx, const uint8_t*, uint64_t, const uint64_t*, const uint32_t*, const uint32_t*,
-                         const uint32_t*, uint32_t, uint32_t, const sss_params*, uint32_t*, uint32_t*) {
-    return sss_fail(ctx, SSS_ERR_UNIMPLEMENTED, "sss_partition not built yet");
+sss_status sss_partition(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,
+                         const uint32_t* lengths, const uint32_t* trunc, const uint32_t* run_perm, uint32_t n,
+                         uint32_t p, const sss_params* params, uint32_t* out_splitters, uint32_t* out_bounds) {
+    SSS_TRY(check_common(ctx, chars, offsets, lengths, n, p));
+    if (!run_perm && n > 0) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "run_perm must be non-NULL");
+    if (!out_bounds || (p > 1 && !out_splitters))
+        return sss_fail(ctx, SSS_ERR_INVALID_ARG, "outputs must be non-NULL");
+    cudaSetDevice(ctx->device);
+    sss_params prm = resolve_params(params);
+    StrIn in{chars, n_chars, offsets, lengths, n};
+    char* ws;
+    SSS_TRY(sss_workspace(ctx, need_partition(n, p, prm.v), &ws));
+    Arena ar{ws, 0, 0};
+    return impl_partition(ctx, ar, in, trunc, run_perm, p, prm.v, out_splitters, out_bounds);
 }
 
-sss_status sss_lcp_merge(sss_ctx* ctx, const uint8_t*, uint64_t, const uint64_t*, const uint32_t*, const uint32_t*,
-                         const uint32_t*, const uint32_t*, uint32_t, uint32_t, const sss_params*, uint32_t*,
-                         uint32_t*) {
-    return sss_fail(ctx, SSS_ERR_UNIMPLEMENTED, "sss_lcp_merge not built yet");
+sss_status sss_lcp_merge(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,
+                         const uint32_t* lengths, const uint32_t* trunc, const uint32_t* run_perm,
+                         const uint32_t* run_lcp, uint32_t n, uint32_t p, const sss_params* params,
+                         uint32_t* out_perm, uint32_t* out_lcp) {
+    SSS_TRY(check_common(ctx, chars, offsets, lengths, n, p));
+    if (n > 0 && (!run_perm || !run_lcp || !out_perm || !out_lcp))
+        return sss_fail(ctx, SSS_ERR_INVALID_ARG, "NULL pointer");
+    if (n == 0) return SSS_OK;
+    cudaSetDevice(ctx->device);
+    sss_params prm = resolve_params(params);
+    StrIn in{chars, n_chars, offsets, lengths, n};
+    uint64_t tot = 0;
+    SSS_TRY(impl_sum_tlen(ctx, in, trunc, &tot));
+    size_t need = need_merge(n, p, prm.v, tot);
+    char* ws;
+    SSS_TRY(sss_workspace(ctx, need, &ws));
+    return impl_merge(ctx, ws, need, in, trunc, run_perm, run_lcp, p, prm.v, tot, out_perm, out_lcp);
 }
 
 sss_status sss_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,
@@ -306,11 +370,47 @@ sss_status sss_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const 
     SSS_TRY(check_common(ctx, chars, offsets, lengths, n, p));
     if (n > 0 && (!out_perm || !out_lcp)) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "outputs must be non-NULL");
     if (n == 0) return SSS_OK;
-    if (p > 1) return sss_fail(ctx, SSS_ERR_UNIMPLEMENTED, "p > 1 not built yet");
-    SSS_TRY(sss_local_sort(ctx, chars, n_chars, offsets, lengths, n, 1, params, out_perm, out_lcp));
+    cudaSetDevice(ctx->device);
+    sss_params prm = resolve_params(params);
+    StrIn in{chars, n_chars, offsets, lengths, n};
+    if (prm.flags & SSS_FLAG_CHECKED) SSS_TRY(checked_input(ctx, in));
+    if (p == 1) {
+        char* ws;
+        SSS_TRY(sss_workspace(ctx, need_local_sort(n, 1, prm), &ws));
+        Arena ar{ws, 0, 0};
+        SSS_TRY(impl_local_sort(ctx, ar, in, 1, prm, out_perm, out_lcp));
+        if (out_dist) SSS_TRY(impl_dist(ctx, lengths, n, out_perm, out_lcp, out_dist));
+        if (out_approx)
+            SSS_CUDA(cudaMemcpyAsync(out_approx, lengths, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        return SSS_OK;
+    }
+    uint64_t total_len = 0;
+    SSS_TRY(impl_sum_tlen(ctx, in, nullptr, &total_len));
+    size_t need = need_pipeline(n, total_len, p, prm);
+    char* ws;
+    SSS_TRY(sss_workspace(ctx, need, &ws));
+    Arena ar{ws, need, 0};
+    uint32_t* run_perm = ar.take<uint32_t>(n);
+    uint32_t* run_lcp = ar.take<uint32_t>(n);
+    uint32_t* approx = ar.take<uint32_t>(n);
+    size_t stage_off = (ar.off + 255) & ~size_t(255);
+    char* stage = ws + stage_off;
+    size_t stage_bytes = need - stage_off;
+    {
+        Arena sa{stage, stage_bytes, 0};
+        SSS_TRY(impl_local_sort(ctx, sa, in, p, prm, run_perm, run_lcp));
+    }
+    const uint32_t* trunc = nullptr;
+    if (!(prm.flags & SSS_FLAG_MS)) {
+        Arena sa{stage, stage_bytes, 0};
+        SSS_TRY(impl_dist_prefix(ctx, sa, in, run_perm, run_lcp, p, prm, approx));
+        trunc = approx;
+    }
+    SSS_TRY(impl_merge(ctx, stage, stage_bytes, in, trunc, run_perm, run_lcp, p, prm.v, total_len, out_perm, out_lcp));
     if (out_dist) SSS_TRY(impl_dist(ctx, lengths, n, out_perm, out_lcp, out_dist));
-    if (out_approx) SSS_CUDA(cudaMemcpyAsync(out_approx, lengths, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice,
-                                             ctx->stream));
+    if (out_approx)
+        SSS_CUDA(cudaMemcpyAsync(out_approx, trunc ? trunc : lengths, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
     return SSS_OK;
 }
 

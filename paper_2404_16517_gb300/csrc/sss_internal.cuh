@@ -69,6 +69,8 @@ struct sss_ctx {
     size_t h_pin_bytes = 0;
     // sticky device error word
     unsigned* d_err = nullptr;
+    // small device scratch for counters and reductions (never inside the workspace)
+    unsigned long long* d_small = nullptr;
     std::string last_error;
     // instrumentation
     KStat stats[SSS_MAX_KERNELS];
@@ -131,7 +133,7 @@ sss_status sss_launch(sss_ctx* ctx, const char* name, void (*kernel)(KArgs...), 
     return SSS_OK;
 }
 
-inline uint32_t part_lo(uint32_t n, uint32_t p, uint32_t i) {
+__host__ __device__ inline uint32_t part_lo(uint32_t n, uint32_t p, uint32_t i) {
     return (uint32_t)(((uint64_t)i * n) / p);
 }
 
@@ -148,6 +150,19 @@ struct StrIn {
 sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p, const sss_params& prm,
                            uint32_t* perm, uint32_t* lcp);
 size_t need_local_sort(uint32_t n, uint32_t p, const sss_params& prm);
+
+size_t need_dist_prefix(uint32_t n);
+sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& in, const uint32_t* run_perm,
+                            const uint32_t* run_lcp, uint32_t p, const sss_params& prm, uint32_t* approx);
+
+size_t need_partition(uint32_t n, uint32_t p, uint32_t v);
+sss_status impl_partition(sss_ctx* ctx, Arena& ar, const StrIn& in, const uint32_t* trunc, const uint32_t* run_perm,
+                          uint32_t p, uint32_t v, uint32_t* out_spl, uint32_t* out_bounds);
+size_t need_merge(uint32_t n, uint32_t p, uint32_t v, uint64_t nrecchars);
+sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, const uint32_t* trunc,
+                      const uint32_t* run_perm, const uint32_t* run_lcp, uint32_t p, uint32_t v,
+                      uint64_t nrecchars, uint32_t* out_perm, uint32_t* out_lcp);
+sss_status impl_sum_tlen(sss_ctx* ctx, const StrIn& in, const uint32_t* trunc, uint64_t* out);
 
 sss_status impl_dist(sss_ctx* ctx, const uint32_t* lens, uint32_t n, const uint32_t* perm, const uint32_t* lcp,
                      uint32_t* dist);

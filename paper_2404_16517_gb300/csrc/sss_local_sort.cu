@@ -21,6 +21,7 @@
 
 #include "sss_device.cuh"
 #include "sss_internal.cuh"
+#include "sss_sampleparts.cuh"
 
 namespace {
 
@@ -30,10 +31,6 @@ constexpr uint32_t INF32 = 0xFFFFFFFFu;
 // size classes
 constexpr int TINY_T = 64, TINY_CAP = 64;       // segments of 2..64 strings
 constexpr int MED_T = 256, MED_CAP = 2048;      // segments of 65..2048 strings
-constexpr int LG_TILE = 1024, LG_T = 256;       // large path tile / threads
-constexpr int LG_OVS = 16;                      // samples per range bucket
-constexpr int LG_BMAX = 256;                    // max range buckets per segment
-constexpr int LG_NBMAX = 2 * LG_BMAX - 1;       // range + equality buckets
 constexpr int BK_T = 512, BK_CAP = 4096;        // bucket sort CTA
 constexpr int LG_TARGET = BK_CAP / 2;           // target range-bucket size
 
@@ -210,23 +207,6 @@ constexpr size_t finish_smem(int cap) { return (size_t)cap * (8 + 8 + 4 * 6); }
 
 // ---------------------------------------------------------------------------
 // Large path.
-struct LgSegInfo {
-    Seg seg;            // start, size, depth
-    uint32_t tiles;     // number of tiles
-    uint32_t tile0;     // first tile index
-    uint32_t nb;        // range buckets B (splitters B-1, buckets 2B-1)
-    uint32_t hist_base; // offset into hist (bucket-major: b*tiles + t)
-    uint32_t bst_base;  // offset into bucket starts (2B entries)
-    uint32_t pad[3];
-};
-
-struct LgTile {
-    uint32_t s;      // segment index
-    uint32_t begin;  // absolute first position
-    uint32_t end;    // absolute end position
-    uint32_t t;      // tile index within segment
-};
-
 __global__ void __launch_bounds__(LG_T) k_lg_ext(const LgTile* __restrict__ tiles, const LgSegInfo* __restrict__ info,
                                                  const uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
                                                  const uint32_t* __restrict__ lens, const uint32_t* __restrict__ perm,
@@ -256,133 +236,6 @@ __global__ void __launch_bounds__(LG_T) k_lg_keys(const LgTile* __restrict__ til
     for (uint32_t q = tl.begin + threadIdx.x; q < tl.end; q += LG_T) {
         uint32_t e = perm[q];
         K[q] = load_word_be(chars + offs[e], lens[e], d);
-    }
-}
-
-// One CTA per segment: evenly spaced samples, sorted; splitter b = sample (b+1)*OVS-1.
-__global__ void __launch_bounds__(512) k_lg_samples(const LgSegInfo* __restrict__ info, const uint64_t* __restrict__ K,
-                                                    uint64_t* __restrict__ spl) {
-    __shared__ uint64_t sh[LG_BMAX * LG_OVS];
-    LgSegInfo si = info[blockIdx.x];
-    uint32_t S = si.nb * LG_OVS;
-    for (uint32_t i = threadIdx.x; i < S; i += 512) {
-        uint64_t q = si.seg.start + ((2 * (uint64_t)i + 1) * si.seg.size) / (2 * (uint64_t)S);
-        sh[i] = K[q];
-    }
-    __syncthreads();
-    bitonic_sort64<512>(sh, S);
-    for (uint32_t b = threadIdx.x; b + 1 < si.nb; b += 512)
-        spl[(size_t)blockIdx.x * (LG_BMAX - 1) + b] = sh[(b + 1) * LG_OVS - 1];
-}
-
-// first splitter >= k (lower bound) among nsp sorted splitters
-__device__ __forceinline__ uint32_t lower_bound64(const uint64_t* s, uint32_t nsp, uint64_t k) {
-    uint32_t lo = 0, hi = nsp;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (s[mid] < k) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-__global__ void __launch_bounds__(LG_T) k_lg_classify(const LgTile* __restrict__ tiles,
-                                                      const LgSegInfo* __restrict__ info,
-                                                      const uint64_t* __restrict__ K, const uint64_t* __restrict__ spl,
-                                                      uint32_t* __restrict__ hist, uint32_t* __restrict__ rankinfo) {
-    constexpr int W = LG_T / 32;
-    constexpr int PER_WARP = LG_TILE / W;  // contiguous positions per warp
-    __shared__ uint64_t ssp[LG_BMAX];
-    __shared__ uint32_t cnt[W][LG_NBMAX];
-    LgTile tl = tiles[blockIdx.x];
-    LgSegInfo si = info[tl.s];
-    uint32_t nsp = si.nb - 1, nbk = 2 * si.nb - 1;
-    for (uint32_t i = threadIdx.x; i < nsp; i += LG_T) ssp[i] = spl[(size_t)tl.s * (LG_BMAX - 1) + i];
-    for (uint32_t i = threadIdx.x; i < (uint32_t)(W * LG_NBMAX); i += LG_T) (&cnt[0][0])[i] = 0;
-    __syncthreads();
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t lt = (1u << lane) - 1u;
-    uint32_t myb[PER_WARP / 32], myr[PER_WARP / 32];
-#pragma unroll
-    for (int it = 0; it < PER_WARP / 32; ++it) {
-        uint32_t q = tl.begin + w * PER_WARP + it * 32 + lane;
-        bool valid = q < tl.end;
-        uint32_t b = 0xFFFFu;
-        if (valid) {
-            uint64_t k = K[q];
-            uint32_t lb = lower_bound64(ssp, nsp, k);
-            b = 2 * lb + ((lb < nsp && ssp[lb] == k) ? 1u : 0u);
-        }
-        uint32_t peers = __match_any_sync(SSS_FULL, b);
-        uint32_t leader = __ffs(peers) - 1;
-        uint32_t base = 0;
-        if (valid && lane == (int)leader) {
-            base = cnt[w][b];
-            cnt[w][b] = base + __popc(peers);
-        }
-        base = __shfl_sync(SSS_FULL, base, leader);
-        myb[it] = b;
-        myr[it] = base + __popc(peers & lt);
-    }
-    __syncthreads();
-    // exclusive prefix over warps for every bucket; tile total into hist
-    for (uint32_t b = threadIdx.x; b < nbk; b += LG_T) {
-        uint32_t run = 0;
-#pragma unroll
-        for (int ww = 0; ww < W; ++ww) {
-            uint32_t t = cnt[ww][b];
-            cnt[ww][b] = run;
-            run += t;
-        }
-        hist[si.hist_base + b * si.tiles + tl.t] = run;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int it = 0; it < PER_WARP / 32; ++it) {
-        uint32_t q = tl.begin + w * PER_WARP + it * 32 + lane;
-        if (q < tl.end) rankinfo[q] = (myb[it] << 16) | (cnt[w][myb[it]] + myr[it]);
-    }
-}
-
-// Per segment: prefix of every bucket over the tiles, then bucket starts.
-__global__ void __launch_bounds__(512) k_lg_offsets(const LgSegInfo* __restrict__ info, uint32_t* __restrict__ hist,
-                                                    uint32_t* __restrict__ bst) {
-    __shared__ uint32_t sh_warp[32];
-    LgSegInfo si = info[blockIdx.x];
-    uint32_t nbk = 2 * si.nb - 1;
-    uint32_t b = threadIdx.x;
-    uint32_t tot = 0;
-    if (b < nbk) {
-        uint32_t* h = hist + si.hist_base + b * si.tiles;
-        for (uint32_t t = 0; t < si.tiles; ++t) {
-            uint32_t v = h[t];
-            h[t] = tot;
-            tot += v;
-        }
-    }
-    uint32_t total;
-    uint32_t ex = BlockScan<512>::exclusive_sum(tot, sh_warp, &total);
-    if (b < nbk) bst[si.bst_base + b] = si.seg.start + ex;
-    if (b == 0) bst[si.bst_base + nbk] = si.seg.start + si.seg.size;
-}
-
-__global__ void __launch_bounds__(LG_T) k_lg_scatter(const LgTile* __restrict__ tiles, const LgSegInfo* __restrict__ info,
-                                                     const uint32_t* __restrict__ hist, const uint32_t* __restrict__ bst,
-                                                     const uint32_t* __restrict__ rankinfo,
-                                                     const uint64_t* __restrict__ K, const uint32_t* __restrict__ perm,
-                                                     uint64_t* __restrict__ tK, uint32_t* __restrict__ tV,
-                                                     unsigned* err) {
-    LgTile tl = tiles[blockIdx.x];
-    LgSegInfo si = info[tl.s];
-    for (uint32_t q = tl.begin + threadIdx.x; q < tl.end; q += LG_T) {
-        uint32_t ri = rankinfo[q];
-        uint32_t b = ri >> 16;
-        uint32_t dst = bst[si.bst_base + b] + hist[si.hist_base + b * si.tiles + tl.t] + (ri & 0xFFFFu);
-        if (dst < si.seg.start || dst >= si.seg.start + si.seg.size) {
-            atomicOr(err, ERRBIT_OVERFLOW);
-            continue;
-        }
-        tK[dst] = K[q];
-        tV[dst] = perm[q];
     }
 }
 
@@ -520,40 +373,28 @@ struct LsBufs {
     uint64_t* K;
     uint64_t* tK;
     uint32_t* tV;
-    uint32_t* rankinfo;
     Seg* tiny;
     Seg* med;
     Seg* large;
     uint32_t* cnt;
     uint32_t* segmin;
-    uint64_t* spl;
-    uint32_t* hist;
-    uint32_t* bst;
-    LgSegInfo* info;
-    LgTile* tiles;
-    uint32_t cap_tiny, cap_med, cap_large, cap_tiles, cap_hist;
+    SpBufs sp;
+    uint32_t cap_tiny, cap_med, cap_large;
 };
 
 void carve_ls(Arena& ar, uint32_t n, uint32_t p, LsBufs& b) {
     b.cap_tiny = n / 2 + 2;
     b.cap_med = n / (TINY_CAP + 1) + 2;
     b.cap_large = n / (MED_CAP + 1) + p + 2;
-    b.cap_tiles = n / LG_TILE + b.cap_large + 2;
-    b.cap_hist = LG_NBMAX * b.cap_tiles;
     b.K = ar.take<uint64_t>(n);
     b.tK = ar.take<uint64_t>(n);
     b.tV = ar.take<uint32_t>(n);
-    b.rankinfo = ar.take<uint32_t>(n);
     b.tiny = ar.take<Seg>(b.cap_tiny);
     b.med = ar.take<Seg>(b.cap_med);
     b.large = ar.take<Seg>(b.cap_large);
     b.cnt = ar.take<uint32_t>(4);
     b.segmin = ar.take<uint32_t>(b.cap_large);
-    b.spl = ar.take<uint64_t>((size_t)b.cap_large * (LG_BMAX - 1));
-    b.hist = ar.take<uint32_t>(b.cap_hist);
-    b.bst = ar.take<uint32_t>((size_t)b.cap_large * (LG_NBMAX + 1));
-    b.info = ar.take<LgSegInfo>(b.cap_large);
-    b.tiles = ar.take<LgTile>(b.cap_tiles);
+    carve_sp(ar, n, b.cap_large, b.sp);
 }
 
 sss_status run_finishers(sss_ctx* ctx, const LsBufs& B, uint32_t ntiny, uint32_t nmed, const StrIn& in,
@@ -609,8 +450,8 @@ sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p,
         else large.push_back(s);
     }
     // pinned staging: segment info + tiles + counters
-    size_t pin_bytes = sizeof(uint32_t) * 4 + sizeof(Seg) * (size_t)(B.cap_large + B.cap_med + B.cap_tiny) +
-                       sizeof(LgSegInfo) * B.cap_large + sizeof(LgTile) * B.cap_tiles + 1024;
+    size_t pin_bytes = sizeof(uint32_t) * 16 + sizeof(Seg) * (size_t)(B.cap_large + B.cap_med + B.cap_tiny) +
+                       sizeof(LgSegInfo) * B.cap_large + sizeof(LgTile) * B.sp.cap_tiles + 1024;
     void* pin;
     SSS_TRY(sss_pinned(ctx, pin_bytes, &pin));
     uint32_t* h_cnt = reinterpret_cast<uint32_t*>(pin);
@@ -634,55 +475,28 @@ sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p,
     while (!large.empty()) {
         if (++rounds > 100000u) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: round limit exceeded");
         uint32_t ns = (uint32_t)large.size();
-        uint32_t ntiles = 0, hist_off = 0;
-        for (uint32_t s = 0; s < ns; ++s) {
-            const Seg& sg = large[s];
-            uint32_t tiles = (sg.size + LG_TILE - 1) / LG_TILE;
-            uint32_t nb = (sg.size + LG_TARGET - 1) / LG_TARGET;
-            nb = std::max(2u, std::min((uint32_t)LG_BMAX, nb));
-            LgSegInfo si{};
-            si.seg = sg;
-            si.tiles = tiles;
-            si.tile0 = ntiles;
-            si.nb = nb;
-            si.hist_base = hist_off;
-            si.bst_base = s * (LG_NBMAX + 1);
-            h_info[s] = si;
-            for (uint32_t t = 0; t < tiles; ++t) {
-                uint32_t b0 = sg.start + t * LG_TILE;
-                h_tiles[ntiles + t] = LgTile{s, b0, std::min(b0 + (uint32_t)LG_TILE, sg.start + sg.size), t};
-            }
-            ntiles += tiles;
-            hist_off += (2 * nb - 1) * tiles;
-        }
-        if (ntiles > B.cap_tiles || hist_off > B.cap_hist || ns > B.cap_large)
+        uint32_t ntiles = 0;
+        if (!plan_sp(large, LG_TARGET, B.sp, h_info, h_tiles, &ntiles))
             return sss_fail(ctx, SSS_ERR_CUDA, "local sort: internal capacity exceeded");
-        SSS_CUDA(cudaMemcpyAsync(B.info, h_info, sizeof(LgSegInfo) * ns, cudaMemcpyHostToDevice, ctx->stream));
-        SSS_CUDA(cudaMemcpyAsync(B.tiles, h_tiles, sizeof(LgTile) * ntiles, cudaMemcpyHostToDevice, ctx->stream));
+        SSS_CUDA(cudaMemcpyAsync(B.sp.info, h_info, sizeof(LgSegInfo) * ns, cudaMemcpyHostToDevice, ctx->stream));
+        SSS_CUDA(cudaMemcpyAsync(B.sp.tiles, h_tiles, sizeof(LgTile) * ntiles, cudaMemcpyHostToDevice,
+                                 ctx->stream));
         SSS_CUDA(cudaMemsetAsync(B.segmin, 0xFF, sizeof(uint32_t) * ns, ctx->stream));
         SSS_CUDA(cudaMemsetAsync(B.cnt, 0, sizeof(uint32_t) * 4, ctx->stream));
-        SSS_TRY(sss_launch(ctx, "ls_lg_ext", k_lg_ext, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.tiles,
-                           (const LgSegInfo*)B.info, in.chars, in.offs, in.lens, (const uint32_t*)perm, B.segmin));
-        SSS_TRY(sss_launch(ctx, "ls_lg_keys", k_lg_keys, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.tiles,
-                           (const LgSegInfo*)B.info, in.chars, in.offs, in.lens, (const uint32_t*)perm,
+        SSS_TRY(sss_launch(ctx, "ls_lg_ext", k_lg_ext, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.sp.tiles,
+                           (const LgSegInfo*)B.sp.info, in.chars, in.offs, in.lens, (const uint32_t*)perm,
+                           B.segmin));
+        SSS_TRY(sss_launch(ctx, "ls_lg_keys", k_lg_keys, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.sp.tiles,
+                           (const LgSegInfo*)B.sp.info, in.chars, in.offs, in.lens, (const uint32_t*)perm,
                            (const uint32_t*)B.segmin, B.K));
-        SSS_TRY(sss_launch(ctx, "ls_lg_samples", k_lg_samples, dim3(ns), dim3(512), 0, (const LgSegInfo*)B.info,
-                           (const uint64_t*)B.K, B.spl));
-        SSS_TRY(sss_launch(ctx, "ls_lg_classify", k_lg_classify, dim3(ntiles), dim3(LG_T), 0,
-                           (const LgTile*)B.tiles, (const LgSegInfo*)B.info, (const uint64_t*)B.K,
-                           (const uint64_t*)B.spl, B.hist, B.rankinfo));
-        SSS_TRY(sss_launch(ctx, "ls_lg_offsets", k_lg_offsets, dim3(ns), dim3(512), 0, (const LgSegInfo*)B.info,
-                           B.hist, B.bst));
-        SSS_TRY(sss_launch(ctx, "ls_lg_scatter", k_lg_scatter, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.tiles,
-                           (const LgSegInfo*)B.info, (const uint32_t*)B.hist, (const uint32_t*)B.bst,
-                           (const uint32_t*)B.rankinfo, (const uint64_t*)B.K, (const uint32_t*)perm, B.tK, B.tV,
-                           ctx->d_err));
+        SSS_TRY(launch_sp(ctx, B.sp, ns, ntiles, B.K, perm, B.tK, B.tV, "ls_lg_samples", "ls_lg_classify",
+                          "ls_lg_offsets", "ls_lg_scatter"));
         SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets, dim3(LG_NBMAX, ns), dim3(BK_T),
-                           (size_t)BK_CAP * (8 + 8 + 4 + 4), (const LgSegInfo*)B.info, (const uint32_t*)B.bst,
+                           (size_t)BK_CAP * (8 + 8 + 4 + 4), (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst,
                            (const uint32_t*)B.segmin, (const uint64_t*)B.tK, (const uint32_t*)B.tV, in.lens, B.K, perm,
                            lcp, L, ctx->d_err));
-        SSS_TRY(sss_launch(ctx, "ls_lg_seams", k_lg_seams, dim3(ns), dim3(512), 0, (const LgSegInfo*)B.info,
-                           (const uint32_t*)B.bst, (const uint32_t*)B.segmin, (const uint64_t*)B.K, lcp));
+        SSS_TRY(sss_launch(ctx, "ls_lg_seams", k_lg_seams, dim3(ns), dim3(512), 0, (const LgSegInfo*)B.sp.info,
+                           (const uint32_t*)B.sp.bst, (const uint32_t*)B.segmin, (const uint64_t*)B.K, lcp));
         SSS_CUDA(cudaMemcpyAsync(h_cnt, B.cnt, sizeof(uint32_t) * 3, cudaMemcpyDeviceToHost, ctx->stream));
         SSS_CUDA(cudaMemcpyAsync(h_cnt + 3, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
         SSS_CUDA(cudaStreamSynchronize(ctx->stream));

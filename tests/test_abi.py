@@ -45,7 +45,7 @@ def test_status_strings_and_defaults():
     assert h.sss_status_string(0) == b"ok"
     p = sss.params()
     assert p.v == 2 and p.kmax == sss.SSS_KMAX_AUTO and p.kmin == 0
-    assert sss.workspace_bytes(1 << 20, 16) > (1 << 20) * 8
+    assert sss.workspace_bytes(1 << 20, 500 << 20, 16) > (1 << 20) * 8
 
 
 def test_null_context_is_rejected():
