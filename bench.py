@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark of the string sorter on one or more GB300s (one replica per GPU).
+
+Workload (default): the full prefix-doubling merge sort of 4,194,304 strings of
+500 characters over A-Z in p = 16 partitions (chars 0-241 from one of 64
+seeded templates, the rest uniform; D/N about 0.5), generated on the device.
+A step is one sss_sort call over the whole set (local sort, prefix doubling,
+partition, LCP-compressed exchange, LCP merge, plus dist).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank sorts its own copy of
+the workload (replicas, weak scaling); value = all ranks' characters / the
+slowest rank's time.  ``--impl reference`` times the plain-C oracle on a
+bounded sample of the same workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sorted chars/s and strings/s on 1 GB300 (% of HBM roofline); p50/p99 request latency"
+WORKLOAD = "pdms_4194304x500_AZ_T64_shared242_p16"
+N_FULL, LEN, P = 4194304, 500, 16
+CPU_SAMPLE = 1 << 19  # strings timed on the oracle
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def lib_source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2404_16517_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        with open(os.path.join(d, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+class Clocks:
+    """Sample SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, ws, rank):
+    """The oracle (plain C, single thread) on a bounded sample of the workload."""
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import datagen
+    import oracle
+
+    n = args.cpu_sample
+    try:
+        import torch
+        import datagen.cuda as dgc
+        if torch.cuda.is_available():
+            c, o, l = dgc.config2(N_FULL, 0, n)
+            ss = datagen.StringSet(c.cpu().numpy(), o.cpu().numpy().view(np.uint64), l.cpu().numpy().view(np.uint32))
+        else:
+            raise RuntimeError
+    except Exception:
+        ss = datagen.config2(N_FULL, 0, n)
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.pdms(ss, P, 2, 0, 9, 0)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+        if s == 0 and args.steps + args.warmup > 1 and dt * (args.steps + args.warmup) > 240:
+            # keep the whole reference run within a few minutes
+            args.steps = max(1, int(240 // dt) - args.warmup)
+    t = statistics.median(times)
+    chars = n * LEN
+    value = chars / t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "chars/s", "n_gpus": ws,
+           "steps": len(times), "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+           "strings_per_s": n / t,
+           "config": {"workload": WORKLOAD, "sample_strings": n, "partitions": P},
+           "cpu_baseline": {"value": value, "unit": "chars/s", "cores": 1, "kind": "oracle",
+                            "sample": f"first {n} of the {N_FULL} strings (same generator), p={P}, one "
+                                      f"single-threaded oracle PDMS pass per step"},
+           "e2e": {"value": value, "unit": "chars/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def cpu_baseline(n: int):
+    import numpy as np
+
+    import datagen
+    import datagen.cuda as dgc
+    import oracle
+    c, o, l = dgc.config2(N_FULL, 0, n)
+    ss = datagen.StringSet(c.cpu().numpy(), o.cpu().numpy().view(np.uint64), l.cpu().numpy().view(np.uint32))
+    t0 = time.perf_counter()
+    oracle.pdms(ss, P, 2, 0, 9, 0)
+    dt = time.perf_counter() - t0
+    return {"value": n * LEN / dt, "unit": "chars/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} of the {N_FULL} strings (same generator), p={P}, single-threaded oracle PDMS, "
+                      f"{dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_FULL)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--breakdown", action="store_true", help="per-kernel times to stderr")
+    ap.add_argument("--merge-ms", type=int, default=0, help="merge segment spacing (0 = library default)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import numpy as np
+    import torch
+
+    import datagen.cuda as dgc
+    import paper_2404_16517_gb300 as sss
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    n = args.n
+    chars, offs, lens = dgc.config2(n, 0, n)
+    N = n * LEN
+    ctx = sss.context(local)
+    prm = sss.params(merge_ms=args.merge_ms)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp = torch.empty(n, dtype=torch.int32, device=dev)
+    dist_t = torch.empty(n, dtype=torch.int32, device=dev)
+    approx = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def step():
+        sss.sss_sort(chars, offs, lens, P, prm, perm, lcp, out_dist=dist_t, out_approx=approx, ctx=ctx)
+
+    # warm-up; the second one with every kernel timed to find the dominant kernel
+    # (the first pays for lazy module loading)
+    step()
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    ctx.set_timing(True, "")
+    step()
+    torch.cuda.synchronize()
+    stats_all = ctx.kernel_stats()
+    ctx.set_timing(False)
+    for _ in range(args.warmup - 2):
+        step()
+    torch.cuda.synchronize()
+    dom = max(stats_all.items(), key=lambda kv: kv[1]["total_ms"])[0]
+    D = int(dist_t.to(torch.int64).sum().item())
+    Dapprox = int(approx.to(torch.int64).sum().item())
+
+    # timed region: events on the context stream, the dominant kernel timed too
+    ctx.reset_stats()
+    ctx.set_timing(True, dom)
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    stats = ctx.kernel_stats()
+    ctx.set_timing(False)
+    launches = sum(v["launches"] for v in stats.values())
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = N * ws / (ms_step / 1e3)
+
+    # roofline of the dominant kernel
+    hbm, peak_kind = peaks()
+    dstat = stats.get(dom, {"launches": 0, "total_ms": 0.0, "timed": 0})
+    avg_ms = dstat["total_ms"] / max(1, dstat["timed"])
+    algo = algorithmic_bytes(dom, n, N, D, Dapprox, dstat["launches"] / max(1, args.steps))
+    achieved = algo / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+    traffic = known_traffic(dom)
+
+    # end to end: host buffers, copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        h_chars = torch.empty(chars.numel(), dtype=torch.uint8, pin_memory=True)
+        h_chars.copy_(chars)
+        h_offs = offs.cpu().pin_memory()
+        h_lens = lens.cpu().pin_memory()
+        h_perm = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        h_lcp = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        d_chars = torch.empty_like(chars)
+        d_offs = torch.empty_like(offs)
+        d_lens = torch.empty_like(lens)
+
+        def e2e_step():
+            d_chars.copy_(h_chars, non_blocking=True)
+            d_offs.copy_(h_offs, non_blocking=True)
+            d_lens.copy_(h_lens, non_blocking=True)
+            sss.sss_sort(d_chars, d_offs, d_lens, P, prm, perm, lcp, ctx=ctx)
+            h_perm.copy_(perm, non_blocking=True)
+            h_lcp.copy_(lcp, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(st)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        a1.record(st)
+        torch.cuda.synchronize()
+        ems = a0.elapsed_time(a1) / args.e2e_steps
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        ok = bool(np.array_equal(h_perm.numpy(), perm.cpu().numpy()))
+        e2e = {"value": N * ws / (ems / 1e3), "unit": "chars/s",
+               "h2d_bytes_per_step": int(chars.numel() + 8 * n + 4 * n), "d2h_bytes_per_step": int(8 * n),
+               "ms_per_step": ems, "result_read_back": ok}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        try:
+            cpu = cpu_baseline(args.cpu_sample)
+        except Exception as ex:  # reported, not fatal
+            cpu = {"error": str(ex)[:200]}
+
+    if args.breakdown and rank == 0:
+        tot = sum(v["total_ms"] for v in stats_all.values())
+        for k, v in sorted(stats_all.items(), key=lambda kv: -kv[1]["total_ms"]):
+            print(f"{k:18s} launches {v['launches']:5d}  {v['total_ms']:8.3f} ms  {100 * v['total_ms'] / tot:5.1f}%",
+                  file=sys.stderr)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "chars/s", "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+               "strings_per_s": n * ws / (ms_step / 1e3),
+               "config": {"workload": WORKLOAD, "strings": n, "chars": N, "partitions": P,
+                          "D_over_N": D / N, "approx_over_N": Dapprox / N,
+                          "l2": "inputs (2.1 GB of chars) larger than L2; no flush",
+                          "parallelism": f"replicas x{ws}"},
+               "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                            "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                            "algorithmic_bytes_per_launch": algo, "avg_launch_ms": avg_ms},
+               "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+               "kernel_ms_per_step": {k: v["total_ms"] for k, v in stats_all.items()}}
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def algorithmic_bytes(kernel: str, n: int, N: int, D: int, Dapprox: int, launches_per_step: float) -> float:
+    """Minimum bytes a launch of `kernel` must move on this workload."""
+    lps = max(launches_per_step, 1.0)
+    models = {
+        # local sort: every string's distinguishing prefix plus its view and outputs
+        "ls_lg_ext": (D + 16 * n) / lps,
+        "ls_finish_cta": (D + 24 * n) / lps,
+        "pd_hash": (Dapprox / 2 + 32 * n) / lps,
+        "d_merge": 32 * n / lps,
+        "d_search": 32 * n / lps,
+    }
+    return float(models.get(kernel, 24 * n / lps))
+
+
+def known_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the current library source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("source_hash") == lib_source_hash() and kernel in d.get("kernels", {}):
+            return d["kernels"][kernel]
+    except Exception:
+        pass
+    return None
+
+
+if __name__ == "__main__":
+    sys.exit(main())

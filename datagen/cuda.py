@@ -1,0 +1,66 @@
+"""Device-side generation of the template string sets of ``datagen`` (same
+definitions, produced directly in CUDA memory).  Built with nvcc into
+``datagen/libsssgen.so``; used by the benchmark for full-size workloads and
+checked against the numpy generator by the GPU tests."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import tempfile
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gen_cuda.cu")
+_SO = os.path.join(_HERE, "libsssgen.so")
+
+
+def build(force: bool = False) -> str:
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        from paper_2404_16517_gb300 import _build as b
+        fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
+        os.close(fd)
+        cmd = [b.nvcc(), *b.ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
+               "-o", tmp, _SRC, "-Xlinker", f"-rpath,{b.cuda_lib_dir()}", "-L", b.cuda_lib_dir()]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        f = _lib.sssgen_template_set
+        f.restype = C.c_int
+        f.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
+                      C.c_uint32, C.c_char_p, C.c_uint32, C.c_uint64, C.c_uint64, C.c_void_p]
+    return _lib
+
+
+def template_set(seed: int, n: int, length: int, n_templates: int, shared: int, alphabet: bytes,
+                 first: int = 0, count: int | None = None, device: str = "cuda"):
+    """Device tensors (chars u8, offs i64, lens i32) of strings first..first+count-1."""
+    import torch
+    if count is None:
+        count = n - first
+    chars = torch.empty(max(1, count * length), dtype=torch.uint8, device=device)
+    offs = torch.empty(count, dtype=torch.int64, device=device)
+    lens = torch.empty(count, dtype=torch.int32, device=device)
+    st = torch.cuda.current_stream(chars.device).cuda_stream
+    rc = lib().sssgen_template_set(C.c_void_p(chars.data_ptr()), C.c_void_p(offs.data_ptr()),
+                                   C.c_void_p(lens.data_ptr()), seed, n, length, n_templates, shared, alphabet,
+                                   len(alphabet), first, count, C.c_void_p(st))
+    if rc != 0:
+        raise RuntimeError(f"sssgen_template_set failed ({rc})")
+    return chars, offs, lens
+
+
+def config2(n: int = 4194304, first: int = 0, count: int | None = None, device: str = "cuda"):
+    return template_set(2, n, 500, 64, 242, b"ABCDEFGHIJKLMNOPQRSTUVWXYZ", first, count, device)
+
+
+def config1(device: str = "cuda"):
+    return template_set(1, 65536, 100, 4, 42, b"ABCDEFGHIJKLMNOPQRSTUVWXYZ", 0, None, device)

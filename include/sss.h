@@ -57,6 +57,9 @@ typedef enum sss_status {
                                   scan strings for 0x00 bytes; errors are sticky */
 #define SSS_FLAG_NO_LOCAL_LCP_SKIP 0x4u /* doubling: hash every active string
                                   instead of one per locally-equal prefix group */
+#define SSS_FLAG_DEDUPE_SORT 0x8u /* doubling: detect duplicate keys by sorting
+                                  them (bucketed shared-memory sorts) instead of
+                                  the exact hash table */
 
 typedef struct sss_params {
     uint32_t kmin;      /* first doubling round: prefix length 2^kmin (default 0) */
@@ -65,7 +68,8 @@ typedef struct sss_params {
     uint32_t flags;     /* SSS_FLAG_* */
     uint64_t hash_seed; /* seed of the prefix hash (default 0) */
     uint32_t cta_cap;   /* tuning: largest segment sorted inside one CTA (0 = default) */
-    uint32_t reserved[5];
+    uint32_t merge_ms;  /* tuning: merge segment spacing, a power of two 8..1024 (0 = default) */
+    uint32_t reserved[4];
 } sss_params;
 
 #define SSS_KMAX_AUTO 0xFFFFFFFFu

@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(_PKG, "libsss.so")
 SSS_FLAG_MS = 0x1
 SSS_FLAG_CHECKED = 0x2
 SSS_FLAG_NO_LOCAL_LCP_SKIP = 0x4
+SSS_FLAG_DEDUPE_SORT = 0x8
 SSS_KMAX_AUTO = 0xFFFFFFFF
 SSS_MAX_KERNELS = 64
 
@@ -40,7 +41,8 @@ class SssError(RuntimeError):
 
 class sss_params(C.Structure):
     _fields_ = [("kmin", C.c_uint32), ("kmax", C.c_uint32), ("v", C.c_uint32), ("flags", C.c_uint32),
-                ("hash_seed", C.c_uint64), ("cta_cap", C.c_uint32), ("reserved", C.c_uint32 * 5)]
+                ("hash_seed", C.c_uint64), ("cta_cap", C.c_uint32), ("merge_ms", C.c_uint32),
+                ("reserved", C.c_uint32 * 4)]
 
 
 class sss_kernel_stat(C.Structure):
@@ -101,10 +103,11 @@ def exported_symbols() -> list[str]:
 
 
 def params(kmin: int = 0, kmax: int = SSS_KMAX_AUTO, v: int = 2, flags: int = 0, hash_seed: int = 0,
-           cta_cap: int = 0) -> sss_params:
+           cta_cap: int = 0, merge_ms: int = 0) -> sss_params:
     p = sss_params()
     lib().sss_params_default(C.byref(p))
     p.kmin, p.kmax, p.v, p.flags, p.hash_seed, p.cta_cap = kmin, kmax, v, flags, hash_seed, cta_cap
+    p.merge_ms = merge_ms
     return p
 
 

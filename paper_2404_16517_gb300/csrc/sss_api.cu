@@ -38,7 +38,15 @@ sss_status sss_workspace(sss_ctx* ctx, size_t bytes, char** out) {
     return SSS_OK;
 }
 
+sss_status sss_upload(sss_ctx* ctx, void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return SSS_OK;
+    SSS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    SSS_CUDA(cudaEventRecord(ctx->pin_event, ctx->stream));
+    return SSS_OK;
+}
+
 sss_status sss_pinned(sss_ctx* ctx, size_t bytes, void** out) {
+    SSS_CUDA(cudaEventSynchronize(ctx->pin_event));
     if (bytes > ctx->h_pin_bytes) {
         if (ctx->h_pin) {
             cudaStreamSynchronize(ctx->stream);
@@ -146,6 +154,8 @@ sss_status sss_create(sss_ctx** out, int device, void* stream) {
         delete ctx;
         return SSS_ERR_OOM;
     }
+    cudaEventCreateWithFlags(&ctx->pin_event, cudaEventDisableTiming);
+    cudaEventRecord(ctx->pin_event, ctx->stream);
     cudaDeviceSynchronize();
     *out = ctx;
     return SSS_OK;
@@ -161,6 +171,7 @@ sss_status sss_destroy(sss_ctx* ctx) {
     if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->d_small) cudaFree(ctx->d_small);
+    if (ctx->pin_event) cudaEventDestroy(ctx->pin_event);
     delete ctx;
     return SSS_OK;
 }
@@ -361,7 +372,7 @@ sss_status sss_lcp_merge(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, c
     size_t need = need_merge(n, p, prm.v, tot);
     char* ws;
     SSS_TRY(sss_workspace(ctx, need, &ws));
-    return impl_merge(ctx, ws, need, in, trunc, run_perm, run_lcp, p, prm.v, tot, out_perm, out_lcp);
+    return impl_merge(ctx, ws, need, in, trunc, run_perm, run_lcp, p, prm.v, prm.merge_ms, tot, out_perm, out_lcp);
 }
 
 sss_status sss_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,
@@ -406,7 +417,8 @@ sss_status sss_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const 
         SSS_TRY(impl_dist_prefix(ctx, sa, in, run_perm, run_lcp, p, prm, approx));
         trunc = approx;
     }
-    SSS_TRY(impl_merge(ctx, stage, stage_bytes, in, trunc, run_perm, run_lcp, p, prm.v, total_len, out_perm, out_lcp));
+    SSS_TRY(impl_merge(ctx, stage, stage_bytes, in, trunc, run_perm, run_lcp, p, prm.v, prm.merge_ms, total_len,
+                       out_perm, out_lcp));
     if (out_dist) SSS_TRY(impl_dist(ctx, lengths, n, out_perm, out_lcp, out_dist));
     if (out_approx)
         SSS_CUDA(cudaMemcpyAsync(out_approx, trunc ? trunc : lengths, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice,

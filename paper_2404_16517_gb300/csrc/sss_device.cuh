@@ -28,6 +28,40 @@ __device__ __forceinline__ uint64_t load_word_be(const uint8_t* __restrict__ s, 
     return x;
 }
 
+// Consecutive big-endian 8-character words of s[d .. len), zero past len, with
+// one aligned 8-byte load per word.  Only aligned words that hold at least one
+// character of the string are loaded.
+struct WordStream {
+    const uint64_t* p;  // next aligned word to load
+    const uint8_t* end;
+    uint64_t cur;       // current aligned word, big-endian
+    uint32_t sh;        // misalignment in bits
+    uint32_t rem;       // characters left from the current position
+    __device__ __forceinline__ void init(const uint8_t* __restrict__ s, uint32_t len, uint32_t d) {
+        rem = len > d ? len - d : 0;
+        uintptr_t a = (uintptr_t)(s + d);
+        p = reinterpret_cast<const uint64_t*>(a & ~uintptr_t(7));
+        sh = (uint32_t)(a & 7) * 8;
+        end = s + len;
+        cur = rem ? bswap64(__ldg(p)) : 0;
+        ++p;
+    }
+    __device__ __forceinline__ uint64_t next() {
+        if (rem == 0) return 0;
+        uint64_t nx = (reinterpret_cast<const uint8_t*>(p) < end) ? bswap64(__ldg(p)) : 0;
+        ++p;
+        uint64_t w = sh ? ((cur << sh) | (nx >> (64 - sh))) : cur;
+        cur = nx;
+        if (rem < 8) {
+            w &= ~0ull << (8 * (8 - rem));
+            rem = 0;
+        } else {
+            rem -= 8;
+        }
+        return w;
+    }
+};
+
 // Number of equal characters of a[d..] and b[d..], capped at min(la, lb) - d.
 // Stops early (returning some value >= *runmin) once it has passed *runmin: the
 // caller only needs the minimum over a group, and runmin only decreases.
@@ -37,9 +71,12 @@ __device__ __forceinline__ uint32_t lcp_extend(const uint8_t* __restrict__ a, ui
     uint32_t m = la < lb ? la : lb;
     if (d >= m) return 0;
     uint32_t cap = m - d;
+    WordStream A, B;
+    A.init(a, la, d);
+    B.init(b, lb, d);
     for (uint32_t k = 0; k < cap; k += 8) {
-        if (runmin != nullptr && k >= *runmin) return k;
-        uint64_t x = load_word_be(a, la, d + k) ^ load_word_be(b, lb, d + k);
+        if (runmin != nullptr && (k & 63) == 0 && k > 0 && k >= *runmin) return k;
+        uint64_t x = A.next() ^ B.next();
         if (x) {
             uint32_t r = k + ((uint32_t)__clzll((long long)x) >> 3);
             return r < cap ? r : cap;

@@ -18,10 +18,21 @@
 // Horner's rule resumes from the stored h of the L/2-prefix, so a string that
 // was hashed in the previous round reads only characters [L/2, L).
 //
-// Duplicate detection: the (key, rep) pairs are bucketed by the key's top bits
-// (keys are uniform), each bucket is sorted in shared memory and equal
-// neighbours mark duplicates.  A bucket larger than shared memory (only with
-// many equal keys) is sorted in chunks and cross-checked by binary search.
+// Work per round: position q starts a group from the round whose L exceeds its
+// local LCP, k*(q) = bit length of lcp[q]; positions are bucketed once by k*
+// (and equal strings by the round that covers their length), so a round only
+// touches its reps, the positions that become reps next round and the equal
+// strings that end this round -- not all n positions.
+//
+// Duplicate detection, two exact variants:
+//  * sort (the appendix's route): the (key, rep) pairs are bucketed by the key's
+//    top bits (keys are uniform), each bucket is sorted in shared memory and
+//    equal neighbours mark duplicates; a bucket larger than shared memory (only
+//    with many equal keys) is sorted in chunks and cross-checked by binary search.
+//  * hash table (default; the single-shot filter of the appendix with the full
+//    64-bit key stored, so there are no false positives): keys are inserted into
+//    an open-addressing table of >= 2x slots with atomicCAS, a second insert of a
+//    key marks its slot, and each rep reads its slot's mark.
 #include <algorithm>
 #include <vector>
 
@@ -35,6 +46,7 @@ constexpr uint64_t GAMMA = 0x9E3779B97F4A7C15ull;
 constexpr uint32_t ACTIVE = 0xFFFFFFFFu;
 constexpr int DD_T = 512, DD_CAP = 4096;  // dedupe bucket CTA
 constexpr int HB_MAX = 13;                // max top bits for bucketing (8192 buckets)
+constexpr int KBINS = 34;                 // rounds 0..33 for the per-position round buckets
 
 __host__ __device__ __forceinline__ uint64_t smix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -94,20 +106,74 @@ __device__ __forceinline__ void warp_append(bool want, uint32_t q, uint32_t* lis
     if (want) list[base + __popc(m & ((1u << lane) - 1u))] = q;
 }
 
-__global__ void k_pd_init(PdIn in, const uint32_t* __restrict__ lens, uint32_t* __restrict__ apos,
-                          uint32_t* __restrict__ lpos, uint32_t* __restrict__ hlen, uint32_t* __restrict__ act,
-                          uint32_t* __restrict__ reps, uint32_t* __restrict__ cnt, uint64_t L0) {
-    uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-    bool valid = q < in.n;
-    bool rep = false;
-    if (valid) {
-        apos[q] = ACTIVE;
-        lpos[q] = lens[ord_of(in, q)];
-        hlen[q] = 0;
-        act[q] = q;
-        rep = group_start(in, q, L0);
+// round from which q starts a group (lcp[q] < 2^k), at least kmin
+__device__ __forceinline__ uint32_t kstar_of(const PdIn& in, uint32_t q, uint32_t kmin) {
+    uint32_t k = 0;
+    if (in.run_lcp && !is_part_start(q, in.n, in.p)) {
+        uint32_t l = in.run_lcp[q];
+        k = l ? 32u - (uint32_t)__clz(l) : 0u;
     }
-    warp_append(rep, q, reps, &cnt[0]);
+    return k > kmin ? k : kmin;
+}
+// first round whose L covers the whole string (2^k >= len), at least kmin
+__device__ __forceinline__ uint32_t klen_of(uint32_t len, uint32_t kmin) {
+    uint32_t k = len <= 1 ? 0u : 32u - (uint32_t)__clz(len - 1);
+    return k > kmin ? k : kmin;
+}
+
+// per-position state; counts of the round buckets
+__global__ void k_pd_init(PdIn in, const uint32_t* __restrict__ lens, uint32_t* __restrict__ apos,
+                          uint32_t* __restrict__ lpos, uint32_t* __restrict__ hlen, uint32_t* __restrict__ cnt_ks,
+                          uint32_t* __restrict__ cnt_kl, uint32_t kmin) {
+    __shared__ uint32_t hs[KBINS], hl[KBINS];
+    for (int i = threadIdx.x; i < KBINS; i += blockDim.x) hs[i] = hl[i] = 0;
+    __syncthreads();
+    uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < in.n) {
+        uint32_t len = lens[ord_of(in, q)];
+        apos[q] = ACTIVE;
+        lpos[q] = len;
+        hlen[q] = 0;
+        uint32_t ks = kstar_of(in, q, kmin), kl = klen_of(len, kmin);
+        atomicAdd(&hs[ks], 1u);
+        if (kl < ks) atomicAdd(&hl[kl], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < KBINS; i += blockDim.x) {
+        if (hs[i]) atomicAdd(&cnt_ks[i], hs[i]);
+        if (hl[i]) atomicAdd(&cnt_kl[i], hl[i]);
+    }
+}
+
+// scatter positions into their round buckets; one global reservation per
+// (CTA, bucket) keeps the cursors uncontended
+__global__ void __launch_bounds__(256) k_pd_lists(PdIn in, const uint32_t* __restrict__ lpos,
+                                                  uint32_t* __restrict__ cur_ks, uint32_t* __restrict__ cur_kl,
+                                                  uint32_t* __restrict__ list_ks, uint32_t* __restrict__ list_kl,
+                                                  uint32_t kmin) {
+    __shared__ uint32_t cs[KBINS], cl[KBINS], bs[KBINS], bl[KBINS];
+    for (int i = threadIdx.x; i < KBINS; i += blockDim.x) cs[i] = cl[i] = 0;
+    __syncthreads();
+    uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t ks = 0, kl = 0, rs = 0, rl = 0;
+    bool valid = q < in.n, inl = false;
+    if (valid) {
+        ks = kstar_of(in, q, kmin);
+        kl = klen_of(lpos[q], kmin);
+        inl = kl < ks;
+        rs = atomicAdd(&cs[ks], 1u);
+        if (inl) rl = atomicAdd(&cl[kl], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < KBINS; i += blockDim.x) {
+        bs[i] = cs[i] ? atomicAdd(&cur_ks[i], cs[i]) : 0u;
+        bl[i] = cl[i] ? atomicAdd(&cur_kl[i], cl[i]) : 0u;
+    }
+    __syncthreads();
+    if (valid) {
+        list_ks[bs[ks] + rs] = q;
+        if (inl) list_kl[bl[kl] + rl] = q;
+    }
 }
 
 // B1: keys of the reps (incremental Horner from the L/2-prefix when available)
@@ -128,10 +194,33 @@ __global__ void k_pd_hash(PdIn in, const uint32_t* __restrict__ reps, uint32_t n
         w0 = (uint32_t)(L / 16);
     }
     uint32_t nw = (le + 7) / 8;
-    for (uint32_t w = w0; w < nw; ++w) {
-        uint64_t x = load_word_be(str, le, 8 * w);
-        h = fold_limb(h, B, x >> 32);
-        h = fold_limb(h, B, x & 0xFFFFFFFFull);
+    if (w0 < nw) {
+        // words w0..nw-1 of the prefix, read as aligned 8-byte loads issued in
+        // batches of 8 (only words that hold a character of the prefix are loaded)
+        uintptr_t a0 = (uintptr_t)(str + 8 * w0);
+        const uint64_t* pw = reinterpret_cast<const uint64_t*>(a0 & ~uintptr_t(7));
+        const uint32_t sh = (uint32_t)(a0 & 7) * 8;
+        const uint8_t* end = str + le;
+        uint64_t prev = bswap64(__ldg(pw));
+        for (uint32_t w = w0; w < nw; w += 8) {
+            uint64_t buf[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint64_t* pi = pw + 1 + i;
+                buf[i] = reinterpret_cast<const uint8_t*>(pi) < end ? bswap64(__ldg(pi)) : 0ull;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (w + i >= nw) break;
+                uint64_t x = sh ? ((prev << sh) | (buf[i] >> (64 - sh))) : prev;
+                prev = buf[i];
+                uint32_t left = le - 8 * (w + i);
+                if (left < 8) x &= ~0ull << (8 * (8 - left));
+                h = fold_limb(h, B, x >> 32);
+                h = fold_limb(h, B, x & 0xFFFFFFFFull);
+            }
+            pw += 8;
+        }
     }
     hst[q] = h;
     hlen[q] = le;
@@ -279,38 +368,104 @@ __global__ void __launch_bounds__(DD_T) k_pd_buckets(const uint32_t* __restrict_
     }
 }
 
-// B4: retire unique / fully tested strings; compact the survivors and the next
-// round's reps.
-__global__ void k_pd_retire(PdIn in, const uint32_t* __restrict__ act, uint32_t nact,
-                            const uint32_t* __restrict__ lpos, const uint8_t* __restrict__ dupf,
-                            uint32_t* __restrict__ apos, uint32_t* __restrict__ act_next,
-                            uint32_t* __restrict__ reps_next, uint32_t* __restrict__ cnt, uint64_t L, int last) {
+// B2/B3, hash-table variant: insert every rep key; a second copy marks the slot
+__global__ void k_pd_ht_insert(const uint64_t* __restrict__ K, uint32_t m, unsigned long long* __restrict__ tab,
+                               uint8_t* __restrict__ mark, uint32_t tmask, uint32_t* __restrict__ zero_cnt,
+                               unsigned* err) {
     uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    bool keep = false, rep_next = false;
-    uint32_t q = 0;
-    if (j < nact) {
-        q = act[j];
-        uint32_t len = lpos[q];
-        bool dup;
-        if (group_start(in, q, L)) {
-            bool single = true;
-            if (in.run_lcp) {
-                uint32_t pe = part_end_of(q, in.n, in.p);
-                single = !(q + 1 < pe && in.run_lcp[q + 1] >= L);
-            }
-            dup = !single || dupf[q] != 0;
-        } else {
-            dup = true;
+    if (j >= m) return;
+    uint64_t k = K[j];
+    if (k == 0) {  // 0 marks an empty slot: count zero keys apart
+        atomicAdd(zero_cnt, 1u);
+        return;
+    }
+    uint32_t h = (uint32_t)k & tmask;
+    for (uint32_t i = 0; i <= tmask; ++i) {
+        unsigned long long old = atomicCAS(&tab[h], 0ull, (unsigned long long)k);
+        if (old == 0ull) return;
+        if (old == k) {
+            mark[h] = 1;
+            return;
         }
+        h = (h + 1) & tmask;
+    }
+    atomicOr(err, ERRBIT_OVERFLOW);
+}
+
+__device__ __forceinline__ bool ht_dup(const unsigned long long* tab, const uint8_t* mark, uint32_t tmask,
+                                       uint32_t zero_cnt, uint64_t k) {
+    if (k == 0) return zero_cnt > 1;
+    uint32_t h = (uint32_t)k & tmask;
+    for (uint32_t i = 0; i <= tmask; ++i) {
+        uint64_t t = tab[h];
+        if (t == k) return mark[h] != 0;
+        if (t == 0) return false;  // not reachable: every key was inserted
+        h = (h + 1) & tmask;
+    }
+    return true;
+}
+
+// B4: retire the reps whose group is one string with a unique key (or whose
+// length <= L); survivors stay reps next round.
+__global__ void k_pd_retire(PdIn in, const uint32_t* __restrict__ reps, uint32_t nreps,
+                            const uint32_t* __restrict__ lpos, const uint64_t* __restrict__ K,
+                            const uint8_t* __restrict__ dupf, const unsigned long long* __restrict__ tab,
+                            const uint8_t* __restrict__ mark, uint32_t tmask, const uint32_t* __restrict__ zero_cnt,
+                            uint32_t* __restrict__ apos, uint32_t* __restrict__ reps_next,
+                            uint32_t* __restrict__ cnt, uint64_t L, int use_ht) {
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    bool keep = false;
+    uint32_t q = 0, retired = 0;
+    if (j < nreps) {
+        q = reps[j];
+        uint32_t len = lpos[q];
+        bool single = true;
+        if (in.run_lcp) {
+            uint32_t pe = part_end_of(q, in.n, in.p);
+            single = !(q + 1 < pe && in.run_lcp[q + 1] >= L);
+        }
+        bool dup = !single;
+        if (!dup) dup = use_ht ? ht_dup(tab, mark, tmask, *zero_cnt, K[j]) : (dupf[q] != 0);
         if (!dup || (uint64_t)len <= L) {
             apos[q] = (uint64_t)len < L ? len : (uint32_t)L;
+            retired = 1;
         } else {
             keep = true;
-            rep_next = !last && group_start(in, q, 2 * L);
         }
     }
-    warp_append(keep, q, act_next, &cnt[1]);
-    warp_append(rep_next, q, reps_next, &cnt[0]);
+    warp_append(keep, q, reps_next, &cnt[0]);
+    uint32_t r = __reduce_add_sync(SSS_FULL, retired);
+    if ((threadIdx.x & 31) == 0 && r) atomicAdd(&cnt[1], r);
+}
+
+// strings equal to their local predecessor whose whole length is tested this
+// round: duplicates that retire with approx = len
+__global__ void k_pd_retire_equal(const uint32_t* __restrict__ list, uint32_t m, const uint32_t* __restrict__ lpos,
+                                  uint32_t* __restrict__ apos, uint32_t* __restrict__ cnt) {
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t retired = 0;
+    if (j < m) {
+        uint32_t q = list[j];
+        if (apos[q] == ACTIVE) {
+            apos[q] = lpos[q];
+            retired = 1;
+        }
+    }
+    uint32_t r = __reduce_add_sync(SSS_FULL, retired);
+    if ((threadIdx.x & 31) == 0 && r) atomicAdd(&cnt[1], r);
+}
+
+// positions that start a group from the next round on become reps (if active)
+__global__ void k_pd_newreps(const uint32_t* __restrict__ list, uint32_t m, const uint32_t* __restrict__ apos,
+                             uint32_t* __restrict__ reps_next, uint32_t* __restrict__ cnt) {
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    bool want = false;
+    uint32_t q = 0;
+    if (j < m) {
+        q = list[j];
+        want = apos[q] == ACTIVE;
+    }
+    warp_append(want, q, reps_next, &cnt[0]);
 }
 
 __global__ void k_pd_final(PdIn in, const uint32_t* __restrict__ apos, const uint32_t* __restrict__ lpos,
@@ -326,8 +481,12 @@ struct PdBufs {
     uint32_t* lpos;
     uint32_t* hlen;
     uint64_t* hst;
-    uint32_t* act[2];
+    uint32_t* list_ks;
+    uint32_t* list_kl;
     uint32_t* reps[2];
+    unsigned long long* tab;
+    uint8_t* mark;
+    uint32_t tcap;
     uint64_t* K;
     uint32_t* V;
     uint64_t* tK;
@@ -344,8 +503,8 @@ void carve_pd(Arena& ar, uint32_t n, PdBufs& b) {
     b.lpos = ar.take<uint32_t>(n);
     b.hlen = ar.take<uint32_t>(n);
     b.hst = ar.take<uint64_t>(n);
-    b.act[0] = ar.take<uint32_t>(n);
-    b.act[1] = ar.take<uint32_t>(n);
+    b.list_ks = ar.take<uint32_t>(n);
+    b.list_kl = ar.take<uint32_t>(n);
     b.reps[0] = ar.take<uint32_t>(n);
     b.reps[1] = ar.take<uint32_t>(n);
     b.K = ar.take<uint64_t>(n);
@@ -356,7 +515,11 @@ void carve_pd(Arena& ar, uint32_t n, PdBufs& b) {
     b.hist = ar.take<uint32_t>((1u << HB_MAX) + 1);
     b.bstart = ar.take<uint32_t>((1u << HB_MAX) + 1);
     b.cursor = ar.take<uint32_t>((1u << HB_MAX) + 1);
-    b.cnt = ar.take<uint32_t>(8);
+    b.cnt = ar.take<uint32_t>(8 + 4 * KBINS);
+    b.tcap = 1024;
+    while (b.tcap < 2ull * n) b.tcap <<= 1;
+    b.tab = ar.take<unsigned long long>(b.tcap);
+    b.mark = ar.take<uint8_t>(b.tcap);
 }
 
 uint64_t host_smix(uint64_t z) { return smix64(z); }
@@ -384,57 +547,100 @@ sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& sin, const uin
         g_pd_attr[ctx->device & 63] = true;
     }
     PdIn in{sin.chars, sin.offs, run_perm, run_lcp, n, run_perm ? p : 1u};
-    uint32_t kmin = prm.kmin, kmax = prm.kmax == SSS_KMAX_AUTO ? 31u : prm.kmax;
-    if (kmax > 31) kmax = 31;
+    const uint32_t kmin = std::min<uint32_t>(prm.kmin, 31u);
+    uint32_t kmax = prm.kmax == SSS_KMAX_AUTO ? 31u : std::min<uint32_t>(prm.kmax, 31u);
+    const bool use_ht = !(prm.flags & SSS_FLAG_DEDUPE_SORT);
     const uint64_t Bh = 2 + host_smix(prm.hash_seed + GAMMA) % (P61 - 3);
 
     void* pin;
-    SSS_TRY(sss_pinned(ctx, 64, &pin));
-    uint32_t* h_cnt = static_cast<uint32_t*>(pin);
+    SSS_TRY(sss_pinned(ctx, sizeof(uint32_t) * (8 + 4 * KBINS), &pin));
+    uint32_t* h = static_cast<uint32_t*>(pin);
+    uint32_t* cnt = B.cnt;                  // [0] reps next, [1] retired, [2] zero keys
+    uint32_t* cnt_ks = B.cnt + 8;           // KBINS
+    uint32_t* cnt_kl = cnt_ks + KBINS;      // KBINS
+    uint32_t* cur_ks = cnt_kl + KBINS;      // KBINS
+    uint32_t* cur_kl = cur_ks + KBINS;      // KBINS
 
-    SSS_CUDA(cudaMemsetAsync(B.cnt, 0, sizeof(uint32_t) * 8, ctx->stream));
-    uint32_t nact = n, nreps = 0;
-    if (kmin <= kmax) {
-        SSS_TRY(sss_launch(ctx, "pd_init", k_pd_init, dim3((n + 255) / 256), dim3(256), 0, in, sin.lens, B.apos,
-                           B.lpos, B.hlen, B.act[0], B.reps[0], B.cnt, (uint64_t)1 << kmin));
-        SSS_CUDA(cudaMemcpyAsync(h_cnt, B.cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
-        SSS_CUDA(cudaStreamSynchronize(ctx->stream));
-        nreps = h_cnt[0];
-    } else {
-        // no rounds: every string keeps approx = len
-        SSS_TRY(sss_launch(ctx, "pd_init", k_pd_init, dim3((n + 255) / 256), dim3(256), 0, in, sin.lens, B.apos,
-                           B.lpos, B.hlen, B.act[0], B.reps[0], B.cnt, (uint64_t)1));
+    SSS_CUDA(cudaMemsetAsync(B.cnt, 0, sizeof(uint32_t) * (8 + 4 * KBINS), ctx->stream));
+    SSS_TRY(sss_launch(ctx, "pd_init", k_pd_init, dim3((n + 255) / 256), dim3(256), 0, in, sin.lens, B.apos, B.lpos,
+                       B.hlen, cnt_ks, cnt_kl, kmin));
+    if (kmin > kmax) {
+        return sss_launch(ctx, "pd_final", k_pd_final, dim3((n + 255) / 256), dim3(256), 0, in,
+                          (const uint32_t*)B.apos, (const uint32_t*)B.lpos, approx);
     }
-    int cur = 0;
-    for (uint32_t k = kmin; k <= kmax && nact > 0; ++k) {
+    SSS_CUDA(cudaMemcpyAsync(h, cnt_ks, sizeof(uint32_t) * 2 * KBINS, cudaMemcpyDeviceToHost, ctx->stream));
+    SSS_CUDA(cudaStreamSynchronize(ctx->stream));
+    uint32_t ks_off[KBINS + 1], kl_off[KBINS + 1];
+    ks_off[0] = kl_off[0] = 0;
+    for (int i = 0; i < KBINS; ++i) {
+        ks_off[i + 1] = ks_off[i] + h[i];
+        kl_off[i + 1] = kl_off[i] + h[KBINS + i];
+    }
+    // list cursors start at the bucket offsets
+    for (int i = 0; i < KBINS; ++i) {
+        h[i] = ks_off[i];
+        h[KBINS + i] = kl_off[i];
+    }
+    SSS_TRY(sss_upload(ctx, cur_ks, h, sizeof(uint32_t) * 2 * KBINS));
+    SSS_TRY(sss_launch(ctx, "pd_lists", k_pd_lists, dim3((n + 255) / 256), dim3(256), 0, in, (const uint32_t*)B.lpos,
+                       cur_ks, cur_kl, B.list_ks, B.list_kl, kmin));
+    // the first round's reps are the positions that start a group at L = 2^kmin
+    const uint32_t* reps = B.list_ks + ks_off[kmin];
+    uint32_t nreps = ks_off[kmin + 1] - ks_off[kmin];
+    uint32_t retired = 0;
+    int nxt = 0;
+    for (uint32_t k = kmin; k <= kmax && retired < n; ++k) {
         const uint64_t L = 1ull << k;
+        uint32_t tmask = 0;
         if (nreps > 0) {
-            SSS_TRY(sss_launch(ctx, "pd_hash", k_pd_hash, dim3((nreps + 255) / 256), dim3(256), 0, in,
-                               (const uint32_t*)B.reps[cur], nreps, (const uint32_t*)B.lpos, B.hst, B.hlen, B.K, B.V, L,
-                               Bh));
-            uint32_t bits = 0;
-            while (bits < (uint32_t)HB_MAX && ((uint64_t)nreps >> bits) > 1024) ++bits;
-            uint32_t nb = 1u << bits;
-            SSS_CUDA(cudaMemsetAsync(B.hist, 0, sizeof(uint32_t) * (nb + 1), ctx->stream));
-            uint32_t hgrid = std::min<uint32_t>((nreps + 4095) / 4096, 2u * (uint32_t)ctx->sm_count);
-            SSS_TRY(sss_launch(ctx, "pd_hist", k_pd_hist, dim3(hgrid), dim3(512), 0, (const uint64_t*)B.K, nreps, bits,
-                               B.hist));
-            SSS_TRY(sss_launch(ctx, "pd_scan", k_pd_scan, dim3(1), dim3(1024), 0, B.hist, nb, B.bstart, B.cursor));
-            SSS_TRY(sss_launch(ctx, "pd_scatter", k_pd_scatter, dim3((nreps + 255) / 256), dim3(256), 0,
-                               (const uint64_t*)B.K, (const uint32_t*)B.V, nreps, bits, (const uint32_t*)B.bstart,
-                               B.cursor, B.tK, B.tV));
-            SSS_TRY(sss_launch(ctx, "pd_buckets", k_pd_buckets, dim3(nb), dim3(DD_T), (size_t)DD_CAP * (8 + 8 + 1),
-                               (const uint32_t*)B.bstart, B.tK, B.tV, B.dupf));
+            SSS_TRY(sss_launch(ctx, "pd_hash", k_pd_hash, dim3((nreps + 255) / 256), dim3(256), 0, in, reps, nreps,
+                               (const uint32_t*)B.lpos, B.hst, B.hlen, B.K, B.V, L, Bh));
+            if (use_ht) {
+                uint32_t T = 1024;
+                while (T < 2ull * nreps) T <<= 1;
+                tmask = T - 1;
+                SSS_CUDA(cudaMemsetAsync(B.tab, 0, sizeof(unsigned long long) * T, ctx->stream));
+                SSS_CUDA(cudaMemsetAsync(B.mark, 0, T, ctx->stream));
+                SSS_CUDA(cudaMemsetAsync(&cnt[2], 0, sizeof(uint32_t), ctx->stream));
+                SSS_TRY(sss_launch(ctx, "pd_ht_insert", k_pd_ht_insert, dim3((nreps + 255) / 256), dim3(256), 0,
+                                   (const uint64_t*)B.K, nreps, B.tab, B.mark, tmask, &cnt[2], ctx->d_err));
+            } else {
+                uint32_t bits = 0;
+                while (bits < (uint32_t)HB_MAX && ((uint64_t)nreps >> bits) > 1024) ++bits;
+                uint32_t nb = 1u << bits;
+                SSS_CUDA(cudaMemsetAsync(B.hist, 0, sizeof(uint32_t) * (nb + 1), ctx->stream));
+                uint32_t hgrid = std::min<uint32_t>((nreps + 4095) / 4096, 2u * (uint32_t)ctx->sm_count);
+                SSS_TRY(sss_launch(ctx, "pd_hist", k_pd_hist, dim3(hgrid), dim3(512), 0, (const uint64_t*)B.K, nreps,
+                                   bits, B.hist));
+                SSS_TRY(sss_launch(ctx, "pd_scan", k_pd_scan, dim3(1), dim3(1024), 0, B.hist, nb, B.bstart,
+                                   B.cursor));
+                SSS_TRY(sss_launch(ctx, "pd_scatter", k_pd_scatter, dim3((nreps + 255) / 256), dim3(256), 0,
+                                   (const uint64_t*)B.K, (const uint32_t*)B.V, nreps, bits,
+                                   (const uint32_t*)B.bstart, B.cursor, B.tK, B.tV));
+                SSS_TRY(sss_launch(ctx, "pd_buckets", k_pd_buckets, dim3(nb), dim3(DD_T),
+                                   (size_t)DD_CAP * (8 + 8 + 1), (const uint32_t*)B.bstart, B.tK, B.tV, B.dupf));
+            }
         }
-        SSS_CUDA(cudaMemsetAsync(B.cnt, 0, sizeof(uint32_t) * 2, ctx->stream));
-        SSS_TRY(sss_launch(ctx, "pd_retire", k_pd_retire, dim3((nact + 255) / 256), dim3(256), 0, in,
-                           (const uint32_t*)B.act[cur], nact, (const uint32_t*)B.lpos, (const uint8_t*)B.dupf, B.apos,
-                           B.act[cur ^ 1], B.reps[cur ^ 1], B.cnt, L, (int)(k == kmax)));
-        SSS_CUDA(cudaMemcpyAsync(h_cnt, B.cnt, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, ctx->stream));
+        SSS_CUDA(cudaMemsetAsync(&cnt[0], 0, sizeof(uint32_t), ctx->stream));
+        SSS_TRY(sss_launch(ctx, "pd_retire", k_pd_retire, dim3((nreps + 255) / 256), dim3(256), 0, in, reps, nreps,
+                           (const uint32_t*)B.lpos, (const uint64_t*)B.K, (const uint8_t*)B.dupf,
+                           (const unsigned long long*)B.tab, (const uint8_t*)B.mark, tmask,
+                           (const uint32_t*)&cnt[2], B.apos, B.reps[nxt], cnt, L, (int)use_ht));
+        uint32_t ne = kl_off[k + 1] - kl_off[k];
+        SSS_TRY(sss_launch(ctx, "pd_retire_equal", k_pd_retire_equal, dim3((ne + 255) / 256), dim3(256), 0,
+                           (const uint32_t*)(B.list_kl + kl_off[k]), ne, (const uint32_t*)B.lpos, B.apos, cnt));
+        if (k < kmax) {
+            uint32_t nn = ks_off[k + 2] - ks_off[k + 1];
+            SSS_TRY(sss_launch(ctx, "pd_newreps", k_pd_newreps, dim3((nn + 255) / 256), dim3(256), 0,
+                               (const uint32_t*)(B.list_ks + ks_off[k + 1]), nn, (const uint32_t*)B.apos,
+                               B.reps[nxt], cnt));
+        }
+        SSS_CUDA(cudaMemcpyAsync(h, cnt, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, ctx->stream));
         SSS_CUDA(cudaStreamSynchronize(ctx->stream));
-        nreps = h_cnt[0];
-        nact = h_cnt[1];
-        cur ^= 1;
+        nreps = h[0];
+        retired = h[1];
+        reps = B.reps[nxt];
+        nxt ^= 1;
     }
     return sss_launch(ctx, "pd_final", k_pd_final, dim3((n + 255) / 256), dim3(256), 0, in, (const uint32_t*)B.apos,
                       (const uint32_t*)B.lpos, approx);

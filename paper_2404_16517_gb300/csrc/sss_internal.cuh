@@ -64,9 +64,11 @@ struct sss_ctx {
     // caller-supplied work memory
     void* ws_user = nullptr;
     size_t ws_user_bytes = 0;
-    // pinned host staging for small counters and segment lists
+    // pinned host staging for small counters and segment lists; pin_event is
+    // recorded after every upload from it, and waited on before it is reused
     void* h_pin = nullptr;
     size_t h_pin_bytes = 0;
+    cudaEvent_t pin_event = nullptr;
     // sticky device error word
     unsigned* d_err = nullptr;
     // small device scratch for counters and reductions (never inside the workspace)
@@ -100,8 +102,11 @@ sss_status sss_fail(sss_ctx* c, sss_status s, const std::string& msg);
 
 // Work memory of at least `bytes`; grows library-owned memory when needed.
 sss_status sss_workspace(sss_ctx* ctx, size_t bytes, char** out);
-// Pinned host staging of at least `bytes`.
+// Pinned host staging of at least `bytes` (waits until earlier uploads from it
+// have completed).
 sss_status sss_pinned(sss_ctx* ctx, size_t bytes, void** out);
+// Asynchronous upload from the pinned staging buffer (tracked by pin_event).
+sss_status sss_upload(sss_ctx* ctx, void* dst, const void* src, size_t bytes);
 
 // Instrumentation hooks used by the launch wrapper.
 int sss_stat_index(sss_ctx* ctx, const char* name);
@@ -160,7 +165,7 @@ sss_status impl_partition(sss_ctx* ctx, Arena& ar, const StrIn& in, const uint32
                           uint32_t p, uint32_t v, uint32_t* out_spl, uint32_t* out_bounds);
 size_t need_merge(uint32_t n, uint32_t p, uint32_t v, uint64_t nrecchars);
 sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, const uint32_t* trunc,
-                      const uint32_t* run_perm, const uint32_t* run_lcp, uint32_t p, uint32_t v,
+                      const uint32_t* run_perm, const uint32_t* run_lcp, uint32_t p, uint32_t v, uint32_t ms,
                       uint64_t nrecchars, uint32_t* out_perm, uint32_t* out_lcp);
 sss_status impl_sum_tlen(sss_ctx* ctx, const StrIn& in, const uint32_t* trunc, uint64_t* out);
 

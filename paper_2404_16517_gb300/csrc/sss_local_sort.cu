@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(BK_T) k_lg_buckets(const LgSegInfo* __restrict
                                                      const uint64_t* __restrict__ tK, const uint32_t* __restrict__ tV,
                                                      const uint32_t* __restrict__ lens, uint64_t* __restrict__ K,
                                                      uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
-                                                     SegLists L, unsigned* err) {
+                                                     SegLists L, unsigned* err, uint32_t ns) {
     constexpr int ITEMS = BK_CAP / BK_T;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* sHi = reinterpret_cast<uint64_t*>(smem);
@@ -255,8 +255,9 @@ __global__ void __launch_bounds__(BK_T) k_lg_buckets(const LgSegInfo* __restrict
     uint32_t* sA = reinterpret_cast<uint32_t*>(sLo + BK_CAP);
     uint32_t* sN = sA + BK_CAP;
     __shared__ uint32_t sh_warp[32];
-    LgSegInfo si = info[blockIdx.y];
-    uint32_t b = blockIdx.x;
+    const uint32_t sidx = segment_of_bucket(info, ns, blockIdx.x);
+    LgSegInfo si = info[sidx];
+    uint32_t b = blockIdx.x - si.bk_base;
     uint32_t nbk = 2 * si.nb - 1;
     if (b >= nbk) return;
     uint32_t bs = bst[si.bst_base + b], be = bst[si.bst_base + b + 1];
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(BK_T) k_lg_buckets(const LgSegInfo* __restrict
     }
     uint32_t m = be - bs;
     if (m == 0) return;
-    uint32_t d = si.seg.depth + segmin[blockIdx.y];
+    uint32_t d = si.seg.depth + segmin[sidx];
     bool eq = (b & 1u) != 0;
     if (eq || m > (uint32_t)BK_CAP) {
         for (uint32_t q = bs + threadIdx.x; q < be; q += BK_T) {
@@ -462,9 +463,8 @@ sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p,
     if (!tiny.empty() || !med.empty()) {
         std::copy(tiny.begin(), tiny.end(), h_seg);
         std::copy(med.begin(), med.end(), h_seg + tiny.size());
-        SSS_CUDA(cudaMemcpyAsync(B.tiny, h_seg, sizeof(Seg) * tiny.size(), cudaMemcpyHostToDevice, ctx->stream));
-        SSS_CUDA(cudaMemcpyAsync(B.med, h_seg + tiny.size(), sizeof(Seg) * med.size(), cudaMemcpyHostToDevice,
-                                 ctx->stream));
+        SSS_TRY(sss_upload(ctx, B.tiny, h_seg, sizeof(Seg) * tiny.size()));
+        SSS_TRY(sss_upload(ctx, B.med, h_seg + tiny.size(), sizeof(Seg) * med.size()));
         SSS_TRY(run_finishers(ctx, B, (uint32_t)tiny.size(), (uint32_t)med.size(), in, perm, lcp));
         // staging is reused below: wait for the uploads
         SSS_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -475,12 +475,11 @@ sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p,
     while (!large.empty()) {
         if (++rounds > 100000u) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: round limit exceeded");
         uint32_t ns = (uint32_t)large.size();
-        uint32_t ntiles = 0;
-        if (!plan_sp(large, LG_TARGET, B.sp, h_info, h_tiles, &ntiles))
+        uint32_t ntiles = 0, nbuckets = 0;
+        if (!plan_sp(large, LG_TARGET, B.sp, h_info, h_tiles, &ntiles, &nbuckets))
             return sss_fail(ctx, SSS_ERR_CUDA, "local sort: internal capacity exceeded");
-        SSS_CUDA(cudaMemcpyAsync(B.sp.info, h_info, sizeof(LgSegInfo) * ns, cudaMemcpyHostToDevice, ctx->stream));
-        SSS_CUDA(cudaMemcpyAsync(B.sp.tiles, h_tiles, sizeof(LgTile) * ntiles, cudaMemcpyHostToDevice,
-                                 ctx->stream));
+        SSS_TRY(sss_upload(ctx, B.sp.info, h_info, sizeof(LgSegInfo) * ns));
+        SSS_TRY(sss_upload(ctx, B.sp.tiles, h_tiles, sizeof(LgTile) * ntiles));
         SSS_CUDA(cudaMemsetAsync(B.segmin, 0xFF, sizeof(uint32_t) * ns, ctx->stream));
         SSS_CUDA(cudaMemsetAsync(B.cnt, 0, sizeof(uint32_t) * 4, ctx->stream));
         SSS_TRY(sss_launch(ctx, "ls_lg_ext", k_lg_ext, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.sp.tiles,
@@ -491,10 +490,10 @@ sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p,
                            (const uint32_t*)B.segmin, B.K));
         SSS_TRY(launch_sp(ctx, B.sp, ns, ntiles, B.K, perm, B.tK, B.tV, "ls_lg_samples", "ls_lg_classify",
                           "ls_lg_offsets", "ls_lg_scatter"));
-        SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets, dim3(LG_NBMAX, ns), dim3(BK_T),
+        SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets, dim3(nbuckets), dim3(BK_T),
                            (size_t)BK_CAP * (8 + 8 + 4 + 4), (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst,
                            (const uint32_t*)B.segmin, (const uint64_t*)B.tK, (const uint32_t*)B.tV, in.lens, B.K, perm,
-                           lcp, L, ctx->d_err));
+                           lcp, L, ctx->d_err, ns));
         SSS_TRY(sss_launch(ctx, "ls_lg_seams", k_lg_seams, dim3(ns), dim3(512), 0, (const LgSegInfo*)B.sp.info,
                            (const uint32_t*)B.sp.bst, (const uint32_t*)B.segmin, (const uint64_t*)B.K, lcp));
         SSS_CUDA(cudaMemcpyAsync(h_cnt, B.cnt, sizeof(uint32_t) * 3, cudaMemcpyDeviceToHost, ctx->stream));

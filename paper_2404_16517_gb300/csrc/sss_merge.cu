@@ -24,7 +24,7 @@
 namespace {
 
 constexpr uint32_t MINF = 0xFFFFFFFFu;  // "minus infinity" splitter
-constexpr int MS = 64;                   // merge segment sample spacing
+constexpr uint32_t MS_DEFAULT = 32;      // merge segment sample spacing (default)
 
 // ---------------------------------------------------------------------------
 // string comparison helpers on (truncated) original strings
@@ -339,7 +339,7 @@ __device__ __forceinline__ uint32_t lcp_search(const Strs& S, const Recs& R, con
 // one thread per sample: rank in the other run and LCPs with the neighbours there
 __global__ void k_d_search(Strs S, Recs R, const uint32_t* __restrict__ Rin, const Pair* __restrict__ pairs,
                            uint32_t npairs, uint32_t nsamp, uint32_t* __restrict__ srank,
-                           uint32_t* __restrict__ sl0, uint32_t* __restrict__ sl1) {
+                           uint32_t* __restrict__ sl0, uint32_t* __restrict__ sl1, uint32_t MS) {
     uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nsamp) return;
     // pair of sample g: last pair with sa <= g
@@ -366,7 +366,7 @@ __global__ void k_d_search(Strs S, Recs R, const uint32_t* __restrict__ Rin, con
 __global__ void k_d_merge(Strs S, Recs R, const uint32_t* __restrict__ Rin, const uint32_t* __restrict__ Hin,
                           uint32_t* __restrict__ Rout, uint32_t* __restrict__ Hout, const Pair* __restrict__ pairs,
                           uint32_t npairs, uint32_t nsamp, const uint32_t* __restrict__ srank,
-                          const uint32_t* __restrict__ sl0, const uint32_t* __restrict__ sl1) {
+                          const uint32_t* __restrict__ sl0, const uint32_t* __restrict__ sl1, uint32_t MS) {
     uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nsamp) return;
     uint32_t a = 0, c = npairs;
@@ -564,6 +564,7 @@ void carve_mg_small(Arena& ar, uint32_t n, uint32_t p, uint32_t v, MgBufs& b) {
 }
 
 void carve_mg(Arena& ar, uint32_t n, uint32_t p, uint32_t v, uint64_t nrecchars, MgBufs& b) {
+    const uint32_t MS = 8;  // smallest spacing: sample arrays sized for it
     carve_mg_small(ar, n, p, v, b);
     b.piece_off = ar.take<uint32_t>((size_t)p * p);
     b.bstart = ar.take<uint32_t>(p + 1);
@@ -580,18 +581,25 @@ void carve_mg(Arena& ar, uint32_t n, uint32_t p, uint32_t v, uint64_t nrecchars,
     b.HA[0] = ar.take<uint32_t>(n);
     b.HA[1] = ar.take<uint32_t>(n);
     uint32_t maxpairs = p * ((p + 1) / 2) + 1;
-    b.pairs = ar.take<Pair>(maxpairs);
+    b.pairs = ar.take<Pair>((size_t)p * p + 16);  // every level's pairs (< p per bucket in total)
     uint32_t maxs = n / MS + maxpairs * 2 + 2;
     b.srank = ar.take<uint32_t>(maxs);
     b.sl0 = ar.take<uint32_t>(maxs);
     b.sl1 = ar.take<uint32_t>(maxs);
 }
 
-__global__ void k_sum_tlen(Strs S, uint32_t n, unsigned long long* out) {
+__global__ void __launch_bounds__(256) k_sum_tlen(Strs S, uint32_t n, unsigned long long* out) {
+    __shared__ uint64_t sw[8];
     uint64_t v = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v += tlen(S, i);
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(SSS_FULL, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, (unsigned long long)v);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t t = 0;
+        for (int w = 0; w < 8; ++w) t += sw[w];
+        if (t) atomicAdd(out, (unsigned long long)t);
+    }
 }
 
 __global__ void k_iota(uint32_t* a, uint32_t n) {
@@ -654,8 +662,10 @@ size_t need_merge(uint32_t n, uint32_t p, uint32_t v, uint64_t nrecchars) {
 // Stages C and D.  The record-character bound (sum of truncated lengths) is
 // needed to size the work memory, so it is computed first by the caller.
 sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, const uint32_t* trunc,
-                      const uint32_t* run_perm, const uint32_t* run_lcp, uint32_t p, uint32_t v,
+                      const uint32_t* run_perm, const uint32_t* run_lcp, uint32_t p, uint32_t v, uint32_t ms_param,
                       uint64_t nrecchars, uint32_t* out_perm, uint32_t* out_lcp) {
+    uint32_t MS = MS_DEFAULT;
+    if (ms_param >= 8 && ms_param <= 1024 && (ms_param & (ms_param - 1)) == 0) MS = ms_param;
     const uint32_t n = in.n;
     Arena ar{ws, ws_bytes, 0};
     MgBufs b;
@@ -665,7 +675,7 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
 
     // bounds to the host: piece sizes, bucket starts, piece offsets
     void* pin;
-    size_t pin_need = sizeof(uint32_t) * ((size_t)p * (p + 1) + (size_t)p * p + p + 1) + sizeof(Pair) * (p * p + 4);
+    size_t pin_need = sizeof(uint32_t) * ((size_t)p * (p + 1) + (size_t)p * p + p + 1) + sizeof(Pair) * (p * p + 16);
     SSS_TRY(sss_pinned(ctx, pin_need + 256, &pin));
     uint32_t* hb = static_cast<uint32_t*>(pin);
     uint32_t* hpo = hb + (size_t)p * (p + 1);
@@ -686,8 +696,8 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
     }
     hbs[p] = acc;
     if (acc != n) return sss_fail(ctx, SSS_ERR_CUDA, "merge: bucket bounds do not cover the input");
-    SSS_CUDA(cudaMemcpyAsync(b.piece_off, hpo, sizeof(uint32_t) * p * p, cudaMemcpyHostToDevice, ctx->stream));
-    SSS_CUDA(cudaMemcpyAsync(b.bstart, hbs, sizeof(uint32_t) * (p + 1), cudaMemcpyHostToDevice, ctx->stream));
+    SSS_TRY(sss_upload(ctx, b.piece_off, hpo, sizeof(uint32_t) * p * p));
+    SSS_TRY(sss_upload(ctx, b.bstart, hbs, sizeof(uint32_t) * (p + 1)));
 
     // D1: records and their characters
     SSS_TRY(sss_launch(ctx, "d_records", k_d_records, dim3((n + 255) / 256), dim3(256), 0, run_perm, run_lcp, n, p, S,
@@ -703,15 +713,18 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
     SSS_TRY(sss_launch(ctx, "d_iota", k_iota, dim3((n + 255) / 256), dim3(256), 0, b.RA[0], n));
     SSS_CUDA(cudaMemcpyAsync(b.HA[0], b.R.h, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
 
-    // D2: pairwise merge levels; runs of bucket j at level 0 are its pieces
+    // D2: pairwise merge levels; runs of bucket j at level 0 are its pieces.
+    // All levels' pair tables are planned on the host and uploaded at once.
     std::vector<std::vector<uint32_t>> runs(p);  // run sizes per bucket
     for (uint32_t j = 0; j < p; ++j) runs[j] = psz[j];
-    int cur = 0;
+    std::vector<Pair> all_pairs;
+    std::vector<uint32_t> lvl_first, lvl_np, lvl_ns;
     for (;;) {
         bool more = false;
         for (uint32_t j = 0; j < p; ++j) more |= runs[j].size() > 1;
         if (!more) break;
         uint32_t np = 0, ns = 0;
+        lvl_first.push_back((uint32_t)all_pairs.size());
         for (uint32_t j = 0; j < p; ++j) {
             uint32_t pos = hbs[j];
             std::vector<uint32_t> next;
@@ -727,22 +740,36 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
                     ns += (na + MS - 1) / MS;
                     pr.sb = ns;
                     ns += (nb + MS - 1) / MS;
-                    hpairs[np++] = pr;
+                    all_pairs.push_back(pr);
+                    ++np;
                 }
                 pos += na + nb;
                 next.push_back(na + nb);
             }
             runs[j] = next;
         }
-        SSS_CUDA(cudaMemcpyAsync(b.pairs, hpairs, sizeof(Pair) * np, cudaMemcpyHostToDevice, ctx->stream));
+        lvl_np.push_back(np);
+        lvl_ns.push_back(ns);
+    }
+    const uint32_t nlev = (uint32_t)lvl_np.size();
+    Pair* d_pairs = nullptr;
+    if (nlev > 0) {
+        // the pinned region after the bucket tables was reserved for the pairs
+        if (all_pairs.size() > (size_t)p * p + 16) return sss_fail(ctx, SSS_ERR_CUDA, "merge: pair table overflow");
+        std::copy(all_pairs.begin(), all_pairs.end(), hpairs);
+        d_pairs = b.pairs;
+        SSS_TRY(sss_upload(ctx, d_pairs, hpairs, sizeof(Pair) * all_pairs.size()));
+    }
+    int cur = 0;
+    for (uint32_t lv = 0; lv < nlev; ++lv) {
+        const Pair* pr = d_pairs + lvl_first[lv];
+        uint32_t np = lvl_np[lv], ns = lvl_ns[lv];
         SSS_TRY(sss_launch(ctx, "d_search", k_d_search, dim3((ns + 127) / 128), dim3(128), 0, S, b.R,
-                           (const uint32_t*)b.RA[cur], (const Pair*)b.pairs, np, ns, b.srank, b.sl0, b.sl1));
+                           (const uint32_t*)b.RA[cur], pr, np, ns, b.srank, b.sl0, b.sl1, MS));
         SSS_TRY(sss_launch(ctx, "d_merge", k_d_merge, dim3((ns + 127) / 128), dim3(128), 0, S, b.R,
                            (const uint32_t*)b.RA[cur], (const uint32_t*)b.HA[cur], b.RA[cur ^ 1], b.HA[cur ^ 1],
-                           (const Pair*)b.pairs, np, ns, (const uint32_t*)b.srank, (const uint32_t*)b.sl0,
-                           (const uint32_t*)b.sl1));
-        // the pinned pair table is rewritten next level: wait for the upload
-        SSS_CUDA(cudaStreamSynchronize(ctx->stream));
+                           pr, np, ns, (const uint32_t*)b.srank, (const uint32_t*)b.sl0, (const uint32_t*)b.sl1,
+                           MS));
         cur ^= 1;
     }
     // D3

@@ -30,7 +30,8 @@ struct LgSegInfo {
     uint32_t nb;        // range buckets B (splitters B-1, buckets 2B-1)
     uint32_t hist_base; // offset into hist (bucket-major: b*tiles + t)
     uint32_t bst_base;  // offset into bucket starts (2B entries)
-    uint32_t pad[3];
+    uint32_t bk_base;   // index of this segment's first bucket in the flat bucket list
+    uint32_t pad[2];
 };
 
 struct LgTile {
@@ -194,10 +195,10 @@ inline void carve_sp(Arena& ar, uint32_t n, uint32_t cap_segs, SpBufs& b) {
 // pinned staging (h_info, h_tiles).  Range buckets target `target` keys each.
 // Returns false when a capacity would be exceeded.
 inline bool plan_sp(const std::vector<Seg>& segs, uint32_t target, const SpBufs& B, LgSegInfo* h_info,
-                    LgTile* h_tiles, uint32_t* out_ntiles) {
+                    LgTile* h_tiles, uint32_t* out_ntiles, uint32_t* out_nbuckets = nullptr) {
     uint32_t ns = (uint32_t)segs.size();
     if (ns > B.cap_segs) return false;
-    uint32_t ntiles = 0, hist_off = 0;
+    uint32_t ntiles = 0, hist_off = 0, nbk = 0;
     for (uint32_t s = 0; s < ns; ++s) {
         const Seg& sg = segs[s];
         uint32_t tiles = (sg.size + LG_TILE - 1) / LG_TILE;
@@ -210,6 +211,8 @@ inline bool plan_sp(const std::vector<Seg>& segs, uint32_t target, const SpBufs&
         si.nb = nb;
         si.hist_base = hist_off;
         si.bst_base = s * (LG_NBMAX + 1);
+        si.bk_base = nbk;
+        nbk += 2 * nb - 1;
         h_info[s] = si;
         if (ntiles + tiles > B.cap_tiles) return false;
         for (uint32_t t = 0; t < tiles; ++t) {
@@ -221,6 +224,7 @@ inline bool plan_sp(const std::vector<Seg>& segs, uint32_t target, const SpBufs&
         if (hist_off > B.cap_hist) return false;
     }
     *out_ntiles = ntiles;
+    if (out_nbuckets) *out_nbuckets = nbk;
     return true;
 }
 
@@ -238,6 +242,16 @@ inline sss_status launch_sp(sss_ctx* ctx, const SpBufs& B, uint32_t ns, uint32_t
                        (const LgSegInfo*)B.info, (const uint32_t*)B.hist, (const uint32_t*)B.bst,
                        (const uint32_t*)B.rankinfo, K, V, tK, tV, ctx->d_err));
     return SSS_OK;
+}
+
+// segment of flat bucket g: last segment with bk_base <= g
+__device__ __forceinline__ uint32_t segment_of_bucket(const LgSegInfo* info, uint32_t ns, uint32_t g) {
+    uint32_t a = 0, c = ns;
+    while (a + 1 < c) {
+        uint32_t mid = (a + c) >> 1;
+        if (info[mid].bk_base <= g) a = mid; else c = mid;
+    }
+    return a;
 }
 
 }  // namespace

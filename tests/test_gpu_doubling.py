@@ -18,10 +18,10 @@ def sss():
     return m
 
 
-def run_gpu(ss, p, kmin, kmax, seed, use_runs):
+def run_gpu(ss, p, kmin, kmax, seed, use_runs, sort_dedupe=False):
     m = sss()
     chars, offs, lens = m.to_device(ss)
-    prm = m.params(kmin=kmin, kmax=kmax, hash_seed=seed)
+    prm = m.params(kmin=kmin, kmax=kmax, hash_seed=seed, flags=m.SSS_FLAG_DEDUPE_SORT if sort_dedupe else 0)
     if use_runs:
         rp, rl = m.sss_local_sort(chars, offs, lens, p)
         a = m.sss_dist_prefix(chars, offs, lens, rp, rl, p, prm)
@@ -36,9 +36,11 @@ def check(ss, p=1, kmin=0, kmax=None, seed=0):
         kmax = oracle.default_kmax(ss)
     want = oracle.doubling(ss, kmin, kmax, seed)
     for use_runs in (False, True):
-        got = run_gpu(ss, p, kmin, kmax, seed, use_runs)
-        bad = np.flatnonzero(got != want)
-        assert bad.size == 0, f"use_runs={use_runs}: approx differs at {bad[:5]} got {got[bad[:5]]} want {want[bad[:5]]}"
+        for sort_dedupe in (False, True):
+            got = run_gpu(ss, p, kmin, kmax, seed, use_runs, sort_dedupe)
+            bad = np.flatnonzero(got != want)
+            assert bad.size == 0, (f"use_runs={use_runs} sort_dedupe={sort_dedupe}: approx differs at {bad[:5]} "
+                                   f"got {got[bad[:5]]} want {want[bad[:5]]}")
 
 
 def test_handworked_example():
