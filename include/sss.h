@@ -28,7 +28,7 @@
  *    first use and grown when a larger problem arrives, or supplied by the caller
  *    with sss_set_workspace().
  *  - A context is not thread-safe; use one context per host thread.
- *  - Limits: n < 2^32 - 1, p <= 4096, string lengths < 2^31.
+ *  - Limits: n < 2^32 - 1, 1 <= p <= 1024, string lengths < 2^31.
  */
 #ifndef SSS_H
 #define SSS_H
@@ -60,6 +60,9 @@ typedef enum sss_status {
 #define SSS_FLAG_DEDUPE_SORT 0x8u /* doubling: detect duplicate keys by sorting
                                   them (bucketed shared-memory sorts) instead of
                                   the exact hash table */
+#define SSS_FLAG_MERGE_TREE 0x10u /* merge: pairwise LCP-merge tree over whole
+                                  buckets instead of second-level sub-buckets
+                                  merged inside one CTA each */
 
 typedef struct sss_params {
     uint32_t kmin;      /* first doubling round: prefix length 2^kmin (default 0) */

@@ -252,7 +252,7 @@ static sss_status check_common(sss_ctx* ctx, const uint8_t* chars, const uint64_
                                uint32_t n, uint32_t p) {
     if (!ctx) return SSS_ERR_INVALID_ARG;
     if (n == 0xFFFFFFFFu) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "n must be < 2^32 - 1");
-    if (p == 0 || p > 4096) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "p must be in 1..4096");
+    if (p == 0 || p > 1024) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "p must be in 1..1024");
     if (n > 0 && (!offs || !lens)) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "offsets/lengths must be non-NULL");
     if (n > 0 && !chars) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "chars must be non-NULL");
     return SSS_OK;
@@ -372,7 +372,8 @@ sss_status sss_lcp_merge(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, c
     size_t need = need_merge(n, p, prm.v, tot);
     char* ws;
     SSS_TRY(sss_workspace(ctx, need, &ws));
-    return impl_merge(ctx, ws, need, in, trunc, run_perm, run_lcp, p, prm.v, prm.merge_ms, tot, out_perm, out_lcp);
+    return impl_merge(ctx, ws, need, in, trunc, run_perm, run_lcp, p, prm.v, prm.merge_ms, prm.flags, tot, out_perm,
+                      out_lcp);
 }
 
 sss_status sss_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,
@@ -417,8 +418,8 @@ sss_status sss_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const 
         SSS_TRY(impl_dist_prefix(ctx, sa, in, run_perm, run_lcp, p, prm, approx));
         trunc = approx;
     }
-    SSS_TRY(impl_merge(ctx, stage, stage_bytes, in, trunc, run_perm, run_lcp, p, prm.v, prm.merge_ms, total_len,
-                       out_perm, out_lcp));
+    SSS_TRY(impl_merge(ctx, stage, stage_bytes, in, trunc, run_perm, run_lcp, p, prm.v, prm.merge_ms, prm.flags,
+                       total_len, out_perm, out_lcp));
     if (out_dist) SSS_TRY(impl_dist(ctx, lengths, n, out_perm, out_lcp, out_dist));
     if (out_approx)
         SSS_CUDA(cudaMemcpyAsync(out_approx, trunc ? trunc : lengths, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice,

@@ -156,6 +156,14 @@ sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p,
                            uint32_t* perm, uint32_t* lcp);
 size_t need_local_sort(uint32_t n, uint32_t p, const sss_params& prm);
 
+// Finish segments of positions whose strings share their first `depth`
+// characters (stage A's CTA finisher): perm[start..start+size) is sorted by the
+// strings (lengths from in.lens, ties by index) and lcp is set inside each segment.
+sss_status impl_finish_segments(sss_ctx* ctx, const Seg* tiny, uint32_t ntiny, const Seg* med, uint32_t nmed,
+                                const StrIn& in, uint32_t* perm, uint32_t* lcp);
+uint32_t finish_cap_tiny();
+uint32_t finish_cap_med();
+
 size_t need_dist_prefix(uint32_t n);
 sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& in, const uint32_t* run_perm,
                             const uint32_t* run_lcp, uint32_t p, const sss_params& prm, uint32_t* approx);
@@ -166,7 +174,7 @@ sss_status impl_partition(sss_ctx* ctx, Arena& ar, const StrIn& in, const uint32
 size_t need_merge(uint32_t n, uint32_t p, uint32_t v, uint64_t nrecchars);
 sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, const uint32_t* trunc,
                       const uint32_t* run_perm, const uint32_t* run_lcp, uint32_t p, uint32_t v, uint32_t ms,
-                      uint64_t nrecchars, uint32_t* out_perm, uint32_t* out_lcp);
+                      uint32_t flags, uint64_t nrecchars, uint32_t* out_perm, uint32_t* out_lcp);
 sss_status impl_sum_tlen(sss_ctx* ctx, const StrIn& in, const uint32_t* trunc, uint64_t* out);
 
 sss_status impl_dist(sss_ctx* ctx, const uint32_t* lens, uint32_t n, const uint32_t* perm, const uint32_t* lcp,

@@ -421,13 +421,7 @@ size_t need_local_sort(uint32_t n, uint32_t p, const sss_params& prm) {
 
 static bool g_attr_done[64];
 
-sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p, const sss_params& prm,
-                           uint32_t* perm, uint32_t* lcp) {
-    (void)prm;
-    const uint32_t n = in.n;
-    if (n == 0) return SSS_OK;
-    LsBufs B;
-    carve_ls(ar, n, p, B);
+static sss_status set_ls_attributes(sss_ctx* ctx) {
     if (!g_attr_done[ctx->device & 63]) {
         SSS_CUDA(cudaFuncSetAttribute(k_finish<MED_T, MED_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)finish_smem(MED_CAP)));
@@ -437,6 +431,17 @@ sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p,
                                       (int)(BK_CAP * (8 + 8 + 4 + 4))));
         g_attr_done[ctx->device & 63] = true;
     }
+    return SSS_OK;
+}
+
+sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p, const sss_params& prm,
+                           uint32_t* perm, uint32_t* lcp) {
+    (void)prm;
+    const uint32_t n = in.n;
+    if (n == 0) return SSS_OK;
+    LsBufs B;
+    carve_ls(ar, n, p, B);
+    SSS_TRY(set_ls_attributes(ctx));
     SSS_TRY(sss_launch(ctx, "ls_init", k_init_perm, dim3((n + 255) / 256), dim3(256), 0, perm, lcp, n));
 
     // initial segments: the partitions
@@ -515,6 +520,19 @@ sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p,
     }
     return SSS_OK;
 }
+
+sss_status impl_finish_segments(sss_ctx* ctx, const Seg* tiny, uint32_t ntiny, const Seg* med, uint32_t nmed,
+                                const StrIn& in, uint32_t* perm, uint32_t* lcp) {
+    SSS_TRY(set_ls_attributes(ctx));
+    SSS_TRY(sss_launch(ctx, "ls_finish_tiny", k_finish<TINY_T, TINY_CAP>, dim3(ntiny), dim3(TINY_T),
+                       finish_smem(TINY_CAP), tiny, in.chars, in.offs, in.lens, perm, lcp, ctx->d_err));
+    SSS_TRY(sss_launch(ctx, "ls_finish_cta", k_finish<MED_T, MED_CAP>, dim3(nmed), dim3(MED_T),
+                       finish_smem(MED_CAP), med, in.chars, in.offs, in.lens, perm, lcp, ctx->d_err));
+    return SSS_OK;
+}
+
+uint32_t finish_cap_tiny() { return TINY_CAP; }
+uint32_t finish_cap_med() { return MED_CAP; }
 
 sss_status impl_dist(sss_ctx* ctx, const uint32_t* lens, uint32_t n, const uint32_t* perm, const uint32_t* lcp,
                      uint32_t* dist) {

@@ -523,6 +523,325 @@ __global__ void k_d_out(const Recs R, const uint32_t* __restrict__ Rfin, const u
     out_lcp[q] = Hfin[q];
 }
 
+// ---------------------------------------------------------------------------
+// Stage D, second level (the multi-level idea of Section 3 on one GPU): every
+// level-1 bucket is split again by regular sampling into sub-buckets of at most
+// D2_CAP strings, and each sub-bucket's p slices are merged inside one CTA.
+constexpr uint32_t D2_CAP = 2048;  // strings merged by one CTA (<= the stage-A CTA finisher)
+constexpr uint32_t D2_OVS = 16;    // samples per sub-bucket
+constexpr int D2_T = 512;
+
+struct BucketInfo {
+    uint32_t sbase;  // first sorted-sample index of the bucket
+    uint32_t nsmp;   // samples drawn in the bucket
+    uint32_t sb0;    // first global sub-bucket
+    uint32_t nsb;    // sub-buckets
+    uint32_t ss0;    // first global sub-splitter
+    uint32_t fref;   // the bucket's lower splitter (MINF: none)
+    uint32_t pad[2];
+};
+
+__device__ __forceinline__ uint32_t last_le(const uint32_t* a, uint32_t n, uint32_t g, uint32_t stride, uint32_t off) {
+    // last index i < n with a[i*stride+off] <= g (a non-decreasing, a[off] <= g)
+    uint32_t lo = 0, hi = n;
+    while (lo + 1 < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (a[mid * stride + off] <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_d2_samples(const uint32_t* __restrict__ run_perm, Strs S, const uint32_t* __restrict__ pso,
+                             const uint32_t* __restrict__ pstart, uint32_t npieces, uint32_t S2, uint32_t step,
+                             uint32_t* __restrict__ smp, uint64_t* __restrict__ s_offs,
+                             uint32_t* __restrict__ s_lens) {
+    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= S2) return;
+    // last piece with pso <= g (pso has npieces+1 entries, pso[npieces] = S2)
+    uint32_t lo = 0, hi = npieces;
+    while (lo + 1 < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (pso[mid] <= g) lo = mid; else hi = mid;
+    }
+    uint32_t k = g - pso[lo];
+    uint32_t q = pstart[lo] + (k + 1) * step - 1;
+    uint32_t s = run_perm[q];
+    smp[g] = s;
+    s_offs[g] = S.offs[s];
+    s_lens[g] = tlen(S, s);
+}
+
+__global__ void k_d2_subspl(const BucketInfo* __restrict__ bi, uint32_t p, uint32_t nss,
+                            const uint32_t* __restrict__ smp, const uint32_t* __restrict__ sperm,
+                            uint32_t* __restrict__ subspl) {
+    uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= nss) return;
+    uint32_t j = last_le(&bi[0].ss0, p, m, sizeof(BucketInfo) / 4, 0);
+    // skip buckets without sub-splitters that share ss0
+    while (j + 1 < p && bi[j + 1].ss0 <= m) ++j;
+    uint32_t k = m - bi[j].ss0;
+    subspl[m] = smp[sperm[bi[j].sbase + D2_OVS * (k + 1) - 1]];
+}
+
+// sb[m*p+i] = number of strings of piece (bucket of m, i) that are <= subspl[m]
+__global__ void k_d2_bounds(const uint32_t* __restrict__ run_perm, Strs S, const BucketInfo* __restrict__ bi,
+                            uint32_t p, uint32_t nss, const uint32_t* __restrict__ pstart,
+                            const uint32_t* __restrict__ psz, const uint32_t* __restrict__ subspl,
+                            uint32_t* __restrict__ sb) {
+    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nss * p) return;
+    uint32_t m = g / p, i = g % p;
+    uint32_t j = last_le(&bi[0].ss0, p, m, sizeof(BucketInfo) / 4, 0);
+    while (j + 1 < p && bi[j + 1].ss0 <= m) ++j;
+    uint32_t f = subspl[m];
+    const uint8_t* fs = S.chars + S.offs[f];
+    uint32_t fl = tlen(S, f);
+    uint32_t q0 = pstart[j * p + i];
+    uint32_t a = 0, b = psz[j * p + i], la = 0, lb = 0;
+    while (a < b) {
+        uint32_t mid = (a + b) >> 1;
+        uint32_t e = run_perm[q0 + mid];
+        uint32_t d = la < lb ? la : lb, l;
+        int c = cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, d, &l);
+        if (c <= 0) {
+            a = mid + 1;
+            la = l;
+        } else {
+            b = mid;
+            lb = l;
+        }
+    }
+    sb[g] = a;
+}
+
+__device__ __forceinline__ uint32_t bucket_of_sub(const BucketInfo* bi, uint32_t p, uint32_t b) {
+    uint32_t j = last_le(&bi[0].sb0, p, b, sizeof(BucketInfo) / 4, 0);
+    while (j + 1 < p && bi[j + 1].sb0 <= b) ++j;
+    return j;
+}
+
+// slice (sub-bucket b, piece i): [lo, hi) within the piece
+__device__ __forceinline__ void slice_range(const BucketInfo& B, uint32_t b, uint32_t i, uint32_t p,
+                                            const uint32_t* sb, const uint32_t* psz, uint32_t j, uint32_t* lo,
+                                            uint32_t* hi) {
+    uint32_t k = b - B.sb0;
+    *lo = k == 0 ? 0u : sb[(B.ss0 + k - 1) * p + i];
+    *hi = k + 1 == B.nsb ? psz[j * p + i] : sb[(B.ss0 + k) * p + i];
+}
+
+__global__ void k_d2_slices(const BucketInfo* __restrict__ bi, uint32_t p, uint32_t nsb,
+                            const uint32_t* __restrict__ sb, const uint32_t* __restrict__ psz,
+                            uint32_t* __restrict__ ssz) {
+    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nsb * p) return;
+    uint32_t b = g / p, i = g % p;
+    uint32_t j = bucket_of_sub(bi, p, b);
+    uint32_t lo, hi;
+    slice_range(bi[j], b, i, p, sb, psz, j, &lo, &hi);
+    ssz[g] = hi > lo ? hi - lo : 0u;
+}
+
+__global__ void k_d2_oversized(const uint64_t* __restrict__ soff, uint32_t p, uint32_t nsb,
+                               uint32_t* __restrict__ list, uint32_t* __restrict__ cnt) {
+    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nsb) return;
+    if (soff[(uint64_t)(b + 1) * p] - soff[(uint64_t)b * p] > D2_CAP) list[atomicAdd(cnt, 1u)] = b;
+}
+
+// D1 at the second level: run position q -> record of its sub-bucket slice.  The
+// first string of every slice keeps all its characters (h = 0).
+__global__ void k_d2_records(const uint32_t* __restrict__ run_perm, const uint32_t* __restrict__ run_lcp, uint32_t n,
+                             uint32_t p, Strs S, const uint32_t* __restrict__ bounds,
+                             const BucketInfo* __restrict__ bi, const uint32_t* __restrict__ sb,
+                             const uint64_t* __restrict__ soff, Recs R, uint32_t* __restrict__ clen, unsigned* err) {
+    uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    uint32_t i = (uint32_t)(((uint64_t)(q + 1) * p + n - 1) / n - 1);
+    uint32_t t = q - part_lo(n, p, i);
+    const uint32_t* b1 = bounds + (size_t)i * (p + 1);
+    uint32_t a = 0, c = p;
+    while (a + 1 < c) {
+        uint32_t mid = (a + c) >> 1;
+        if (b1[mid] <= t) a = mid; else c = mid;
+    }
+    const uint32_t j = a;
+    const uint32_t tp = t - b1[j];
+    const BucketInfo B = bi[j];
+    // sub-bucket: number of sub-splitters of bucket j whose bound is <= tp
+    uint32_t lo = 0, hi = B.nsb - 1;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (sb[(B.ss0 + mid) * p + i] <= tp) lo = mid + 1; else hi = mid;
+    }
+    const uint32_t k = lo;
+    const uint32_t slo = k == 0 ? 0u : sb[(B.ss0 + k - 1) * p + i];
+    const uint64_t r64 = soff[(uint64_t)(B.sb0 + k) * p + i] + (tp - slo);
+    if (r64 >= n) {
+        atomicOr(err, ERRBIT_OVERFLOW);
+        return;
+    }
+    const uint32_t r = (uint32_t)r64;
+    uint32_t s = run_perm[q];
+    uint32_t tl = tlen(S, s);
+    uint32_t h = 0;
+    if (tp > slo) {
+        uint32_t prev_tl = tlen(S, run_perm[q - 1]);
+        h = run_lcp[q];
+        h = h < tl ? h : tl;
+        h = h < prev_tl ? h : prev_tl;
+    }
+    R.idx[r] = s;
+    R.h[r] = h;
+    R.tl[r] = tl;
+    clen[r] = tl - h;
+}
+
+// the lower reference string of sub-bucket b (MINF: the empty string)
+__device__ __forceinline__ uint32_t sub_ref(const BucketInfo& B, uint32_t b, const uint32_t* subspl) {
+    uint32_t k = b - B.sb0;
+    return k == 0 ? B.fref : subspl[B.ss0 + k - 1];
+}
+
+// Decode each slice once, in order: r = LCP with the sub-bucket's reference
+// string (every string of the sub-bucket is greater than it), key = the 8
+// characters at depth r.  Uses only the stored LCPs and record characters:
+// r(e) = min(r(prev), h(e)); characters below h(e) are the predecessor's.
+__global__ void k_d2_decode(Strs S, Recs R, const BucketInfo* __restrict__ bi, uint32_t p, uint32_t nsb,
+                            const uint64_t* __restrict__ soff, const uint32_t* __restrict__ subspl,
+                            uint32_t* __restrict__ rr, uint64_t* __restrict__ rk) {
+    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nsb * p) return;
+    uint32_t b = g / p;
+    uint32_t s0 = (uint32_t)soff[g], s1 = (uint32_t)soff[g + 1];
+    if (s0 >= s1) return;
+    uint32_t j = bucket_of_sub(bi, p, b);
+    uint32_t ref = sub_ref(bi[j], b, subspl);
+    uint32_t r = 0;
+    if (ref != MINF) {
+        uint32_t l;
+        uint32_t e = R.idx[s0];
+        cmp_from(S.chars + S.offs[ref], tlen(S, ref), S.chars + S.offs[e], tlen(S, e), 0, &l);
+        r = l;
+    }
+    uint64_t key = load_word_be(R.chars + R.base[s0], R.tl[s0], r);
+    rr[s0] = r;
+    rk[s0] = key;
+    for (uint32_t u = s0 + 1; u < s1; ++u) {
+        uint32_t h = R.h[u];
+        if (h <= r) {
+            r = h;
+            key = load_word_be(R.chars + R.base[u], R.tl[u], r);
+        } else if (h - r < 8) {
+            uint32_t d = h - r;
+            key = (key & (~0ull << (64 - 8 * d))) | (load_word_be(R.chars + R.base[u], R.tl[u], h) >> (8 * d));
+        }
+        rr[u] = r;
+        rk[u] = key;
+    }
+}
+
+// One CTA per sub-bucket: merge its slices by (LCP with the reference desc,
+// next 8 characters, run order).  A run of equal keys whose strings go on
+// shares its first r+8 characters: it becomes a segment for the CTA finisher,
+// which orders it by the characters from r+8 on (equal strings by index).
+struct TieLists {
+    Seg* tiny;
+    Seg* med;
+    uint32_t* cnt;  // [0] tiny, [1] med
+    uint32_t cap_tiny, cap_med, lim_tiny;
+};
+
+__global__ void __launch_bounds__(D2_T) k_d2_cta(Strs S, Recs R, const uint64_t* __restrict__ soff, uint32_t p,
+                                                 const uint32_t* __restrict__ rr, const uint64_t* __restrict__ rk,
+                                                 uint32_t* __restrict__ out_perm, uint32_t* __restrict__ out_lcp,
+                                                 TieLists T, unsigned* err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* sHi = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* sLo = sHi + D2_CAP;
+    const uint32_t b = blockIdx.x;
+    const uint32_t base = (uint32_t)soff[(uint64_t)b * p];
+    const uint32_t m = (uint32_t)soff[(uint64_t)(b + 1) * p] - base;
+    if (m == 0 || m > D2_CAP) return;
+    for (uint32_t u = threadIdx.x; u < m; u += D2_T) {
+        uint32_t r = rr[base + u];
+        uint64_t k = rk[base + u];
+        sHi[u] = ((uint64_t)(~r) << 32) | (k >> 32);
+        sLo[u] = (k << 32) | u;
+    }
+    __syncthreads();
+    bitonic_sort128<D2_T>(sHi, sLo, m);
+    for (uint32_t t = threadIdx.x; t < m; t += D2_T) {
+        uint32_t u = (uint32_t)sLo[t];
+        out_perm[base + t] = R.idx[base + u];
+        uint32_t rb = ~(uint32_t)(sHi[t] >> 32);
+        uint64_t kb = ((sHi[t] & 0xFFFFFFFFull) << 32) | (sLo[t] >> 32);
+        bool tie_next = t + 1 < m && sHi[t + 1] == sHi[t] && (sLo[t + 1] >> 32) == (sLo[t] >> 32);
+        bool tie_prev = false;
+        if (t > 0) {
+            uint32_t ra = ~(uint32_t)(sHi[t - 1] >> 32);
+            uint64_t ka = ((sHi[t - 1] & 0xFFFFFFFFull) << 32) | (sLo[t - 1] >> 32);
+            tie_prev = ra == rb && ka == kb;
+            uint32_t l;
+            if (ra != rb) l = ra < rb ? ra : rb;
+            else if (ka != kb) l = ra + word_lcp(ka, kb);
+            else l = word_has_zero(kb) ? R.tl[base + u] : rb + 8;  // equal strings / set by the finisher
+            out_lcp[base + t] = l;  // t == 0: overwritten by k_d2_seams
+        }
+        if (tie_next && !tie_prev && !word_has_zero(kb)) {
+            uint32_t t1 = t + 1;
+            while (t1 < m && sHi[t1] == sHi[t] && (sLo[t1] >> 32) == (sLo[t] >> 32)) ++t1;
+            Seg sg{base + t, t1 - t, rb + 8, 0};
+            if (sg.size <= T.lim_tiny) {
+                uint32_t i = atomicAdd(&T.cnt[0], 1u);
+                if (i < T.cap_tiny) T.tiny[i] = sg; else atomicOr(err, ERRBIT_OVERFLOW);
+            } else {
+                uint32_t i = atomicAdd(&T.cnt[1], 1u);
+                if (i < T.cap_med) T.med[i] = sg; else atomicOr(err, ERRBIT_OVERFLOW);
+            }
+        }
+    }
+}
+
+// LCP across sub-bucket boundaries (all outputs written)
+__global__ void k_d2_seams(Strs S, const uint64_t* __restrict__ soff, uint32_t p, uint32_t nsb,
+                           const uint32_t* __restrict__ out_perm, uint32_t* __restrict__ out_lcp) {
+    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nsb) return;
+    uint32_t s0 = (uint32_t)soff[(uint64_t)b * p], s1 = (uint32_t)soff[(uint64_t)(b + 1) * p];
+    if (s1 == s0) return;
+    uint32_t l = 0;
+    if (s0 > 0) cmp_str_from(S, out_perm[s0 - 1], out_perm[s0], 0, &l);
+    out_lcp[s0] = l;
+}
+
+// fallback for oversized sub-buckets: the pairwise merge tree over their slices
+__global__ void k_d2_fb_init(const uint64_t* __restrict__ soff, uint32_t p, const uint32_t* __restrict__ list,
+                             uint32_t cnt, const uint32_t* __restrict__ rec_h, uint32_t* __restrict__ RA,
+                             uint32_t* __restrict__ HA) {
+    for (uint32_t w = blockIdx.x; w < cnt; w += gridDim.x) {
+        uint32_t b = list[w];
+        uint32_t s0 = (uint32_t)soff[(uint64_t)b * p], s1 = (uint32_t)soff[(uint64_t)(b + 1) * p];
+        for (uint32_t u = s0 + threadIdx.x; u < s1; u += blockDim.x) {
+            RA[u] = u;
+            HA[u] = rec_h[u];
+        }
+    }
+}
+
+__global__ void k_d2_fb_out(const uint64_t* __restrict__ soff, uint32_t p, const uint32_t* __restrict__ list,
+                            uint32_t cnt, const uint32_t* __restrict__ rec_idx, const uint32_t* __restrict__ RA,
+                            const uint32_t* __restrict__ HA, uint32_t* __restrict__ out_perm,
+                            uint32_t* __restrict__ out_lcp) {
+    for (uint32_t w = blockIdx.x; w < cnt; w += gridDim.x) {
+        uint32_t b = list[w];
+        uint32_t s0 = (uint32_t)soff[(uint64_t)b * p], s1 = (uint32_t)soff[(uint64_t)(b + 1) * p];
+        for (uint32_t u = s0 + threadIdx.x; u < s1; u += blockDim.x) {
+            out_perm[u] = rec_idx[RA[u]];
+            out_lcp[u] = HA[u];
+        }
+    }
+}
+
 struct MgBufs {
     uint32_t* smp;
     uint64_t* s_offs;
@@ -545,6 +864,28 @@ struct MgBufs {
     uint32_t* sl1;
     uint32_t* cnt;
     Arena sub;  // work memory for sorting the samples
+    // second level
+    uint32_t cap_s2, cap_nsb;
+    uint32_t* smp2;
+    uint64_t* s2offs;
+    uint32_t* s2lens;
+    uint32_t* s2perm;
+    uint32_t* s2lcp;
+    uint32_t* subspl;
+    uint32_t* sb;
+    uint32_t* ssz;
+    uint64_t* soff;
+    uint32_t* olist;
+    BucketInfo* binfo;
+    uint32_t* pstart;
+    uint32_t* psz;
+    uint32_t* pso;
+    uint32_t* rr;
+    uint64_t* rk;
+    Seg* tie_tiny;
+    Seg* tie_med;
+    Arena sub2;  // work memory for sorting the second-level samples
+    uint32_t max_pairs;
 };
 
 void carve_mg_small(Arena& ar, uint32_t n, uint32_t p, uint32_t v, MgBufs& b) {
@@ -563,6 +904,8 @@ void carve_mg_small(Arena& ar, uint32_t n, uint32_t p, uint32_t v, MgBufs& b) {
     (void)n;
 }
 
+constexpr uint32_t MAX_P_TWO_LEVEL = 256;
+
 void carve_mg(Arena& ar, uint32_t n, uint32_t p, uint32_t v, uint64_t nrecchars, MgBufs& b) {
     const uint32_t MS = 8;  // smallest spacing: sample arrays sized for it
     carve_mg_small(ar, n, p, v, b);
@@ -570,7 +913,6 @@ void carve_mg(Arena& ar, uint32_t n, uint32_t p, uint32_t v, uint64_t nrecchars,
     b.bstart = ar.take<uint32_t>(p + 1);
     b.clen = ar.take<uint32_t>(n);
     b.coff = ar.take<uint64_t>(n + 1);
-    b.btot = ar.take<uint64_t>(n / 4096 + 2);
     b.R.idx = ar.take<uint32_t>(n);
     b.R.h = ar.take<uint32_t>(n);
     b.R.tl = ar.take<uint32_t>(n);
@@ -580,12 +922,45 @@ void carve_mg(Arena& ar, uint32_t n, uint32_t p, uint32_t v, uint64_t nrecchars,
     b.RA[1] = ar.take<uint32_t>(n);
     b.HA[0] = ar.take<uint32_t>(n);
     b.HA[1] = ar.take<uint32_t>(n);
-    uint32_t maxpairs = p * ((p + 1) / 2) + 1;
-    b.pairs = ar.take<Pair>((size_t)p * p + 16);  // every level's pairs (< p per bucket in total)
-    uint32_t maxs = n / MS + maxpairs * 2 + 2;
+    // second level (sized for the smallest sample step, 16)
+    b.cap_s2 = n / 16 + 16;
+    b.cap_nsb = b.cap_s2 / D2_OVS + p + 1;
+    uint32_t pp = p <= MAX_P_TWO_LEVEL ? p : 1;
+    size_t nslices = (size_t)b.cap_nsb * pp;
+    // pairwise-tree pairs over all levels: the level-1 tree has fewer than p*p + p
+    // (every level halves the runs of a bucket, and a pair needs a non-empty run);
+    // the oversized-sub-bucket tree fewer than its slices
+    uint32_t lg = 1;
+    while ((1u << lg) < p) ++lg;
+    size_t tree1 = std::min<size_t>((size_t)p * p + p, (size_t)n * (lg + 1));
+    b.max_pairs = (uint32_t)(std::max<size_t>(tree1, (p <= MAX_P_TWO_LEVEL ? nslices : 0)) + 64);
+    b.pairs = ar.take<Pair>(b.max_pairs);
+    uint32_t maxs = n / MS + b.max_pairs * 2 + 2;
     b.srank = ar.take<uint32_t>(maxs);
     b.sl0 = ar.take<uint32_t>(maxs);
     b.sl1 = ar.take<uint32_t>(maxs);
+    b.btot = ar.take<uint64_t>((std::max<size_t>(n, nslices) + 1) / 4096 + 4);
+    b.smp2 = ar.take<uint32_t>(b.cap_s2);
+    b.s2offs = ar.take<uint64_t>(b.cap_s2);
+    b.s2lens = ar.take<uint32_t>(b.cap_s2);
+    b.s2perm = ar.take<uint32_t>(b.cap_s2);
+    b.s2lcp = ar.take<uint32_t>(b.cap_s2);
+    b.subspl = ar.take<uint32_t>(b.cap_nsb);
+    b.sb = ar.take<uint32_t>(nslices);
+    b.ssz = ar.take<uint32_t>(nslices);
+    b.soff = ar.take<uint64_t>(nslices + 1);
+    b.olist = ar.take<uint32_t>(b.cap_nsb);
+    b.binfo = ar.take<BucketInfo>(p);
+    b.pstart = ar.take<uint32_t>((size_t)p * p);
+    b.psz = ar.take<uint32_t>((size_t)p * p);
+    b.pso = ar.take<uint32_t>((size_t)p * p + 1);
+    b.rr = ar.take<uint32_t>(n);
+    b.rk = ar.take<uint64_t>(n);
+    b.tie_tiny = ar.take<Seg>(n / 2 + 2);
+    b.tie_med = ar.take<Seg>(n / 65 + 2);
+    size_t sub2 = need_local_sort(b.cap_s2, 1, sss_params{});
+    char* base2 = ar.take<char>(sub2);
+    b.sub2 = Arena{base2, sub2, 0};
 }
 
 __global__ void __launch_bounds__(256) k_sum_tlen(Strs S, uint32_t n, unsigned long long* out) {
@@ -661,75 +1036,36 @@ size_t need_merge(uint32_t n, uint32_t p, uint32_t v, uint64_t nrecchars) {
 
 // Stages C and D.  The record-character bound (sum of truncated lengths) is
 // needed to size the work memory, so it is computed first by the caller.
-sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, const uint32_t* trunc,
-                      const uint32_t* run_perm, const uint32_t* run_lcp, uint32_t p, uint32_t v, uint32_t ms_param,
-                      uint64_t nrecchars, uint32_t* out_perm, uint32_t* out_lcp) {
-    uint32_t MS = MS_DEFAULT;
-    if (ms_param >= 8 && ms_param <= 1024 && (ms_param & (ms_param - 1)) == 0) MS = ms_param;
-    const uint32_t n = in.n;
-    Arena ar{ws, ws_bytes, 0};
-    MgBufs b;
-    carve_mg(ar, n, p, v, nrecchars, b);
-    Strs S{in.chars, in.offs, in.lens, trunc};
-    SSS_TRY(run_partition(ctx, in, trunc, run_perm, p, v, b));
+// exclusive scan of count u32 values into u64 offsets (out[count] is not written)
+static sss_status scan_u32_u64(sss_ctx* ctx, const uint32_t* in, uint32_t count, uint64_t* out, uint64_t* btot) {
+    if (count == 0) return SSS_OK;
+    uint32_t nblk = (count + 4095) / 4096;
+    SSS_TRY(sss_launch(ctx, "d_scan", k_scan_blocks, dim3(nblk), dim3(1024), 0, in, count, out, btot));
+    SSS_TRY(sss_launch(ctx, "d_scan_tot", k_scan_totals, dim3(1), dim3(1024), 0, btot, nblk));
+    SSS_TRY(sss_launch(ctx, "d_scan_add", k_scan_add, dim3((count + 255) / 256), dim3(256), 0, out, count,
+                       (const uint64_t*)btot));
+    return SSS_OK;
+}
 
-    // bounds to the host: piece sizes, bucket starts, piece offsets
-    void* pin;
-    size_t pin_need = sizeof(uint32_t) * ((size_t)p * (p + 1) + (size_t)p * p + p + 1) + sizeof(Pair) * (p * p + 16);
-    SSS_TRY(sss_pinned(ctx, pin_need + 256, &pin));
-    uint32_t* hb = static_cast<uint32_t*>(pin);
-    uint32_t* hpo = hb + (size_t)p * (p + 1);
-    uint32_t* hbs = hpo + (size_t)p * p;
-    Pair* hpairs = reinterpret_cast<Pair*>(reinterpret_cast<uintptr_t>(hbs + p + 1 + 15) & ~uintptr_t(15));
-    SSS_CUDA(cudaMemcpyAsync(hb, b.bounds, sizeof(uint32_t) * p * (p + 1), cudaMemcpyDeviceToHost, ctx->stream));
-    SSS_CUDA(cudaStreamSynchronize(ctx->stream));
-    std::vector<std::vector<uint32_t>> psz(p, std::vector<uint32_t>(p));  // psz[j][i]
-    uint32_t acc = 0;
-    for (uint32_t j = 0; j < p; ++j) {
-        hbs[j] = acc;
-        for (uint32_t i = 0; i < p; ++i) {
-            uint32_t sz = hb[(size_t)i * (p + 1) + j + 1] - hb[(size_t)i * (p + 1) + j];
-            psz[j][i] = sz;
-            hpo[(size_t)j * p + i] = acc;
-            acc += sz;
-        }
-    }
-    hbs[p] = acc;
-    if (acc != n) return sss_fail(ctx, SSS_ERR_CUDA, "merge: bucket bounds do not cover the input");
-    SSS_TRY(sss_upload(ctx, b.piece_off, hpo, sizeof(uint32_t) * p * p));
-    SSS_TRY(sss_upload(ctx, b.bstart, hbs, sizeof(uint32_t) * (p + 1)));
+// Pairwise merge tree over groups of runs: group g occupies [base_g, ...) with
+// run sizes sizes_g; every level's pairs are planned at once.
+struct TreePlan {
+    std::vector<Pair> pairs;
+    std::vector<uint32_t> first, np, ns;
+};
 
-    // D1: records and their characters
-    SSS_TRY(sss_launch(ctx, "d_records", k_d_records, dim3((n + 255) / 256), dim3(256), 0, run_perm, run_lcp, n, p, S,
-                       (const uint32_t*)b.bounds, (const uint32_t*)b.piece_off, b.R, b.clen, ctx->d_err));
-    uint32_t nblk = (n + 4095) / 4096;
-    SSS_TRY(sss_launch(ctx, "d_scan", k_scan_blocks, dim3(nblk), dim3(1024), 0, (const uint32_t*)b.clen, n, b.coff,
-                       b.btot));
-    SSS_TRY(sss_launch(ctx, "d_scan_tot", k_scan_totals, dim3(1), dim3(1024), 0, b.btot, nblk));
-    SSS_TRY(sss_launch(ctx, "d_scan_add", k_scan_add, dim3((n + 255) / 256), dim3(256), 0, b.coff, n,
-                       (const uint64_t*)b.btot));
-    SSS_TRY(sss_launch(ctx, "d_copy", k_d_copy, dim3((n + 127) / 128), dim3(128), 0, S, b.R, (const uint64_t*)b.coff,
-                       n));
-    SSS_TRY(sss_launch(ctx, "d_iota", k_iota, dim3((n + 255) / 256), dim3(256), 0, b.RA[0], n));
-    SSS_CUDA(cudaMemcpyAsync(b.HA[0], b.R.h, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-
-    // D2: pairwise merge levels; runs of bucket j at level 0 are its pieces.
-    // All levels' pair tables are planned on the host and uploaded at once.
-    std::vector<std::vector<uint32_t>> runs(p);  // run sizes per bucket
-    for (uint32_t j = 0; j < p; ++j) runs[j] = psz[j];
-    std::vector<Pair> all_pairs;
-    std::vector<uint32_t> lvl_first, lvl_np, lvl_ns;
+static void plan_tree(std::vector<std::pair<uint32_t, std::vector<uint32_t>>> groups, uint32_t MS, TreePlan& T) {
     for (;;) {
         bool more = false;
-        for (uint32_t j = 0; j < p; ++j) more |= runs[j].size() > 1;
+        for (auto& g : groups) more |= g.second.size() > 1;
         if (!more) break;
         uint32_t np = 0, ns = 0;
-        lvl_first.push_back((uint32_t)all_pairs.size());
-        for (uint32_t j = 0; j < p; ++j) {
-            uint32_t pos = hbs[j];
+        T.first.push_back((uint32_t)T.pairs.size());
+        for (auto& g : groups) {
+            uint32_t pos = g.first;
             std::vector<uint32_t> next;
-            for (size_t k = 0; k < runs[j].size(); k += 2) {
-                uint32_t na = runs[j][k], nb = k + 1 < runs[j].size() ? runs[j][k + 1] : 0;
+            for (size_t k = 0; k < g.second.size(); k += 2) {
+                uint32_t na = g.second[k], nb = k + 1 < g.second.size() ? g.second[k + 1] : 0;
                 if (na + nb > 0) {
                     Pair pr{};
                     pr.a0 = pos;
@@ -740,30 +1076,30 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
                     ns += (na + MS - 1) / MS;
                     pr.sb = ns;
                     ns += (nb + MS - 1) / MS;
-                    all_pairs.push_back(pr);
+                    T.pairs.push_back(pr);
                     ++np;
                 }
                 pos += na + nb;
                 next.push_back(na + nb);
             }
-            runs[j] = next;
+            g.second = next;
         }
-        lvl_np.push_back(np);
-        lvl_ns.push_back(ns);
+        T.np.push_back(np);
+        T.ns.push_back(ns);
     }
-    const uint32_t nlev = (uint32_t)lvl_np.size();
-    Pair* d_pairs = nullptr;
-    if (nlev > 0) {
-        // the pinned region after the bucket tables was reserved for the pairs
-        if (all_pairs.size() > (size_t)p * p + 16) return sss_fail(ctx, SSS_ERR_CUDA, "merge: pair table overflow");
-        std::copy(all_pairs.begin(), all_pairs.end(), hpairs);
-        d_pairs = b.pairs;
-        SSS_TRY(sss_upload(ctx, d_pairs, hpairs, sizeof(Pair) * all_pairs.size()));
-    }
-    int cur = 0;
+}
+
+static sss_status run_tree(sss_ctx* ctx, MgBufs& b, const Strs& S, const TreePlan& T, Pair* hpairs, int* cur_io,
+                           uint32_t MS) {
+    const uint32_t nlev = (uint32_t)T.np.size();
+    if (nlev == 0) return SSS_OK;
+    if (T.pairs.size() > b.max_pairs) return sss_fail(ctx, SSS_ERR_CUDA, "merge: pair table overflow");
+    std::copy(T.pairs.begin(), T.pairs.end(), hpairs);
+    SSS_TRY(sss_upload(ctx, b.pairs, hpairs, sizeof(Pair) * T.pairs.size()));
+    int cur = *cur_io;
     for (uint32_t lv = 0; lv < nlev; ++lv) {
-        const Pair* pr = d_pairs + lvl_first[lv];
-        uint32_t np = lvl_np[lv], ns = lvl_ns[lv];
+        const Pair* pr = b.pairs + T.first[lv];
+        uint32_t np = T.np[lv], ns = T.ns[lv];
         SSS_TRY(sss_launch(ctx, "d_search", k_d_search, dim3((ns + 127) / 128), dim3(128), 0, S, b.R,
                            (const uint32_t*)b.RA[cur], pr, np, ns, b.srank, b.sl0, b.sl1, MS));
         SSS_TRY(sss_launch(ctx, "d_merge", k_d_merge, dim3((ns + 127) / 128), dim3(128), 0, S, b.R,
@@ -772,12 +1108,211 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
                            MS));
         cur ^= 1;
     }
-    // D3
-    SSS_TRY(sss_launch(ctx, "d_seams", k_d_seams, dim3((p + 127) / 128), dim3(128), 0, S, b.R,
-                       (const uint32_t*)b.RA[cur], b.HA[cur], (const uint32_t*)b.bstart, p));
-    SSS_TRY(sss_launch(ctx, "d_out", k_d_out, dim3((n + 255) / 256), dim3(256), 0, b.R, (const uint32_t*)b.RA[cur],
-                       (const uint32_t*)b.HA[cur], n, out_perm, out_lcp));
+    *cur_io = cur;
     return SSS_OK;
+}
+
+static bool g_mg_attr[64];
+
+sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, const uint32_t* trunc,
+                      const uint32_t* run_perm, const uint32_t* run_lcp, uint32_t p, uint32_t v, uint32_t ms_param,
+                      uint32_t flags, uint64_t nrecchars, uint32_t* out_perm, uint32_t* out_lcp) {
+    uint32_t MS = MS_DEFAULT;
+    if (ms_param >= 8 && ms_param <= 1024 && (ms_param & (ms_param - 1)) == 0) MS = ms_param;
+    const uint32_t n = in.n;
+    if (p == 1) {  // one sorted run: it is the result
+        SSS_CUDA(cudaMemcpyAsync(out_perm, run_perm, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        SSS_CUDA(cudaMemcpyAsync(out_lcp, run_lcp, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        return SSS_OK;
+    }
+    if (!g_mg_attr[ctx->device & 63]) {
+        SSS_CUDA(cudaFuncSetAttribute(k_d2_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(D2_CAP * (8 + 8))));
+        g_mg_attr[ctx->device & 63] = true;
+    }
+    Arena ar{ws, ws_bytes, 0};
+    MgBufs b;
+    carve_mg(ar, n, p, v, nrecchars, b);
+    Strs S{in.chars, in.offs, in.lens, trunc};
+    SSS_TRY(run_partition(ctx, in, trunc, run_perm, p, v, b));
+    const bool two_level = p <= MAX_P_TWO_LEVEL && !(flags & SSS_FLAG_MERGE_TREE);
+
+    // level-1 bounds and splitters to the host
+    void* pin;
+    const size_t npieces = (size_t)p * p;
+    size_t pin_need = sizeof(uint32_t) * ((size_t)p * (p + 1) + p + 4 * npieces + 16) + sizeof(BucketInfo) * p +
+                      sizeof(Pair) * (b.max_pairs + 16) + 4096;
+    SSS_TRY(sss_pinned(ctx, pin_need, &pin));
+    uint32_t* hb = static_cast<uint32_t*>(pin);
+    uint32_t* hspl = hb + (size_t)p * (p + 1);
+    uint32_t* hpo = hspl + p;             // piece_off   [p*p]
+    uint32_t* hpst = hpo + npieces;       // pstart      [p*p]
+    uint32_t* hpsz = hpst + npieces;      // psz         [p*p]
+    uint32_t* hpso = hpsz + npieces;      // pso         [p*p+1]
+    uint32_t* hbs = hpso + npieces + 1;   // bstart      [p+1]
+    BucketInfo* hbi = reinterpret_cast<BucketInfo*>(reinterpret_cast<uintptr_t>(hbs + p + 1 + 15) & ~uintptr_t(15));
+    uint64_t* hn = reinterpret_cast<uint64_t*>(hbi + p);
+    uint32_t* hcnt = reinterpret_cast<uint32_t*>(hn + 2);
+    Pair* hpairs = reinterpret_cast<Pair*>(reinterpret_cast<uintptr_t>(hcnt + 8 + 15) & ~uintptr_t(15));
+    SSS_CUDA(cudaMemcpyAsync(hb, b.bounds, sizeof(uint32_t) * p * (p + 1), cudaMemcpyDeviceToHost, ctx->stream));
+    SSS_CUDA(cudaMemcpyAsync(hspl, b.spl, sizeof(uint32_t) * (p - 1), cudaMemcpyDeviceToHost, ctx->stream));
+    SSS_CUDA(cudaStreamSynchronize(ctx->stream));
+    uint32_t acc = 0;
+    for (uint32_t j = 0; j < p; ++j) {
+        hbs[j] = acc;
+        for (uint32_t i = 0; i < p; ++i) {
+            uint32_t sz = hb[(size_t)i * (p + 1) + j + 1] - hb[(size_t)i * (p + 1) + j];
+            hpsz[(size_t)j * p + i] = sz;
+            hpst[(size_t)j * p + i] = part_lo(n, p, i) + hb[(size_t)i * (p + 1) + j];
+            hpo[(size_t)j * p + i] = acc;
+            acc += sz;
+        }
+    }
+    hbs[p] = acc;
+    if (acc != n) return sss_fail(ctx, SSS_ERR_CUDA, "merge: bucket bounds do not cover the input");
+    int cur = 0;
+
+    if (!two_level) {
+        // D1 into level-1 buckets, then the pairwise merge tree per bucket
+        SSS_TRY(sss_upload(ctx, b.piece_off, hpo, sizeof(uint32_t) * npieces));
+        SSS_TRY(sss_upload(ctx, b.bstart, hbs, sizeof(uint32_t) * (p + 1)));
+        SSS_TRY(sss_launch(ctx, "d_records", k_d_records, dim3((n + 255) / 256), dim3(256), 0, run_perm, run_lcp, n,
+                           p, S, (const uint32_t*)b.bounds, (const uint32_t*)b.piece_off, b.R, b.clen, ctx->d_err));
+        SSS_TRY(scan_u32_u64(ctx, b.clen, n, b.coff, b.btot));
+        SSS_TRY(sss_launch(ctx, "d_copy", k_d_copy, dim3((n + 127) / 128), dim3(128), 0, S, b.R,
+                           (const uint64_t*)b.coff, n));
+        SSS_TRY(sss_launch(ctx, "d_iota", k_iota, dim3((n + 255) / 256), dim3(256), 0, b.RA[0], n));
+        SSS_CUDA(cudaMemcpyAsync(b.HA[0], b.R.h, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        std::vector<std::pair<uint32_t, std::vector<uint32_t>>> groups(p);
+        for (uint32_t j = 0; j < p; ++j) {
+            groups[j].first = hbs[j];
+            groups[j].second.assign(hpsz + (size_t)j * p, hpsz + (size_t)(j + 1) * p);
+        }
+        TreePlan T;
+        plan_tree(groups, MS, T);
+        SSS_TRY(run_tree(ctx, b, S, T, hpairs, &cur, MS));
+        SSS_TRY(sss_launch(ctx, "d_seams", k_d_seams, dim3((p + 127) / 128), dim3(128), 0, S, b.R,
+                           (const uint32_t*)b.RA[cur], b.HA[cur], (const uint32_t*)b.bstart, p));
+        return sss_launch(ctx, "d_out", k_d_out, dim3((n + 255) / 256), dim3(256), 0, b.R,
+                          (const uint32_t*)b.RA[cur], (const uint32_t*)b.HA[cur], n, out_perm, out_lcp);
+    }
+
+    // second-level plan: regular samples every `step` strings of every piece
+    const uint32_t step = std::max<uint32_t>(16u, D2_CAP / (D2_OVS + p));
+    uint32_t S2 = 0, NSB = 0, NSS = 0, sbase = 0;
+    for (uint32_t j = 0; j < p; ++j) {
+        uint32_t nsmp = 0;
+        for (uint32_t i = 0; i < p; ++i) {
+            hpso[(size_t)j * p + i] = S2;
+            uint32_t c = hpsz[(size_t)j * p + i] / step;
+            S2 += c;
+            nsmp += c;
+        }
+        BucketInfo bi{};
+        bi.sbase = sbase;
+        bi.nsmp = nsmp;
+        bi.nsb = nsmp / D2_OVS + 1;
+        bi.sb0 = NSB;
+        bi.ss0 = NSS;
+        bi.fref = j == 0 ? MINF : hspl[j - 1];
+        hbi[j] = bi;
+        sbase += nsmp;
+        NSB += bi.nsb;
+        NSS += bi.nsb - 1;
+    }
+    hpso[npieces] = S2;
+    if (S2 > b.cap_s2 || NSB > b.cap_nsb) return sss_fail(ctx, SSS_ERR_CUDA, "merge: second-level capacity");
+    *hn = n;
+    SSS_TRY(sss_upload(ctx, b.binfo, hbi, sizeof(BucketInfo) * p));
+    SSS_TRY(sss_upload(ctx, b.pstart, hpst, sizeof(uint32_t) * npieces));
+    SSS_TRY(sss_upload(ctx, b.psz, hpsz, sizeof(uint32_t) * npieces));
+    SSS_TRY(sss_upload(ctx, b.pso, hpso, sizeof(uint32_t) * (npieces + 1)));
+    const uint32_t nslices = NSB * p;
+    SSS_TRY(sss_upload(ctx, b.soff + nslices, hn, sizeof(uint64_t)));
+    if (S2 > 0) {
+        SSS_TRY(sss_launch(ctx, "d2_samples", k_d2_samples, dim3((S2 + 255) / 256), dim3(256), 0, run_perm, S,
+                           (const uint32_t*)b.pso, (const uint32_t*)b.pstart, (uint32_t)npieces, S2, step, b.smp2,
+                           b.s2offs, b.s2lens));
+        StrIn sin{in.chars, in.n_chars, b.s2offs, b.s2lens, S2};
+        Arena sub = b.sub2;
+        SSS_TRY(impl_local_sort(ctx, sub, sin, 1, sss_params{}, b.s2perm, b.s2lcp));
+    }
+    if (NSS > 0) {
+        SSS_TRY(sss_launch(ctx, "d2_subspl", k_d2_subspl, dim3((NSS + 255) / 256), dim3(256), 0,
+                           (const BucketInfo*)b.binfo, p, NSS, (const uint32_t*)b.smp2, (const uint32_t*)b.s2perm,
+                           b.subspl));
+        SSS_TRY(sss_launch(ctx, "d2_bounds", k_d2_bounds, dim3((NSS * p + 127) / 128), dim3(128), 0, run_perm, S,
+                           (const BucketInfo*)b.binfo, p, NSS, (const uint32_t*)b.pstart, (const uint32_t*)b.psz,
+                           (const uint32_t*)b.subspl, b.sb));
+    }
+    SSS_TRY(sss_launch(ctx, "d2_slices", k_d2_slices, dim3((nslices + 255) / 256), dim3(256), 0,
+                       (const BucketInfo*)b.binfo, p, NSB, (const uint32_t*)b.sb, (const uint32_t*)b.psz, b.ssz));
+    SSS_TRY(scan_u32_u64(ctx, b.ssz, nslices, b.soff, b.btot));
+    SSS_CUDA(cudaMemsetAsync(b.cnt, 0, sizeof(uint32_t), ctx->stream));
+    SSS_TRY(sss_launch(ctx, "d2_oversized", k_d2_oversized, dim3((NSB + 255) / 256), dim3(256), 0,
+                       (const uint64_t*)b.soff, p, NSB, b.olist, b.cnt));
+    // D1: LCP-compressed records of every sub-bucket slice
+    SSS_TRY(sss_launch(ctx, "d2_records", k_d2_records, dim3((n + 255) / 256), dim3(256), 0, run_perm, run_lcp, n, p,
+                       S, (const uint32_t*)b.bounds, (const BucketInfo*)b.binfo, (const uint32_t*)b.sb,
+                       (const uint64_t*)b.soff, b.R, b.clen, ctx->d_err));
+    SSS_TRY(scan_u32_u64(ctx, b.clen, n, b.coff, b.btot));
+    SSS_TRY(sss_launch(ctx, "d_copy", k_d_copy, dim3((n + 127) / 128), dim3(128), 0, S, b.R, (const uint64_t*)b.coff,
+                       n));
+    // D2: decode, then merge every sub-bucket in one CTA
+    SSS_TRY(sss_launch(ctx, "d2_decode", k_d2_decode, dim3((nslices + 127) / 128), dim3(128), 0, S, b.R,
+                       (const BucketInfo*)b.binfo, p, NSB, (const uint64_t*)b.soff, (const uint32_t*)b.subspl, b.rr,
+                       b.rk));
+    TieLists TL{b.tie_tiny, b.tie_med, b.cnt + 1, n / 2 + 2, n / 65 + 2, finish_cap_tiny()};
+    SSS_CUDA(cudaMemsetAsync(b.cnt + 1, 0, sizeof(uint32_t) * 2, ctx->stream));
+    SSS_TRY(sss_launch(ctx, "d2_cta", k_d2_cta, dim3(NSB), dim3(D2_T), (size_t)D2_CAP * (8 + 8), S, b.R,
+                       (const uint64_t*)b.soff, p, (const uint32_t*)b.rr, (const uint64_t*)b.rk, out_perm, out_lcp,
+                       TL, ctx->d_err));
+    // oversized sub-buckets (many equal strings): pairwise merge tree over their slices.
+    // (the sample sort above may have grown the pinned staging: re-derive pointers)
+    {
+        const size_t off_cnt = reinterpret_cast<char*>(hcnt) - static_cast<char*>(pin);
+        const size_t off_pairs = reinterpret_cast<char*>(hpairs) - static_cast<char*>(pin);
+        SSS_TRY(sss_pinned(ctx, pin_need, &pin));
+        hcnt = reinterpret_cast<uint32_t*>(static_cast<char*>(pin) + off_cnt);
+        hpairs = reinterpret_cast<Pair*>(static_cast<char*>(pin) + off_pairs);
+    }
+    SSS_CUDA(cudaMemcpyAsync(hcnt, b.cnt, sizeof(uint32_t) * 3, cudaMemcpyDeviceToHost, ctx->stream));
+    SSS_CUDA(cudaStreamSynchronize(ctx->stream));
+    const uint32_t nover = hcnt[0];
+    if (hcnt[1] > n / 2 + 2 || hcnt[2] > n / 65 + 2) return sss_fail(ctx, SSS_ERR_CUDA, "merge: tie list overflow");
+    if (hcnt[1] + hcnt[2] > 0) {
+        // strings compared as their truncated prefixes
+        StrIn tin{in.chars, in.n_chars, in.offs, trunc ? trunc : in.lens, n};
+        SSS_TRY(impl_finish_segments(ctx, b.tie_tiny, hcnt[1], b.tie_med, hcnt[2], tin, out_perm, out_lcp));
+    }
+    if (nover > 0) {
+        std::vector<uint32_t> olist(nover);
+        std::vector<uint32_t> sizes((size_t)nover * p);
+        std::vector<uint64_t> base(nover);
+        SSS_CUDA(cudaMemcpy(olist.data(), b.olist, sizeof(uint32_t) * nover, cudaMemcpyDeviceToHost));
+        std::vector<std::pair<uint32_t, std::vector<uint32_t>>> groups(nover);
+        for (uint32_t w = 0; w < nover; ++w) {
+            uint32_t sbk = olist[w];
+            SSS_CUDA(cudaMemcpy(&base[w], b.soff + (size_t)sbk * p, sizeof(uint64_t), cudaMemcpyDeviceToHost));
+            SSS_CUDA(cudaMemcpy(sizes.data() + (size_t)w * p, b.ssz + (size_t)sbk * p, sizeof(uint32_t) * p,
+                                cudaMemcpyDeviceToHost));
+            groups[w].first = (uint32_t)base[w];
+            groups[w].second.assign(sizes.begin() + (size_t)w * p, sizes.begin() + (size_t)(w + 1) * p);
+        }
+        SSS_TRY(sss_launch(ctx, "d2_fb_init", k_d2_fb_init, dim3(std::min<uint32_t>(nover, 1024)), dim3(256), 0,
+                           (const uint64_t*)b.soff, p, (const uint32_t*)b.olist, nover, (const uint32_t*)b.R.h,
+                           b.RA[0], b.HA[0]));
+        TreePlan T;
+        plan_tree(groups, MS, T);
+        cur = 0;
+        SSS_TRY(run_tree(ctx, b, S, T, hpairs, &cur, MS));
+        SSS_TRY(sss_launch(ctx, "d2_fb_out", k_d2_fb_out, dim3(std::min<uint32_t>(nover, 1024)), dim3(256), 0,
+                           (const uint64_t*)b.soff, p, (const uint32_t*)b.olist, nover, (const uint32_t*)b.R.idx,
+                           (const uint32_t*)b.RA[cur], (const uint32_t*)b.HA[cur], out_perm, out_lcp));
+    }
+    // D3
+    return sss_launch(ctx, "d2_seams", k_d2_seams, dim3((NSB + 255) / 256), dim3(256), 0, S, (const uint64_t*)b.soff,
+                      p, NSB, (const uint32_t*)out_perm, out_lcp);
 }
 
 // Sum of the (truncated) lengths: an upper bound on the record characters.

@@ -47,9 +47,10 @@ def test_partition_matches_oracle(seed, n, p):
     assert np.array_equal(u32(bnd), want_b)
 
 
+@pytest.mark.parametrize("tree", [False, True])
 @pytest.mark.parametrize("seed,n,p,trunc", [(0, 800, 4, False), (1, 5000, 16, True), (2, 3000, 5, True),
-                                            (3, 30000, 16, False), (4, 7, 3, True)])
-def test_lcp_merge_matches_oracle(seed, n, p, trunc):
+                                            (3, 30000, 16, False), (4, 7, 3, True), (5, 60000, 2, True)])
+def test_lcp_merge_matches_oracle(seed, n, p, trunc, tree):
     m = sss()
     ss = rand_set(seed, n)
     rp, rl = oracle.local_sort(ss, p)
@@ -59,10 +60,18 @@ def test_lcp_merge_matches_oracle(seed, n, p, trunc):
     want_p, want_l = oracle.merge(ss, rp, p, bnd, tr)
     chars, offs, lens = m.to_device(ss)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
-    op, ol = m.sss_lcp_merge(chars, offs, lens, t(rp), t(rl), p, trunc=None if tr is None else t(tr))
+    prm = m.params(flags=m.SSS_FLAG_MERGE_TREE if tree else 0)
+    op, ol = m.sss_lcp_merge(chars, offs, lens, t(rp), t(rl), p, trunc=None if tr is None else t(tr), prm=prm)
     m.context().sync()
     assert np.array_equal(u32(op), want_p)
     assert np.array_equal(u32(ol), want_l)
+
+
+def test_merge_many_equal_strings_oversized_sub_buckets():
+    # 30000 strings from 3 values: sub-buckets of equal strings exceed one CTA
+    rnd = random.Random(21)
+    pool = [b"GATTACA" * 3, b"GATTACA" * 3 + b"T", b"CAT"]
+    check_sort(datagen.from_strings([rnd.choice(pool) for _ in range(30000)]), 4)
 
 
 def check_sort(ss, p, flags=0):
@@ -105,6 +114,16 @@ def test_pdms_more_partitions_than_strings():
 def test_ms_mode_full_strings():
     m = sss()
     check_sort(datagen.config2(n=20000), 16, m.SSS_FLAG_MS)
+
+
+def test_pdms_tree_merge_path():
+    m = sss()
+    check_sort(datagen.config2(n=30000), 16, m.SSS_FLAG_MERGE_TREE)
+
+
+def test_pdms_many_partitions_tree_fallback():
+    # p > 256 takes the pairwise-tree merge
+    check_sort(rand_set(77, 6000), 300)
 
 
 def test_pdms_config1():
