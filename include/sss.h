@@ -191,6 +191,35 @@ sss_status sss_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars,
                     uint32_t* out_dist, uint32_t* out_approx);
 
 /* ------------------------------------------------------------------------ */
+/* Allocation-free prefix doubling (stage B) for small sets.  This call has no
+ * counterpart in the paper; it exists for callers that cannot allocate device
+ * memory at the moment they need the result -- e.g. code running inside a host
+ * framework that owns the whole device budget, or a latency-critical request
+ * loop where a cudaMalloc could block or fail.  It needs no context and no
+ * work memory: its state and hash table live in one fixed device array of about
+ * 2.6 MB inside libsss.so, which every GPU that loads the library holds until
+ * the process exits.  It calls no cudaMalloc/cudaFree.
+ *
+ * Computes out_approx exactly as sss_dist_prefix with run_perm = run_lcp = NULL
+ * (every active string hashed every round); one CTA runs all rounds.
+ *   n           : at most SSS_NOALLOC_MAX_STRINGS, else SSS_ERR_INVALID_ARG
+ *                 (nothing is enqueued)
+ *   chars/offsets/lengths/out_approx: device pointers, as for the other calls
+ *   params      : kmin, kmax, hash_seed are used (NULL = defaults)
+ *   cuda_stream : the cudaStream_t the kernel is enqueued on
+ * The first call on a device (the device current at the call) looks up the
+ * array's device address; make that first call before any stream capture.
+ * Every call on a device shares the one array and clears the state it needs at
+ * its start, so calls that may overlap on the GPU (different streams without
+ * ordering) race and give undefined results; order them on one stream.  Errors
+ * are returned for bad arguments and failed launches only; inputs are not
+ * validated on the device. */
+#define SSS_NOALLOC_MAX_STRINGS 65536u
+sss_status sss_dist_prefix_noalloc(const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,
+                                   const uint32_t* lengths, uint32_t n, const sss_params* params,
+                                   uint32_t* out_approx, void* cuda_stream);
+
+/* ------------------------------------------------------------------------ */
 /* Instrumentation: per-kernel launch counts and (when timing is enabled) device
  * time measured with CUDA events on the context's stream around each launch. */
 #define SSS_MAX_KERNELS 64

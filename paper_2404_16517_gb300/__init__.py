@@ -83,6 +83,7 @@ def lib():
             "sss_partition": (st, [vp, vp, u64, vp, vp, vp, vp, u32, u32, P, vp, vp]),
             "sss_lcp_merge": (st, [vp, vp, u64, vp, vp, vp, vp, vp, u32, u32, P, vp, vp]),
             "sss_sort": (st, [vp, vp, u64, vp, vp, u32, u32, P, vp, vp, vp, vp]),
+            "sss_dist_prefix_noalloc": (st, [vp, u64, vp, vp, u32, P, vp, vp]),
             "sss_set_timing": (st, [vp, C.c_int, C.c_char_p]),
             "sss_kernel_stats": (st, [vp, C.POINTER(sss_kernel_stat), u32, C.POINTER(u32)]),
             "sss_reset_stats": (st, [vp]),
@@ -100,7 +101,7 @@ def exported_symbols() -> list[str]:
     return ["sss_params_default", "sss_create", "sss_destroy", "sss_set_stream", "sss_set_workspace",
             "sss_workspace_bytes", "sss_sync", "sss_status_string", "sss_last_error", "sss_local_sort",
             "sss_dist", "sss_dist_prefix", "sss_partition", "sss_lcp_merge", "sss_sort", "sss_set_timing",
-            "sss_kernel_stats", "sss_reset_stats"]
+            "sss_kernel_stats", "sss_reset_stats", "sss_dist_prefix_noalloc"]
 
 
 def params(kmin: int = 0, kmax: int = SSS_KMAX_AUTO, v: int = 2, flags: int = 0, hash_seed: int = 0,
@@ -279,6 +280,25 @@ def sss_sort(chars, offs, lens, p: int = 1, prm: sss_params | None = None, out_p
     ctx._check(lib().sss_sort(ctx.h, _ptr(chars), chars.numel(), _ptr(offs), _ptr(lens), n, p, C.byref(prm),
                               _ptr(op), _ptr(ol), _ptr(d), _ptr(a)), ctx.h)
     return op, ol, d, a
+
+
+NOALLOC_MAX_STRINGS = 65536
+
+
+def sss_dist_prefix_noalloc(chars, offs, lens, prm: sss_params | None = None, out_approx=None):
+    """Allocation-free stage B for at most NOALLOC_MAX_STRINGS strings, on the
+    current torch stream (for callers that cannot allocate device memory; the
+    output tensor must then be supplied by the caller)."""
+    _check_strings(chars, offs, lens)
+    n = lens.numel()
+    a = _out(out_approx, n, chars.device)
+    prm = prm or params()
+    st = torch.cuda.current_stream(chars.device).cuda_stream
+    status = lib().sss_dist_prefix_noalloc(_ptr(chars), chars.numel(), _ptr(offs), _ptr(lens), n, C.byref(prm),
+                                           _ptr(a), C.c_void_p(st))
+    if status != 0:
+        raise SssError(status, "sss_dist_prefix_noalloc failed")
+    return a
 
 
 def workspace_bytes(n: int, total_len: int, p: int = 1, prm: sss_params | None = None) -> int:

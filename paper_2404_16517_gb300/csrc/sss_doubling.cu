@@ -34,6 +34,7 @@
 //    an open-addressing table of >= 2x slots with atomicCAS, a second insert of a
 //    key marks its slot, and each rep reads its slot's mark.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "sss_device.cuh"
@@ -644,4 +645,162 @@ sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& sin, const uin
     }
     return sss_launch(ctx, "pd_final", k_pd_final, dim3((n + 255) / 256), dim3(256), 0, in, (const uint32_t*)B.apos,
                       (const uint32_t*)B.lpos, approx);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of stage B for small sets (sss_dist_prefix_noalloc).
+//
+// Some callers cannot allocate device memory when they need this result: a host
+// framework that owns the whole device budget and hands out no allocator, or a
+// latency-critical request loop where a cudaMalloc could block, fail or
+// fragment memory at an arbitrary moment.  This entry point therefore needs no
+// context and no work memory: its per-string state and its hash table live in
+// the fixed array below, which every GPU that loads the library holds until the
+// process exits.  One CTA runs all rounds (plain doubling, no local runs).
+namespace {
+
+constexpr uint32_t NA_MAXN = SSS_NOALLOC_MAX_STRINGS;  // strings per call
+constexpr uint32_t NA_TSLOTS = 2 * NA_MAXN;            // hash-table slots
+constexpr size_t NA_OFF_APOS = 0;
+constexpr size_t NA_OFF_HLEN = NA_OFF_APOS + sizeof(uint32_t) * NA_MAXN;
+constexpr size_t NA_OFF_HST = NA_OFF_HLEN + sizeof(uint32_t) * NA_MAXN;
+constexpr size_t NA_OFF_KEY = NA_OFF_HST + sizeof(uint64_t) * NA_MAXN;
+constexpr size_t NA_OFF_TAB = NA_OFF_KEY + sizeof(uint64_t) * NA_MAXN;
+constexpr size_t NA_OFF_MARK = NA_OFF_TAB + sizeof(uint64_t) * NA_TSLOTS;
+constexpr size_t NA_BYTES = NA_OFF_MARK + NA_TSLOTS;
+constexpr int NA_T = 1024;
+
+// The scratch shared by every call on a device (contents persist between calls).
+static __device__ __align__(256) unsigned char g_pd_noalloc_scratch[NA_BYTES];
+
+__global__ void __launch_bounds__(NA_T) k_pd_noalloc(const uint8_t* __restrict__ chars,
+                                                     const uint64_t* __restrict__ offs,
+                                                     const uint32_t* __restrict__ lens, uint32_t n, uint32_t kmin,
+                                                     uint32_t kmax, uint64_t B, uint32_t* __restrict__ out_approx,
+                                                     unsigned char* __restrict__ scratch) {
+    uint32_t* apos = reinterpret_cast<uint32_t*>(scratch + NA_OFF_APOS);
+    uint32_t* hlen = reinterpret_cast<uint32_t*>(scratch + NA_OFF_HLEN);
+    uint64_t* hst = reinterpret_cast<uint64_t*>(scratch + NA_OFF_HST);
+    uint64_t* key = reinterpret_cast<uint64_t*>(scratch + NA_OFF_KEY);
+    unsigned long long* tab = reinterpret_cast<unsigned long long*>(scratch + NA_OFF_TAB);
+    uint8_t* mark = scratch + NA_OFF_MARK;
+    __shared__ uint32_t sh_zero, sh_active;
+    const uint32_t tmask = NA_TSLOTS - 1;
+    // every call starts from a clean state: the array keeps the previous call's contents
+    for (uint32_t i = threadIdx.x; i < n; i += NA_T) {
+        apos[i] = ACTIVE;
+        hlen[i] = 0;
+    }
+    __syncthreads();
+    for (uint32_t k = kmin; k <= kmax; ++k) {
+        const uint64_t L = 1ull << k;
+        for (uint32_t t = threadIdx.x; t < NA_TSLOTS; t += NA_T) {
+            tab[t] = 0ull;
+            mark[t] = 0;
+        }
+        if (threadIdx.x == 0) {
+            sh_zero = 0;
+            sh_active = 0;
+        }
+        __syncthreads();
+        // hash every active string's prefix of length min(L, len) and insert its key
+        for (uint32_t i = threadIdx.x; i < n; i += NA_T) {
+            if (apos[i] != ACTIVE) continue;
+            uint32_t len = lens[i];
+            uint32_t le = L < len ? (uint32_t)L : len;
+            const uint8_t* str = chars + offs[i];
+            uint64_t h = 0;
+            uint32_t w0 = 0;
+            if (L >= 16 && hlen[i] == (uint32_t)(L / 2)) {
+                h = hst[i];
+                w0 = (uint32_t)(L / 16);
+            }
+            for (uint32_t w = w0; w < (le + 7) / 8; ++w) {
+                uint64_t x = load_word_be(str, le, 8 * w);
+                h = fold_limb(h, B, x >> 32);
+                h = fold_limb(h, B, x & 0xFFFFFFFFull);
+            }
+            hst[i] = h;
+            hlen[i] = le;
+            uint64_t kk = smix64(h ^ ((uint64_t)le * GAMMA));
+            key[i] = kk;
+            if (kk == 0) {
+                atomicAdd(&sh_zero, 1u);
+                continue;
+            }
+            uint32_t hs = (uint32_t)kk & tmask;
+            for (uint32_t probe = 0; probe <= tmask; ++probe) {
+                unsigned long long old = atomicCAS(&tab[hs], 0ull, (unsigned long long)kk);
+                if (old == 0ull) break;
+                if (old == kk) {
+                    mark[hs] = 1;
+                    break;
+                }
+                hs = (hs + 1) & tmask;
+            }
+        }
+        __syncthreads();
+        // retire strings whose key is unique or whose whole length was tested
+        for (uint32_t i = threadIdx.x; i < n; i += NA_T) {
+            if (apos[i] != ACTIVE) continue;
+            uint32_t len = lens[i];
+            bool dup = ht_dup(tab, mark, tmask, sh_zero, key[i]);
+            if (!dup || (uint64_t)len <= L) apos[i] = (uint64_t)len < L ? len : (uint32_t)L;
+            else atomicAdd(&sh_active, 1u);
+        }
+        __syncthreads();
+        if (sh_active == 0) break;
+        __syncthreads();
+    }
+    for (uint32_t i = threadIdx.x; i < n; i += NA_T) {
+        uint32_t a = apos[i];
+        out_approx[i] = a == ACTIVE ? lens[i] : a;
+    }
+}
+
+std::mutex g_na_mu;
+unsigned char* g_na_ptr[64];
+
+}  // namespace
+
+extern "C" sss_status sss_dist_prefix_noalloc(const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,
+                                              const uint32_t* lengths, uint32_t n, const sss_params* params,
+                                              uint32_t* out_approx, void* cuda_stream) {
+    (void)n_chars;
+    if (n > NA_MAXN) return SSS_ERR_INVALID_ARG;  // beyond the fixed capacity
+    if (n == 0) return SSS_OK;
+    if (!chars || !offsets || !lengths || !out_approx) return SSS_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SSS_ERR_CUDA;
+    unsigned char* scratch;
+    {
+        // first call on this device: look up the device address of the fixed array
+        // (host code may not use the array's name as a device pointer)
+        std::lock_guard<std::mutex> lk(g_na_mu);
+        if (!g_na_ptr[dev]) {
+            void* ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_pd_noalloc_scratch) != cudaSuccess || ptr == nullptr) {
+                cudaGetLastError();
+                return SSS_ERR_CUDA;
+            }
+            g_na_ptr[dev] = static_cast<unsigned char*>(ptr);
+        }
+        scratch = g_na_ptr[dev];
+    }
+    sss_params prm;
+    sss_params_default(&prm);
+    if (params) prm = *params;
+    const uint32_t kmin = std::min<uint32_t>(prm.kmin, 31u);
+    const uint32_t kmax = prm.kmax == SSS_KMAX_AUTO ? 31u : std::min<uint32_t>(prm.kmax, 31u);
+    const uint64_t Bh = 2 + host_smix(prm.hash_seed + GAMMA) % (P61 - 3);
+    if (kmin > kmax) {
+        // no rounds: every string keeps approx = len
+        return cudaMemcpyAsync(out_approx, lengths, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice,
+                               static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess
+                   ? SSS_OK
+                   : SSS_ERR_CUDA;
+    }
+    k_pd_noalloc<<<1, NA_T, 0, static_cast<cudaStream_t>(cuda_stream)>>>(chars, offsets, lengths, n, kmin, kmax, Bh,
+                                                                         out_approx, scratch);
+    return cudaGetLastError() == cudaSuccess ? SSS_OK : SSS_ERR_CUDA;
 }
