@@ -190,6 +190,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--breakdown", action="store_true", help="per-kernel times to stderr")
     ap.add_argument("--merge-ms", type=int, default=0, help="merge segment spacing (0 = library default)")
+    ap.add_argument("--p", type=int, default=P, help="partitions (profiling of smaller cases)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, local = dist_env()
@@ -224,7 +225,7 @@ def main():
     approx = torch.empty(n, dtype=torch.int32, device=dev)
 
     def step():
-        sss.sss_sort(chars, offs, lens, P, prm, perm, lcp, out_dist=dist_t, out_approx=approx, ctx=ctx)
+        sss.sss_sort(chars, offs, lens, args.p, prm, perm, lcp, out_dist=dist_t, out_approx=approx, ctx=ctx)
 
     # warm-up; the second one with every kernel timed to find the dominant kernel
     # (the first pays for lazy module loading)
@@ -298,7 +299,7 @@ def main():
             d_chars.copy_(h_chars, non_blocking=True)
             d_offs.copy_(h_offs, non_blocking=True)
             d_lens.copy_(h_lens, non_blocking=True)
-            sss.sss_sort(d_chars, d_offs, d_lens, P, prm, perm, lcp, ctx=ctx)
+            sss.sss_sort(d_chars, d_offs, d_lens, args.p, prm, perm, lcp, ctx=ctx)
             h_perm.copy_(perm, non_blocking=True)
             h_lcp.copy_(lcp, non_blocking=True)
 
@@ -341,7 +342,8 @@ def main():
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "u8", "data": "synthetic",
                "strings_per_s": n * ws / (ms_step / 1e3),
-               "config": {"workload": WORKLOAD, "strings": n, "chars": N, "partitions": P,
+               "config": {"workload": WORKLOAD if (n == N_FULL and args.p == P) else f"pdms_{n}x500_p{args.p}",
+                          "strings": n, "chars": N, "partitions": args.p,
                           "D_over_N": D / N, "approx_over_N": Dapprox / N,
                           "l2": "inputs (2.1 GB of chars) larger than L2; no flush",
                           "parallelism": f"replicas x{ws}"},

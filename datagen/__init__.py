@@ -182,20 +182,23 @@ def markov_text(seed: int, length: int, sigma: int = 64, alpha: float = 0.1) -> 
     cdf[:, -1] = 1.0
     u = uniform_float(rng(seed, ST_MARKOV, np.arange(length, dtype=np.uint64)))
     first2 = uniform_index(rng(seed, ST_MARKOV, np.arange(length, length + 2, dtype=np.uint64)), sigma)
-    sym = np.empty(length, dtype=np.int64)
+    import bisect
+    rows = cdf.tolist()
+    uu = u.tolist()
+    sym = [0] * length
     sym[0] = int(first2[0])
     if length > 1:
         sym[1] = int(first2[1])
-    # sequential chain: plain loop over a precomputed CDF table
-    a, b = int(sym[0]), int(sym[1]) if length > 1 else 0
-    cdf_list = cdf
+    # sequential chain: invert the row's CDF at one uniform per step
+    a, b = sym[0], sym[1] if length > 1 else 0
+    last = sigma - 1
     for t in range(2, length):
-        row = cdf_list[a * sigma + b]
-        c = int(np.searchsorted(row, u[t], side="right"))
-        if c >= sigma:
-            c = sigma - 1
+        c = bisect.bisect_right(rows[a * sigma + b], uu[t])
+        if c > last:
+            c = last
         sym[t] = c
         a, b = b, c
+    sym = np.asarray(sym, dtype=np.int64)
     return (sym + 0x21).astype(np.uint8)
 
 

@@ -46,6 +46,28 @@ struct WordStream {
         cur = rem ? bswap64(__ldg(p)) : 0;
         ++p;
     }
+    // the next 4 words (32 characters), with the 4 aligned loads issued together
+    __device__ __forceinline__ void next4(uint64_t* w) {
+        uint64_t nx[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint64_t* pi = p + i;
+            nx[i] = (rem > 8u * i && reinterpret_cast<const uint8_t*>(pi) < end) ? bswap64(__ldg(pi)) : 0ull;
+        }
+        p += 4;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            uint64_t x = sh ? ((cur << sh) | (nx[i] >> (64 - sh))) : cur;
+            cur = nx[i];
+            if (rem < 8) {
+                x = rem ? (x & (~0ull << (8 * (8 - rem)))) : 0ull;
+                rem = 0;
+            } else {
+                rem -= 8;
+            }
+            w[i] = x;
+        }
+    }
     __device__ __forceinline__ uint64_t next() {
         if (rem == 0) return 0;
         uint64_t nx = (reinterpret_cast<const uint8_t*>(p) < end) ? bswap64(__ldg(p)) : 0;
@@ -83,6 +105,49 @@ __device__ __forceinline__ uint32_t lcp_extend(const uint8_t* __restrict__ a, ui
         }
     }
     return cap;
+}
+
+// lcp_extend for a member `a` against the segment's reference `b`, in blocks of
+// 32 characters with independent loads.  Besides the LCP v it reports the 8
+// characters of `a` at d + v in *w (then *w_ok = true); a thread that stops early
+// (v >= *runmin + 8, so it cannot set the minimum) reports *w_ok = false.
+__device__ __forceinline__ uint32_t lcp_extend_w(const uint8_t* __restrict__ a, uint32_t la,
+                                                 const uint8_t* __restrict__ b, uint32_t lb, uint32_t d,
+                                                 const volatile uint32_t* runmin, uint64_t* w, bool* w_ok) {
+    uint32_t m = la < lb ? la : lb;
+    uint32_t r;
+    if (d >= m) {
+        r = 0;
+    } else {
+        uint32_t cap = m - d;
+        WordStream A, B;
+        A.init(a, la, d);
+        B.init(b, lb, d);
+        r = cap;
+        for (uint32_t k = 0; k < cap; k += 32) {
+            if (k > 0 && (uint64_t)k >= (uint64_t)(*runmin) + 8u) {
+                *w_ok = false;
+                return k;
+            }
+            uint64_t xa[4], xb[4];
+            A.next4(xa);
+            B.next4(xb);
+            bool hit = false;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uint64_t x = xa[i] ^ xb[i];
+                if (!hit && x) {
+                    uint32_t c = k + 8 * i + ((uint32_t)__clzll((long long)x) >> 3);
+                    r = c < cap ? c : cap;
+                    hit = true;
+                }
+            }
+            if (hit) break;
+        }
+    }
+    *w = load_word_be(a, la, d + r);
+    *w_ok = true;
+    return r;
 }
 
 // First differing character of two distinct words, counted from the word start.
@@ -263,4 +328,91 @@ __device__ void bitonic_sort64(uint64_t* a, uint32_t count) {
             __syncthreads();
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Block merge sort of `count` 128-bit keys (hi, lo) held in shared memory arrays
+// of THREADS*ITEMS entries, ascending.  Each thread sorts ITEMS keys in
+// registers (odd-even transposition), then log2(THREADS) rounds merge pairs of
+// sorted lists: every thread finds its ITEMS outputs with a merge-path binary
+// search and merges them serially.  Slots past `count` are padded with all-ones
+// keys (the arrays are fully overwritten).  O(n log n) work and 2 barriers per
+// round, instead of the bitonic network's O(n log^2 n) and a barrier per stage.
+template <int THREADS, int ITEMS>
+__device__ void block_merge_sort128(uint64_t* sHi, uint64_t* sLo, uint32_t count) {
+    const uint32_t tid = threadIdx.x;
+    uint64_t h[ITEMS], l[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t idx = tid * ITEMS + i;
+        if (idx < count) {
+            h[i] = sHi[idx];
+            l[i] = sLo[idx];
+        } else {
+            h[i] = ~0ull;
+            l[i] = ~0ull;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+#pragma unroll
+        for (int i = (r & 1); i + 1 < ITEMS; i += 2) {
+            if (key128_less(h[i + 1], l[i + 1], h[i], l[i])) {
+                uint64_t th = h[i], tl = l[i];
+                h[i] = h[i + 1];
+                l[i] = l[i + 1];
+                h[i + 1] = th;
+                l[i + 1] = tl;
+            }
+        }
+    }
+    const uint32_t used = (count + ITEMS - 1) / ITEMS;  // threads holding real keys
+    for (uint32_t w = 1; w < used; w <<= 1) {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            sHi[tid * ITEMS + i] = h[i];
+            sLo[tid * ITEMS + i] = l[i];
+        }
+        __syncthreads();
+        const uint32_t L = w * ITEMS;
+        const uint32_t g0 = (tid / (2 * w)) * (2 * L);
+        if (g0 >= count) continue;  // a pair of padding lists stays as it is
+        const uint32_t diag = (tid % (2 * w)) * ITEMS;
+        const uint64_t* Ah = sHi + g0;
+        const uint64_t* Al = sLo + g0;
+        const uint64_t* Bh = Ah + L;
+        const uint64_t* Bl = Al + L;
+        uint32_t lo = diag > L ? diag - L : 0, hi = diag < L ? diag : L;
+        while (lo < hi) {
+            uint32_t mid = (lo + hi) >> 1;
+            uint32_t bj = diag - 1 - mid;
+            if (!key128_less(Bh[bj], Bl[bj], Ah[mid], Al[mid])) lo = mid + 1;
+            else hi = mid;
+        }
+        uint32_t a = lo, b = diag - lo;
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            bool takeA;
+            if (a >= L) takeA = false;
+            else if (b >= L) takeA = true;
+            else takeA = !key128_less(Bh[b], Bl[b], Ah[a], Al[a]);
+            if (takeA) {
+                h[i] = Ah[a];
+                l[i] = Al[a];
+                ++a;
+            } else {
+                h[i] = Bh[b];
+                l[i] = Bl[b];
+                ++b;
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        sHi[tid * ITEMS + i] = h[i];
+        sLo[tid * ITEMS + i] = l[i];
+    }
+    __syncthreads();
 }

@@ -177,9 +177,14 @@ __global__ void __launch_bounds__(256) k_pd_lists(PdIn in, const uint32_t* __res
     }
 }
 
-// B1: keys of the reps (incremental Horner from the L/2-prefix when available)
+// B1: keys of the reps.  Horner resumes from the L/2-prefix state of the
+// previous round: the rep's own state, or (for a position that starts a group
+// only from this round on) the state of its previous group start, which shares
+// that prefix.  States are double-buffered by round parity.
 __global__ void k_pd_hash(PdIn in, const uint32_t* __restrict__ reps, uint32_t nreps, const uint32_t* __restrict__ lpos,
-                          uint64_t* __restrict__ hst, uint32_t* __restrict__ hlen, uint64_t* __restrict__ K,
+                          const uint64_t* __restrict__ hst_in, const uint32_t* __restrict__ hlen_in,
+                          uint64_t* __restrict__ hst_out, uint32_t* __restrict__ hlen_out,
+                          const uint32_t* __restrict__ prevstart, uint64_t* __restrict__ K,
                           uint32_t* __restrict__ V, uint64_t L, uint64_t B) {
     uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nreps) return;
@@ -190,9 +195,13 @@ __global__ void k_pd_hash(PdIn in, const uint32_t* __restrict__ reps, uint32_t n
     const uint8_t* str = in.chars + in.offs[s];
     uint64_t h = 0;
     uint32_t w0 = 0;
-    if (L >= 16 && hlen[q] == (uint32_t)(L / 2)) {
-        h = hst[q];
-        w0 = (uint32_t)(L / 16);
+    if (L >= 16) {
+        uint32_t src = q;
+        if (hlen_in[q] != (uint32_t)(L / 2) && prevstart) src = prevstart[q];
+        if (hlen_in[src] == (uint32_t)(L / 2)) {
+            h = hst_in[src];
+            w0 = (uint32_t)(L / 16);
+        }
     }
     uint32_t nw = (le + 7) / 8;
     if (w0 < nw) {
@@ -223,10 +232,59 @@ __global__ void k_pd_hash(PdIn in, const uint32_t* __restrict__ reps, uint32_t n
             pw += 8;
         }
     }
-    hst[q] = h;
-    hlen[q] = le;
+    hst_out[q] = h;
+    hlen_out[q] = le;
     K[j] = smix64(h ^ ((uint64_t)le * GAMMA));
     V[j] = q;
+}
+
+// prevstart[q] = last position q' <= q that starts a group in round k-1
+// (kstar(q') <= k-1): inclusive max-scan of flagged positions in tiles of 4096,
+// then the carry from earlier tiles.
+__global__ void __launch_bounds__(1024) k_pd_ps_tiles(PdIn in, uint32_t kprev, uint32_t kmin,
+                                                      uint32_t* __restrict__ out, uint32_t* __restrict__ tmax) {
+    constexpr int ITEMS = 4;
+    __shared__ uint32_t sh_warp[32];
+    uint32_t base = blockIdx.x * 4096 + threadIdx.x * ITEMS;
+    uint32_t loc[ITEMS];
+    uint32_t m = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t q = base + i;
+        if (q < in.n && kstar_of(in, q, kmin) <= kprev) m = q + 1;  // +1: 0 means none
+        loc[i] = m;
+    }
+    uint32_t incl = BlockScan<1024>::inclusive_max(m, sh_warp);
+    uint32_t prev = __shfl_up_sync(SSS_FULL, incl, 1);
+    __shared__ uint32_t sh_last[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 31) sh_last[w] = incl;
+    __syncthreads();
+    if (lane == 0) prev = w > 0 ? sh_last[w - 1] : 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t q = base + i;
+        if (q < in.n) out[q] = loc[i] > prev ? loc[i] : prev;
+    }
+    if (threadIdx.x == 1023) tmax[blockIdx.x] = incl;
+}
+
+__global__ void k_pd_ps_carry(uint32_t* __restrict__ tmax, uint32_t nt) {
+    if (threadIdx.x != 0) return;
+    uint32_t run = 0;
+    for (uint32_t t = 0; t < nt; ++t) {
+        uint32_t v = tmax[t];
+        tmax[t] = run;  // exclusive: max over earlier tiles
+        run = v > run ? v : run;
+    }
+}
+
+__global__ void k_pd_ps_apply(uint32_t n, uint32_t* __restrict__ out, const uint32_t* __restrict__ tmax) {
+    uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    uint32_t v = out[q], c = tmax[q / 4096];
+    v = v > c ? v : c;
+    out[q] = v ? v - 1 : q;  // no earlier start (cannot happen): itself
 }
 
 // B2: bucket the keys by their top bits
@@ -313,7 +371,7 @@ __global__ void __launch_bounds__(DD_T) k_pd_buckets(const uint32_t* __restrict_
             sV[i] = tV[bs + i];
         }
         __syncthreads();
-        bitonic_sort128<DD_T>(sK, sV, m);
+        block_merge_sort128<DD_T, DD_CAP / DD_T>(sK, sV, m);
         for (uint32_t i = threadIdx.x; i < m; i += DD_T) {
             uint64_t k = sK[i];
             bool d = (i > 0 && sK[i - 1] == k) || (i + 1 < m && sK[i + 1] == k);
@@ -330,7 +388,7 @@ __global__ void __launch_bounds__(DD_T) k_pd_buckets(const uint32_t* __restrict_
             sV[i] = tV[c0 + i];
         }
         __syncthreads();
-        bitonic_sort128<DD_T>(sK, sV, cm);
+        block_merge_sort128<DD_T, DD_CAP / DD_T>(sK, sV, cm);
         for (uint32_t i = threadIdx.x; i < cm; i += DD_T) {
             tK[c0 + i] = sK[i];
             tV[c0 + i] = (uint32_t)sV[i];
@@ -482,6 +540,10 @@ struct PdBufs {
     uint32_t* lpos;
     uint32_t* hlen;
     uint64_t* hst;
+    uint32_t* hlen2;
+    uint64_t* hst2;
+    uint32_t* prevstart;
+    uint32_t* tmax;
     uint32_t* list_ks;
     uint32_t* list_kl;
     uint32_t* reps[2];
@@ -504,6 +566,10 @@ void carve_pd(Arena& ar, uint32_t n, PdBufs& b) {
     b.lpos = ar.take<uint32_t>(n);
     b.hlen = ar.take<uint32_t>(n);
     b.hst = ar.take<uint64_t>(n);
+    b.hlen2 = ar.take<uint32_t>(n);
+    b.hst2 = ar.take<uint64_t>(n);
+    b.prevstart = ar.take<uint32_t>(n);
+    b.tmax = ar.take<uint32_t>(n / 4096 + 2);
     b.list_ks = ar.take<uint32_t>(n);
     b.list_kl = ar.take<uint32_t>(n);
     b.reps[0] = ar.take<uint32_t>(n);
@@ -563,6 +629,7 @@ sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& sin, const uin
     uint32_t* cur_kl = cur_ks + KBINS;      // KBINS
 
     SSS_CUDA(cudaMemsetAsync(B.cnt, 0, sizeof(uint32_t) * (8 + 4 * KBINS), ctx->stream));
+    SSS_CUDA(cudaMemsetAsync(B.hlen2, 0, sizeof(uint32_t) * n, ctx->stream));
     SSS_TRY(sss_launch(ctx, "pd_init", k_pd_init, dim3((n + 255) / 256), dim3(256), 0, in, sin.lens, B.apos, B.lpos,
                        B.hlen, cnt_ks, cnt_kl, kmin));
     if (kmin > kmax) {
@@ -594,8 +661,27 @@ sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& sin, const uin
         const uint64_t L = 1ull << k;
         uint32_t tmask = 0;
         if (nreps > 0) {
+            // many positions start a group only from this round on: locate their
+            // previous group start, whose L/2-prefix state they share
+            const uint32_t nnew = k > kmin ? ks_off[k + 1] - ks_off[k] : 0;
+            const uint32_t* ps = nullptr;
+            if (run_lcp && k >= 4 && k > kmin && nnew > n / 16) {
+                uint32_t nt = (n + 4095) / 4096;
+                SSS_TRY(sss_launch(ctx, "pd_prevstart", k_pd_ps_tiles, dim3(nt), dim3(1024), 0, in, k - 1, kmin,
+                                   B.prevstart, B.tmax));
+                SSS_TRY(sss_launch(ctx, "pd_prevstart_carry", k_pd_ps_carry, dim3(1), dim3(32), 0, B.tmax, nt));
+                SSS_TRY(sss_launch(ctx, "pd_prevstart_apply", k_pd_ps_apply, dim3((n + 255) / 256), dim3(256), 0, n,
+                                   B.prevstart, (const uint32_t*)B.tmax));
+                ps = B.prevstart;
+            }
+            const bool odd = ((k - kmin) & 1u) != 0;
+            uint64_t* hs_in = odd ? B.hst2 : B.hst;
+            uint32_t* hl_in = odd ? B.hlen2 : B.hlen;
+            uint64_t* hs_out = odd ? B.hst : B.hst2;
+            uint32_t* hl_out = odd ? B.hlen : B.hlen2;
             SSS_TRY(sss_launch(ctx, "pd_hash", k_pd_hash, dim3((nreps + 255) / 256), dim3(256), 0, in, reps, nreps,
-                               (const uint32_t*)B.lpos, B.hst, B.hlen, B.K, B.V, L, Bh));
+                               (const uint32_t*)B.lpos, (const uint64_t*)hs_in, (const uint32_t*)hl_in, hs_out,
+                               hl_out, ps, B.K, B.V, L, Bh));
             if (use_ht) {
                 uint32_t T = 1024;
                 while (T < 2ull * nreps) T <<= 1;

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs
         __syncthreads();
 
         // 4. sort (group, word, index)
-        bitonic_sort128<THREADS>(sHi, sLo, nact);
+        block_merge_sort128<THREADS, ITEMS>(sHi, sLo, nact);
 
         // 5. write back, find new group boundaries, LCP at new boundaries
         for (uint32_t j = tid; j < nact; j += THREADS) {
@@ -210,7 +210,8 @@ constexpr size_t finish_smem(int cap) { return (size_t)cap * (8 + 8 + 4 * 6); }
 __global__ void __launch_bounds__(LG_T) k_lg_ext(const LgTile* __restrict__ tiles, const LgSegInfo* __restrict__ info,
                                                  const uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
                                                  const uint32_t* __restrict__ lens, const uint32_t* __restrict__ perm,
-                                                 uint32_t* segmin) {
+                                                 uint32_t* segmin, uint32_t* __restrict__ extv,
+                                                 uint64_t* __restrict__ extw) {
     LgTile tl = tiles[blockIdx.x];
     LgSegInfo si = info[tl.s];
     uint32_t r = perm[si.seg.start];
@@ -220,22 +221,46 @@ __global__ void __launch_bounds__(LG_T) k_lg_ext(const LgTile* __restrict__ tile
     for (uint32_t q = tl.begin + threadIdx.x; q < tl.end; q += LG_T) {
         if (q == si.seg.start) continue;
         uint32_t e = perm[q];
-        uint32_t v = lcp_extend(chars + offs[e], lens[e], rs, rl, si.seg.depth, &segmin[tl.s]);
+        uint64_t w;
+        bool ok;
+        uint32_t v = lcp_extend_w(chars + offs[e], lens[e], rs, rl, si.seg.depth, &segmin[tl.s], &w, &ok);
+        extv[q] = ok ? v : INF32;  // INF32: agrees with the reference well past the minimum
+        extw[q] = w;
         best = v < best ? v : best;
     }
     best = __reduce_min_sync(SSS_FULL, best);
     if ((threadIdx.x & 31) == 0 && best < *((volatile uint32_t*)&segmin[tl.s])) atomicMin(&segmin[tl.s], best);
 }
 
+// The word at the new depth d' = depth + min: a member agrees with the reference
+// on [depth, depth + v), so its word is the reference's word up to there and its
+// own recorded characters from there on -- no second read of the string.
 __global__ void __launch_bounds__(LG_T) k_lg_keys(const LgTile* __restrict__ tiles, const LgSegInfo* __restrict__ info,
                                                   const uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
                                                   const uint32_t* __restrict__ lens, const uint32_t* __restrict__ perm,
-                                                  const uint32_t* __restrict__ segmin, uint64_t* __restrict__ K) {
+                                                  const uint32_t* __restrict__ segmin,
+                                                  const uint32_t* __restrict__ extv,
+                                                  const uint64_t* __restrict__ extw, uint64_t* __restrict__ K) {
     LgTile tl = tiles[blockIdx.x];
-    uint32_t d = info[tl.s].seg.depth + segmin[tl.s];
+    const LgSegInfo si = info[tl.s];
+    const uint32_t mn = segmin[tl.s];
+    const uint32_t d = si.seg.depth + mn;
+    const uint32_t r = perm[si.seg.start];
+    const uint64_t rw = load_word_be(chars + offs[r], lens[r], d);
     for (uint32_t q = tl.begin + threadIdx.x; q < tl.end; q += LG_T) {
-        uint32_t e = perm[q];
-        K[q] = load_word_be(chars + offs[e], lens[e], d);
+        uint64_t k;
+        if (q == si.seg.start) {
+            k = rw;
+        } else {
+            uint32_t v = extv[q];
+            if (v >= mn + 8) {
+                k = rw;
+            } else {
+                uint32_t o = v - mn;  // characters taken from the reference
+                k = o ? ((rw & (~0ull << (64 - 8 * o))) | (extw[q] >> (8 * o))) : extw[q];
+            }
+        }
+        K[q] = k;
     }
 }
 
@@ -293,7 +318,7 @@ __global__ void __launch_bounds__(BK_T) k_lg_buckets(const LgSegInfo* __restrict
         sLo[i] = tV[bs + i];
     }
     __syncthreads();
-    bitonic_sort128<BK_T>(sHi, sLo, m);
+    block_merge_sort128<BK_T, BK_CAP / BK_T>(sHi, sLo, m);
     for (uint32_t i = threadIdx.x; i < BK_CAP; i += BK_T) {
         uint32_t v = 0;
         if (i < m) {
@@ -374,6 +399,8 @@ struct LsBufs {
     uint64_t* K;
     uint64_t* tK;
     uint32_t* tV;
+    uint32_t* extv;
+    uint64_t* extw;
     Seg* tiny;
     Seg* med;
     Seg* large;
@@ -390,6 +417,8 @@ void carve_ls(Arena& ar, uint32_t n, uint32_t p, LsBufs& b) {
     b.K = ar.take<uint64_t>(n);
     b.tK = ar.take<uint64_t>(n);
     b.tV = ar.take<uint32_t>(n);
+    b.extv = ar.take<uint32_t>(n);
+    b.extw = ar.take<uint64_t>(n);
     b.tiny = ar.take<Seg>(b.cap_tiny);
     b.med = ar.take<Seg>(b.cap_med);
     b.large = ar.take<Seg>(b.cap_large);
@@ -489,10 +518,10 @@ sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p,
         SSS_CUDA(cudaMemsetAsync(B.cnt, 0, sizeof(uint32_t) * 4, ctx->stream));
         SSS_TRY(sss_launch(ctx, "ls_lg_ext", k_lg_ext, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.sp.tiles,
                            (const LgSegInfo*)B.sp.info, in.chars, in.offs, in.lens, (const uint32_t*)perm,
-                           B.segmin));
+                           B.segmin, B.extv, B.extw));
         SSS_TRY(sss_launch(ctx, "ls_lg_keys", k_lg_keys, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.sp.tiles,
                            (const LgSegInfo*)B.sp.info, in.chars, in.offs, in.lens, (const uint32_t*)perm,
-                           (const uint32_t*)B.segmin, B.K));
+                           (const uint32_t*)B.segmin, (const uint32_t*)B.extv, (const uint64_t*)B.extw, B.K));
         SSS_TRY(launch_sp(ctx, B.sp, ns, ntiles, B.K, perm, B.tK, B.tV, "ls_lg_samples", "ls_lg_classify",
                           "ls_lg_offsets", "ls_lg_scatter"));
         SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets, dim3(nbuckets), dim3(BK_T),
