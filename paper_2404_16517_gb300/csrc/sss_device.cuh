@@ -150,6 +150,46 @@ __device__ __forceinline__ uint32_t lcp_extend_w(const uint8_t* __restrict__ a, 
     return r;
 }
 
+// lcp_extend_w with the reference's words [d, d + 8*nref) already in shared
+// memory (refw, zero past the reference's end); only used when
+// min(la, lb) - d <= 8*nref, so every reference word it needs is there.
+__device__ __forceinline__ uint32_t lcp_extend_w_ref(const uint8_t* __restrict__ a, uint32_t la, uint32_t lb,
+                                                     const uint64_t* refw, uint32_t d,
+                                                     const volatile uint32_t* runmin, uint64_t* w, bool* w_ok) {
+    uint32_t m = la < lb ? la : lb;
+    uint32_t r;
+    if (d >= m) {
+        r = 0;
+    } else {
+        uint32_t cap = m - d;
+        WordStream A;
+        A.init(a, la, d);
+        r = cap;
+        for (uint32_t k = 0; k < cap; k += 32) {
+            if (k > 0 && (uint64_t)k >= (uint64_t)(*runmin) + 8u) {
+                *w_ok = false;
+                return k;
+            }
+            uint64_t xa[4];
+            A.next4(xa);
+            bool hit = false;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uint64_t x = xa[i] ^ refw[(k >> 3) + i];
+                if (!hit && x) {
+                    uint32_t c = k + 8 * i + ((uint32_t)__clzll((long long)x) >> 3);
+                    r = c < cap ? c : cap;
+                    hit = true;
+                }
+            }
+            if (hit) break;
+        }
+    }
+    *w = load_word_be(a, la, d + r);
+    *w_ok = true;
+    return r;
+}
+
 // First differing character of two distinct words, counted from the word start.
 __device__ __forceinline__ uint32_t word_lcp(uint64_t a, uint64_t b) {
     uint64_t x = a ^ b;

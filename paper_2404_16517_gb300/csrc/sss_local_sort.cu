@@ -32,6 +32,7 @@ constexpr uint32_t INF32 = 0xFFFFFFFFu;
 constexpr int TINY_T = 64, TINY_CAP = 64;       // segments of 2..64 strings
 constexpr int MED_T = 256, MED_CAP = 2048;      // segments of 65..2048 strings
 constexpr int BK_T = 512, BK_CAP = 4096;        // bucket sort CTA
+constexpr int DIRECT_T = 1024, DIRECT_CAP = 8192;  // whole-segment sort CTA
 constexpr int LG_TARGET = BK_CAP / 2;           // target range-bucket size
 
 struct SegLists {
@@ -212,18 +213,26 @@ __global__ void __launch_bounds__(LG_T) k_lg_ext(const LgTile* __restrict__ tile
                                                  const uint32_t* __restrict__ lens, const uint32_t* __restrict__ perm,
                                                  uint32_t* segmin, uint32_t* __restrict__ extv,
                                                  uint64_t* __restrict__ extw) {
+    constexpr uint32_t NREF = 68;  // 64 words (512 chars) plus a 4-word block of slack
+    __shared__ uint64_t refw[NREF];
     LgTile tl = tiles[blockIdx.x];
     LgSegInfo si = info[tl.s];
     uint32_t r = perm[si.seg.start];
     const uint8_t* rs = chars + offs[r];
     uint32_t rl = lens[r];
+    for (uint32_t i = threadIdx.x; i < NREF; i += LG_T) refw[i] = load_word_be(rs, rl, si.seg.depth + 8 * i);
+    __syncthreads();
     uint32_t best = INF32;
     for (uint32_t q = tl.begin + threadIdx.x; q < tl.end; q += LG_T) {
         if (q == si.seg.start) continue;
         uint32_t e = perm[q];
+        uint32_t le = lens[e];
         uint64_t w;
         bool ok;
-        uint32_t v = lcp_extend_w(chars + offs[e], lens[e], rs, rl, si.seg.depth, &segmin[tl.s], &w, &ok);
+        uint32_t mlen = le < rl ? le : rl;
+        uint32_t v = (mlen <= si.seg.depth + 8 * (NREF - 4))
+                         ? lcp_extend_w_ref(chars + offs[e], le, rl, refw, si.seg.depth, &segmin[tl.s], &w, &ok)
+                         : lcp_extend_w(chars + offs[e], le, rs, rl, si.seg.depth, &segmin[tl.s], &w, &ok);
         extv[q] = ok ? v : INF32;  // INF32: agrees with the reference well past the minimum
         extw[q] = w;
         best = v < best ? v : best;
@@ -261,6 +270,59 @@ __global__ void __launch_bounds__(LG_T) k_lg_keys(const LgTile* __restrict__ til
             }
         }
         K[q] = k;
+    }
+}
+
+// Sort positions [bs, bs+m) (m <= CAP) by (word, index) in one CTA, write the
+// words and indices back, set the LCP at every word change (depth d + first
+// differing byte) and emit the groups of equal words: runs of equal strings
+// get lcp = length, other groups become segments one word deeper.  The first
+// position's LCP is left alone.  Reads srcK/srcV fully before writing K/perm.
+template <int THREADS, int CAP>
+__device__ void sort_emit(unsigned char* smem, uint32_t bs, uint32_t m, uint32_t d, const uint64_t* srcK,
+                          const uint32_t* srcV, const uint32_t* __restrict__ lens, uint64_t* K, uint32_t* perm,
+                          uint32_t* __restrict__ lcp, const SegLists& L, unsigned* err) {
+    constexpr int ITEMS = CAP / THREADS;
+    uint64_t* sHi = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* sLo = sHi + CAP;
+    uint32_t* sA = reinterpret_cast<uint32_t*>(sLo + CAP);
+    uint32_t* sN = sA + CAP;
+    __shared__ uint32_t sh_warp[32];
+    for (uint32_t i = threadIdx.x; i < m; i += THREADS) {
+        sHi[i] = srcK[bs + i];
+        sLo[i] = srcV[bs + i];
+    }
+    __syncthreads();
+    block_merge_sort128<THREADS, ITEMS>(sHi, sLo, m);
+    for (uint32_t i = threadIdx.x; i < CAP; i += THREADS) {
+        uint32_t v = 0;
+        if (i < m) {
+            uint64_t k = sHi[i];
+            K[bs + i] = k;
+            perm[bs + i] = (uint32_t)sLo[i];
+            bool bnd = (i == 0) || (sHi[i - 1] != k);
+            if (bnd && i > 0) lcp[bs + i] = d + word_lcp(sHi[i - 1], k);
+            v = bnd ? i : 0u;
+        }
+        sA[i] = v;
+    }
+    __syncthreads();
+    block_inclusive_max_inplace<THREADS, ITEMS>(sA, m, sh_warp);
+    for (uint32_t i = threadIdx.x; i < m; i += THREADS)
+        if (sA[i] == i) sN[i] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < m; i += THREADS) atomicAdd(&sN[sA[i]], 1u);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < m; i += THREADS) {
+        uint32_t g = sA[i];
+        uint32_t c = sN[g];
+        if (c < 2) continue;
+        uint64_t k = sHi[i];
+        if (word_has_zero(k)) {
+            if (i != g) lcp[bs + i] = lens[(uint32_t)sLo[i]];
+        } else if (i == g) {
+            push_seg(L, bs + g, c, d + 8, err);
+        }
     }
 }
 
@@ -313,42 +375,21 @@ __global__ void __launch_bounds__(BK_T) k_lg_buckets(const LgSegInfo* __restrict
         }
         return;
     }
-    for (uint32_t i = threadIdx.x; i < m; i += BK_T) {
-        sHi[i] = tK[bs + i];
-        sLo[i] = tV[bs + i];
-    }
-    __syncthreads();
-    block_merge_sort128<BK_T, BK_CAP / BK_T>(sHi, sLo, m);
-    for (uint32_t i = threadIdx.x; i < BK_CAP; i += BK_T) {
-        uint32_t v = 0;
-        if (i < m) {
-            uint64_t k = sHi[i];
-            K[bs + i] = k;
-            perm[bs + i] = (uint32_t)sLo[i];
-            bool bnd = (i == 0) || (sHi[i - 1] != k);
-            if (bnd && i > 0) lcp[bs + i] = d + word_lcp(sHi[i - 1], k);
-            v = bnd ? i : 0u;
-        }
-        sA[i] = v;
-    }
-    __syncthreads();
-    block_inclusive_max_inplace<BK_T, ITEMS>(sA, m, sh_warp);
-    for (uint32_t i = threadIdx.x; i < m; i += BK_T)
-        if (sA[i] == i) sN[i] = 0;
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < m; i += BK_T) atomicAdd(&sN[sA[i]], 1u);
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < m; i += BK_T) {
-        uint32_t g = sA[i];
-        uint32_t c = sN[g];
-        if (c < 2) continue;
-        uint64_t k = sHi[i];
-        if (word_has_zero(k)) {
-            if (i != g) lcp[bs + i] = lens[(uint32_t)sLo[i]];
-        } else if (i == g) {
-            push_seg(L, bs + g, c, d + 8, err);
-        }
-    }
+    sort_emit<BK_T, BK_CAP>(smem, bs, m, d, tK, tV, lens, K, perm, lcp, L, err);
+}
+
+// Large segments of at most DIRECT_CAP strings: one CTA sorts the whole segment
+// by its words (no sampling, classification or scatter).
+__global__ void __launch_bounds__(DIRECT_T) k_lg_direct(const LgSegInfo* __restrict__ info, uint32_t first,
+                                                        const uint32_t* __restrict__ segmin,
+                                                        const uint32_t* __restrict__ lens, uint64_t* __restrict__ K,
+                                                        uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
+                                                        SegLists L, unsigned* err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t sidx = first + blockIdx.x;
+    const LgSegInfo si = info[sidx];
+    const uint32_t d = si.seg.depth + segmin[sidx];
+    sort_emit<DIRECT_T, DIRECT_CAP>(smem, si.seg.start, si.seg.size, d, K, perm, lens, K, perm, lcp, L, err);
 }
 
 // LCP at the first position of every non-first, non-empty bucket.
@@ -458,6 +499,8 @@ static sss_status set_ls_attributes(sss_ctx* ctx) {
                                       (int)finish_smem(TINY_CAP)));
         SSS_CUDA(cudaFuncSetAttribute(k_lg_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(BK_CAP * (8 + 8 + 4 + 4))));
+        SSS_CUDA(cudaFuncSetAttribute(k_lg_direct, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(DIRECT_CAP * (8 + 8 + 4 + 4))));
         g_attr_done[ctx->device & 63] = true;
     }
     return SSS_OK;
@@ -508,10 +551,17 @@ sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p,
     uint32_t rounds = 0;
     while (!large.empty()) {
         if (++rounds > 100000u) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: round limit exceeded");
+        // segments that need the sampled partition first, whole-segment sorts after
+        std::stable_partition(large.begin(), large.end(),
+                              [](const Seg& g) { return g.size > (uint32_t)DIRECT_CAP; });
         uint32_t ns = (uint32_t)large.size();
+        uint32_t npart = 0;
+        while (npart < ns && large[npart].size > (uint32_t)DIRECT_CAP) ++npart;
         uint32_t ntiles = 0, nbuckets = 0;
         if (!plan_sp(large, LG_TARGET, B.sp, h_info, h_tiles, &ntiles, &nbuckets))
             return sss_fail(ctx, SSS_ERR_CUDA, "local sort: internal capacity exceeded");
+        const uint32_t ptiles = npart < ns ? h_info[npart].tile0 : ntiles;
+        const uint32_t pbuckets = npart < ns ? h_info[npart].bk_base : nbuckets;
         SSS_TRY(sss_upload(ctx, B.sp.info, h_info, sizeof(LgSegInfo) * ns));
         SSS_TRY(sss_upload(ctx, B.sp.tiles, h_tiles, sizeof(LgTile) * ntiles));
         SSS_CUDA(cudaMemsetAsync(B.segmin, 0xFF, sizeof(uint32_t) * ns, ctx->stream));
@@ -522,14 +572,20 @@ sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p,
         SSS_TRY(sss_launch(ctx, "ls_lg_keys", k_lg_keys, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.sp.tiles,
                            (const LgSegInfo*)B.sp.info, in.chars, in.offs, in.lens, (const uint32_t*)perm,
                            (const uint32_t*)B.segmin, (const uint32_t*)B.extv, (const uint64_t*)B.extw, B.K));
-        SSS_TRY(launch_sp(ctx, B.sp, ns, ntiles, B.K, perm, B.tK, B.tV, "ls_lg_samples", "ls_lg_classify",
-                          "ls_lg_offsets", "ls_lg_scatter"));
-        SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets, dim3(nbuckets), dim3(BK_T),
-                           (size_t)BK_CAP * (8 + 8 + 4 + 4), (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst,
-                           (const uint32_t*)B.segmin, (const uint64_t*)B.tK, (const uint32_t*)B.tV, in.lens, B.K, perm,
-                           lcp, L, ctx->d_err, ns));
-        SSS_TRY(sss_launch(ctx, "ls_lg_seams", k_lg_seams, dim3(ns), dim3(512), 0, (const LgSegInfo*)B.sp.info,
-                           (const uint32_t*)B.sp.bst, (const uint32_t*)B.segmin, (const uint64_t*)B.K, lcp));
+        if (npart > 0) {
+            SSS_TRY(launch_sp(ctx, B.sp, npart, ptiles, B.K, perm, B.tK, B.tV, "ls_lg_samples", "ls_lg_classify",
+                              "ls_lg_offsets", "ls_lg_scatter"));
+            SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets, dim3(pbuckets), dim3(BK_T),
+                               (size_t)BK_CAP * (8 + 8 + 4 + 4), (const LgSegInfo*)B.sp.info,
+                               (const uint32_t*)B.sp.bst, (const uint32_t*)B.segmin, (const uint64_t*)B.tK,
+                               (const uint32_t*)B.tV, in.lens, B.K, perm, lcp, L, ctx->d_err, npart));
+            SSS_TRY(sss_launch(ctx, "ls_lg_seams", k_lg_seams, dim3(npart), dim3(512), 0,
+                               (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst, (const uint32_t*)B.segmin,
+                               (const uint64_t*)B.K, lcp));
+        }
+        SSS_TRY(sss_launch(ctx, "ls_lg_direct", k_lg_direct, dim3(ns - npart), dim3(DIRECT_T),
+                           (size_t)DIRECT_CAP * (8 + 8 + 4 + 4), (const LgSegInfo*)B.sp.info, npart,
+                           (const uint32_t*)B.segmin, in.lens, B.K, perm, lcp, L, ctx->d_err));
         SSS_CUDA(cudaMemcpyAsync(h_cnt, B.cnt, sizeof(uint32_t) * 3, cudaMemcpyDeviceToHost, ctx->stream));
         SSS_CUDA(cudaMemcpyAsync(h_cnt + 3, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
         SSS_CUDA(cudaStreamSynchronize(ctx->stream));

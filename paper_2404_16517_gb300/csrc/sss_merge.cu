@@ -57,6 +57,33 @@ __device__ __forceinline__ int cmp_from(const uint8_t* a, uint32_t la, const uin
     return la < lb ? -1 : (la > lb ? 1 : 0);
 }
 
+// The same comparison by a whole warp: lane k tests the word at d + 256*i + 8k,
+// a ballot finds the first differing word.  Every lane gets the result.
+__device__ __forceinline__ int warp_cmp_from(const uint8_t* a, uint32_t la, const uint8_t* b, uint32_t lb, uint32_t d,
+                                             uint32_t* l) {
+    const int lane = threadIdx.x & 31;
+    uint32_t m = la < lb ? la : lb;
+    for (uint32_t k = d; k < m; k += 256) {
+        uint32_t pos = k + 8 * lane;
+        uint64_t x = 0, y = 0;
+        if (pos < m) {
+            x = load_word_be(a, la, pos);
+            y = load_word_be(b, lb, pos);
+        }
+        uint32_t ne = __ballot_sync(SSS_FULL, x != y);
+        if (ne) {
+            int f = __ffs(ne) - 1;
+            uint64_t xf = __shfl_sync(SSS_FULL, x, f), yf = __shfl_sync(SSS_FULL, y, f);
+            uint32_t c = k + 8 * f + word_lcp(xf, yf);
+            if (c >= m) break;
+            *l = c;
+            return xf < yf ? -1 : 1;
+        }
+    }
+    *l = m;
+    return la < lb ? -1 : (la > lb ? 1 : 0);
+}
+
 __device__ __forceinline__ int cmp_str_from(const Strs& S, uint32_t a, uint32_t b, uint32_t d, uint32_t* l) {
     return cmp_from(S.chars + S.offs[a], tlen(S, a), S.chars + S.offs[b], tlen(S, b), d, l);
 }
@@ -94,10 +121,11 @@ __global__ void k_c_splitters(const uint32_t* __restrict__ smp, const uint32_t* 
     spl[j - 1] = k < 0 ? MINF : smp[sperm[k]];
 }
 
-// bounds[i*(p+1)+j] = #{ s in run i : s <= f_j }, LCP-aware binary search
+// bounds[i*(p+1)+j] = #{ s in run i : s <= f_j }, LCP-aware binary search (one
+// warp per search, warp-wide comparisons)
 __global__ void k_c_bounds(const uint32_t* __restrict__ run_perm, uint32_t n, uint32_t p, Strs S,
                            const uint32_t* __restrict__ spl, uint32_t* __restrict__ bounds) {
-    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (g >= p * (p + 1)) return;
     uint32_t i = g / (p + 1), j = g % (p + 1);
     uint32_t lo = part_lo(n, p, i), hi = part_lo(n, p, i + 1);
@@ -114,7 +142,7 @@ __global__ void k_c_bounds(const uint32_t* __restrict__ run_perm, uint32_t n, ui
             uint32_t mid = (a + b) >> 1;
             uint32_t e = run_perm[lo + mid];
             uint32_t d = la < lb ? la : lb, l;
-            int c = cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, d, &l);
+            int c = warp_cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, d, &l);
             if (c <= 0) {
                 a = mid + 1;
                 la = l;
@@ -125,7 +153,7 @@ __global__ void k_c_bounds(const uint32_t* __restrict__ run_perm, uint32_t n, ui
         }
         res = a;
     }
-    bounds[g] = res;
+    if ((threadIdx.x & 31) == 0) bounds[g] = res;
 }
 
 // ---------------------------------------------------------------------------
@@ -139,6 +167,7 @@ struct Recs {
     uint32_t* tl;
     uint64_t* base;
     uint8_t* chars;
+    uint64_t* head;  // the first 8 characters past h (two-level merge)
 };
 
 // position q of the run layout -> record index; also the record's h and length
@@ -584,11 +613,12 @@ __global__ void k_d2_subspl(const BucketInfo* __restrict__ bi, uint32_t p, uint3
 }
 
 // sb[m*p+i] = number of strings of piece (bucket of m, i) that are <= subspl[m]
+// (one warp per search, warp-wide comparisons)
 __global__ void k_d2_bounds(const uint32_t* __restrict__ run_perm, Strs S, const BucketInfo* __restrict__ bi,
                             uint32_t p, uint32_t nss, const uint32_t* __restrict__ pstart,
                             const uint32_t* __restrict__ psz, const uint32_t* __restrict__ subspl,
                             uint32_t* __restrict__ sb) {
-    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (g >= nss * p) return;
     uint32_t m = g / p, i = g % p;
     uint32_t j = last_le(&bi[0].ss0, p, m, sizeof(BucketInfo) / 4, 0);
@@ -602,7 +632,7 @@ __global__ void k_d2_bounds(const uint32_t* __restrict__ run_perm, Strs S, const
         uint32_t mid = (a + b) >> 1;
         uint32_t e = run_perm[q0 + mid];
         uint32_t d = la < lb ? la : lb, l;
-        int c = cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, d, &l);
+        int c = warp_cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, d, &l);
         if (c <= 0) {
             a = mid + 1;
             la = l;
@@ -611,7 +641,7 @@ __global__ void k_d2_bounds(const uint32_t* __restrict__ run_perm, Strs S, const
             lb = l;
         }
     }
-    sb[g] = a;
+    if ((threadIdx.x & 31) == 0) sb[g] = a;
 }
 
 __device__ __forceinline__ uint32_t bucket_of_sub(const BucketInfo* bi, uint32_t p, uint32_t b) {
@@ -693,6 +723,7 @@ __global__ void k_d2_records(const uint32_t* __restrict__ run_perm, const uint32
     R.idx[r] = s;
     R.h[r] = h;
     R.tl[r] = tl;
+    R.head[r] = load_word_be(S.chars + S.offs[s], tl, h);
     clen[r] = tl - h;
 }
 
@@ -723,17 +754,19 @@ __global__ void k_d2_decode(Strs S, Recs R, const BucketInfo* __restrict__ bi, u
         cmp_from(S.chars + S.offs[ref], tlen(S, ref), S.chars + S.offs[e], tlen(S, e), 0, &l);
         r = l;
     }
-    uint64_t key = load_word_be(R.chars + R.base[s0], R.tl[s0], r);
+    uint32_t e0 = R.idx[s0];
+    uint64_t key = load_word_be(S.chars + S.offs[e0], R.tl[s0], r);
     rr[s0] = r;
     rk[s0] = key;
     for (uint32_t u = s0 + 1; u < s1; ++u) {
         uint32_t h = R.h[u];
+        uint64_t hw = R.head[u];  // characters [h, h+8) of string u
         if (h <= r) {
             r = h;
-            key = load_word_be(R.chars + R.base[u], R.tl[u], r);
+            key = hw;
         } else if (h - r < 8) {
             uint32_t d = h - r;
-            key = (key & (~0ull << (64 - 8 * d))) | (load_word_be(R.chars + R.base[u], R.tl[u], h) >> (8 * d));
+            key = (key & (~0ull << (64 - 8 * d))) | (hw >> (8 * d));
         }
         rr[u] = r;
         rk[u] = key;
@@ -802,16 +835,19 @@ __global__ void __launch_bounds__(D2_T) k_d2_cta(Strs S, Recs R, const uint64_t*
     }
 }
 
-// LCP across sub-bucket boundaries (all outputs written)
+// LCP across sub-bucket boundaries (all outputs written); one warp per seam
 __global__ void k_d2_seams(Strs S, const uint64_t* __restrict__ soff, uint32_t p, uint32_t nsb,
                            const uint32_t* __restrict__ out_perm, uint32_t* __restrict__ out_lcp) {
-    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (b >= nsb) return;
     uint32_t s0 = (uint32_t)soff[(uint64_t)b * p], s1 = (uint32_t)soff[(uint64_t)(b + 1) * p];
     if (s1 == s0) return;
     uint32_t l = 0;
-    if (s0 > 0) cmp_str_from(S, out_perm[s0 - 1], out_perm[s0], 0, &l);
-    out_lcp[s0] = l;
+    if (s0 > 0) {
+        uint32_t a = out_perm[s0 - 1], c = out_perm[s0];
+        warp_cmp_from(S.chars + S.offs[a], tlen(S, a), S.chars + S.offs[c], tlen(S, c), 0, &l);
+    }
+    if ((threadIdx.x & 31) == 0) out_lcp[s0] = l;
 }
 
 // fallback for oversized sub-buckets: the pairwise merge tree over their slices
@@ -917,6 +953,7 @@ void carve_mg(Arena& ar, uint32_t n, uint32_t p, uint32_t v, uint64_t nrecchars,
     b.R.h = ar.take<uint32_t>(n);
     b.R.tl = ar.take<uint32_t>(n);
     b.R.base = ar.take<uint64_t>(n);
+    b.R.head = ar.take<uint64_t>(n);
     b.R.chars = ar.take<uint8_t>(nrecchars + 16);
     b.RA[0] = ar.take<uint32_t>(n);
     b.RA[1] = ar.take<uint32_t>(n);
@@ -1003,7 +1040,7 @@ static sss_status run_partition(sss_ctx* ctx, const StrIn& in, const uint32_t* t
     SSS_TRY(sss_launch(ctx, "c_splitters", k_c_splitters, dim3((p + 127) / 128), dim3(128), 0, (const uint32_t*)b.smp,
                        (const uint32_t*)b.s_perm, ns, p, b.spl));
     uint32_t nb = p * (p + 1);
-    SSS_TRY(sss_launch(ctx, "c_bounds", k_c_bounds, dim3((nb + 127) / 128), dim3(128), 0, run_perm, n, p, S,
+    SSS_TRY(sss_launch(ctx, "c_bounds", k_c_bounds, dim3((nb * 32 + 127) / 128), dim3(128), 0, run_perm, n, p, S,
                        (const uint32_t*)b.spl, b.bounds));
     return SSS_OK;
 }
@@ -1241,7 +1278,7 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
         SSS_TRY(sss_launch(ctx, "d2_subspl", k_d2_subspl, dim3((NSS + 255) / 256), dim3(256), 0,
                            (const BucketInfo*)b.binfo, p, NSS, (const uint32_t*)b.smp2, (const uint32_t*)b.s2perm,
                            b.subspl));
-        SSS_TRY(sss_launch(ctx, "d2_bounds", k_d2_bounds, dim3((NSS * p + 127) / 128), dim3(128), 0, run_perm, S,
+        SSS_TRY(sss_launch(ctx, "d2_bounds", k_d2_bounds, dim3((NSS * p * 32 + 127) / 128), dim3(128), 0, run_perm, S,
                            (const BucketInfo*)b.binfo, p, NSS, (const uint32_t*)b.pstart, (const uint32_t*)b.psz,
                            (const uint32_t*)b.subspl, b.sb));
     }
@@ -1255,9 +1292,6 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
     SSS_TRY(sss_launch(ctx, "d2_records", k_d2_records, dim3((n + 255) / 256), dim3(256), 0, run_perm, run_lcp, n, p,
                        S, (const uint32_t*)b.bounds, (const BucketInfo*)b.binfo, (const uint32_t*)b.sb,
                        (const uint64_t*)b.soff, b.R, b.clen, ctx->d_err));
-    SSS_TRY(scan_u32_u64(ctx, b.clen, n, b.coff, b.btot));
-    SSS_TRY(sss_launch(ctx, "d_copy", k_d_copy, dim3((n + 127) / 128), dim3(128), 0, S, b.R, (const uint64_t*)b.coff,
-                       n));
     // D2: decode, then merge every sub-bucket in one CTA
     SSS_TRY(sss_launch(ctx, "d2_decode", k_d2_decode, dim3((nslices + 127) / 128), dim3(128), 0, S, b.R,
                        (const BucketInfo*)b.binfo, p, NSB, (const uint64_t*)b.soff, (const uint32_t*)b.subspl, b.rr,
@@ -1299,6 +1333,10 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
             groups[w].first = (uint32_t)base[w];
             groups[w].second.assign(sizes.begin() + (size_t)w * p, sizes.begin() + (size_t)(w + 1) * p);
         }
+        // the pairwise tree compares record characters: materialise them
+        SSS_TRY(scan_u32_u64(ctx, b.clen, n, b.coff, b.btot));
+        SSS_TRY(sss_launch(ctx, "d_copy", k_d_copy, dim3((n + 127) / 128), dim3(128), 0, S, b.R,
+                           (const uint64_t*)b.coff, n));
         SSS_TRY(sss_launch(ctx, "d2_fb_init", k_d2_fb_init, dim3(std::min<uint32_t>(nover, 1024)), dim3(256), 0,
                            (const uint64_t*)b.soff, p, (const uint32_t*)b.olist, nover, (const uint32_t*)b.R.h,
                            b.RA[0], b.HA[0]));
@@ -1311,7 +1349,7 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
                            (const uint32_t*)b.RA[cur], (const uint32_t*)b.HA[cur], out_perm, out_lcp));
     }
     // D3
-    return sss_launch(ctx, "d2_seams", k_d2_seams, dim3((NSB + 255) / 256), dim3(256), 0, S, (const uint64_t*)b.soff,
+    return sss_launch(ctx, "d2_seams", k_d2_seams, dim3((NSB * 32 + 255) / 256), dim3(256), 0, S, (const uint64_t*)b.soff,
                       p, NSB, (const uint32_t*)out_perm, out_lcp);
 }
 
