@@ -224,16 +224,10 @@ def config3(scale: int = 0) -> StringSet:
     return suffix_set(3, (1 << 22) >> scale, (1 << 21) >> scale, 256)
 
 
-def instance_set(seed: int, sizes: np.ndarray, len_lo: int, len_hi: int, ratios: np.ndarray,
-                 alphabet: np.ndarray = DNA) -> tuple[StringSet, np.ndarray]:
-    """Independent sort instances packed into one string table.
-
-    Instance k has ``sizes[k]`` strings with lengths uniform in [len_lo, len_hi];
-    string j of instance k copies ``max(0, round(r_k*len) - ceil(log_A n_k) - 1)``
-    chars of the instance's template, then continues uniformly.  Returns the set and
-    ``first`` (u64[m+1]): instance k is strings ``first[k] .. first[k+1]-1``.
-    """
-    a = int(alphabet.shape[0])
+def instance_layout(seed: int, sizes: np.ndarray, len_lo: int, len_hi: int, ratios: np.ndarray, a: int):
+    """Per-string layout of an instance set: (first u64[m+1], lens, offs, copy
+    lengths, instance ids).  String g of instance k copies
+    max(0, round(r_k*len) - ceil(log_a n_k) - 1) template characters."""
     sizes = np.asarray(sizes, dtype=np.int64)
     m = sizes.shape[0]
     first = np.zeros(m + 1, dtype=np.uint64)
@@ -248,16 +242,29 @@ def instance_set(seed: int, sizes: np.ndarray, len_lo: int, len_hi: int, ratios:
     offs = np.zeros(n, dtype=np.uint64)
     if n > 1:
         offs[1:] = np.cumsum(lens[:-1].astype(np.uint64))
+    return first, lens, offs, cp.astype(np.uint32), inst.astype(np.uint32)
+
+
+def instance_set(seed: int, sizes: np.ndarray, len_lo: int, len_hi: int, ratios: np.ndarray,
+                 alphabet: np.ndarray = DNA) -> tuple[StringSet, np.ndarray]:
+    """Independent sort instances packed into one string table.
+
+    Instance k has ``sizes[k]`` strings with lengths uniform in [len_lo, len_hi];
+    string j of instance k copies ``max(0, round(r_k*len) - ceil(log_A n_k) - 1)``
+    chars of the instance's template, then continues uniformly.  Returns the set and
+    ``first`` (u64[m+1]): instance k is strings ``first[k] .. first[k+1]-1``.
+    """
+    a = int(alphabet.shape[0])
+    first, lens, offs, cp, inst = instance_layout(seed, sizes, len_lo, len_hi, ratios, a)
+    n = lens.shape[0]
     N = int(lens.astype(np.uint64).sum())
-    chars = np.empty(N, dtype=np.uint8)
     pos_in = np.arange(N, dtype=np.int64) - np.repeat(offs.astype(np.int64), lens.astype(np.int64))
     owner = np.repeat(np.arange(n, dtype=np.int64), lens.astype(np.int64))
     rand = alphabet[uniform_index(rng(seed, ST_CHARS, np.arange(N, dtype=np.uint64)), a)]
     tmpl_cnt = inst[owner].astype(np.uint64) * _U(1 << 20) + pos_in.astype(np.uint64)
     tmpl = alphabet[uniform_index(rng(seed, ST_TEMPLATE, tmpl_cnt), a)]
-    use_t = pos_in < cp[owner]
-    chars[:] = np.where(use_t, tmpl, rand)
-    ss = StringSet(chars, offs, lens, f"instances(seed={seed},m={m},n={n})")
+    chars = np.where(pos_in < cp[owner].astype(np.int64), tmpl, rand).astype(np.uint8)
+    ss = StringSet(chars, offs, lens, f"instances(seed={seed},m={sizes.shape[0]},n={n})")
     return ss, first
 
 

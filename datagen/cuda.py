@@ -33,6 +33,10 @@ def lib():
     global _lib
     if _lib is None:
         _lib = C.CDLL(build())
+        g = _lib.sssgen_instance_chars
+        g.restype = C.c_int
+        g.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64,
+                      C.c_char_p, C.c_uint32, C.c_void_p]
         f = _lib.sssgen_template_set
         f.restype = C.c_int
         f.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
@@ -64,3 +68,38 @@ def config2(n: int = 4194304, first: int = 0, count: int | None = None, device: 
 
 def config1(device: str = "cuda"):
     return template_set(1, 65536, 100, 4, 42, b"ABCDEFGHIJKLMNOPQRSTUVWXYZ", 0, None, device)
+
+
+def instance_set(seed: int, sizes, len_lo: int, len_hi: int, ratios, alphabet: bytes = b"ACGT", device: str = "cuda"):
+    """Device tensors (chars, offs, lens) and first (numpy u64[m+1]) of an
+    instance set, byte-identical to datagen.instance_set."""
+    import numpy as np
+    import torch
+
+    import datagen
+    first, lens, offs, cp, inst = datagen.instance_layout(seed, np.asarray(sizes), len_lo, len_hi,
+                                                           np.asarray(ratios, dtype=np.float64), len(alphabet))
+    n = lens.shape[0]
+    N = int(lens.astype(np.uint64).sum())
+    chars = torch.empty(max(1, N), dtype=torch.uint8, device=device)
+    t_offs = torch.from_numpy(offs.view(np.int64)).to(device)
+    t_lens = torch.from_numpy(lens.view(np.int32)).to(device)
+    t_cp = torch.from_numpy(cp.view(np.int32)).to(device)
+    t_inst = torch.from_numpy(inst.view(np.int32)).to(device)
+    st = torch.cuda.current_stream(chars.device).cuda_stream
+    rc = lib().sssgen_instance_chars(C.c_void_p(chars.data_ptr()), C.c_void_p(t_offs.data_ptr()),
+                                     C.c_void_p(t_lens.data_ptr()), C.c_void_p(t_cp.data_ptr()),
+                                     C.c_void_p(t_inst.data_ptr()), n, seed, alphabet, len(alphabet), C.c_void_p(st))
+    if rc != 0:
+        raise RuntimeError(f"sssgen_instance_chars failed ({rc})")
+    return chars, t_offs, t_lens, first
+
+
+def config4(m: int = 4096, size_cap: int | None = None, device: str = "cuda"):
+    import numpy as np
+
+    import datagen
+    sizes, r = datagen.config4_sizes(4, m)
+    if size_cap is not None:
+        sizes = np.minimum(sizes, size_cap)
+    return instance_set(4, sizes, 8, 300, r, b"ACGT", device)

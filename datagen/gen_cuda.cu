@@ -55,7 +55,38 @@ __global__ void k_template_set(uint8_t* __restrict__ chars, uint64_t* __restrict
     }
 }
 
+// characters of instance-set strings: string g copies its first cp[g] characters
+// from its instance's template, the rest are uniform (counter = offs[g] + j)
+__global__ void k_instance_chars(uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
+                                 const uint32_t* __restrict__ lens, const uint32_t* __restrict__ cp,
+                                 const uint32_t* __restrict__ inst, uint64_t n, uint64_t kt, uint64_t kc, Alpha al) {
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t o = offs[g];
+        uint32_t l = lens[g], c = cp[g];
+        uint64_t tb = (uint64_t)inst[g] << 20;
+        for (uint32_t j = 0; j < l; ++j) {
+            uint64_t r = j < c ? draw(kt, tb + j) : draw(kc, o + j);
+            chars[o + j] = al.c[uidx(r, al.n)];
+        }
+    }
+}
+
 }  // namespace
+
+extern "C" int sssgen_instance_chars(uint8_t* chars, const uint64_t* offs, const uint32_t* lens, const uint32_t* cp,
+                                     const uint32_t* inst, uint64_t n, uint64_t seed, const uint8_t* alphabet,
+                                     uint32_t alen, void* stream) {
+    if (alen == 0 || alen > 64) return 1;
+    Alpha al{};
+    for (uint32_t k = 0; k < alen; ++k) al.c[k] = alphabet[k];
+    al.n = alen;
+    if (n == 0) return 0;
+    uint32_t grid = (uint32_t)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
+    k_instance_chars<<<grid, 256, 0, (cudaStream_t)stream>>>(chars, offs, lens, cp, inst, n,
+                                                             stream_key(seed, ST_TEMPLATE), stream_key(seed, ST_CHARS),
+                                                             al);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
 
 extern "C" int sssgen_template_set(uint8_t* chars, uint64_t* offs, uint32_t* lens, uint64_t seed, uint64_t n,
                                    uint32_t length, uint32_t ntmpl, uint32_t shared, const uint8_t* alphabet,

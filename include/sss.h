@@ -190,6 +190,30 @@ sss_status sss_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars,
                     const sss_params* params, uint32_t* out_perm, uint32_t* out_lcp,
                     uint32_t* out_dist, uint32_t* out_approx);
 
+/* Batched sorting: m independent instances, instance k being the strings
+ * [first, first + n) of one shared string table of n_table strings.  All
+ * instances are sorted together (stage A over all of them at once: the
+ * instances are the initial segments of one radix sort), which beats one call
+ * per instance by sharing every launch and synchronisation.
+ * instances   : HOST array of m entries; instances must not overlap; p must be
+ *               0 or 1 (SSS_ERR_UNIMPLEMENTED otherwise)
+ * out_perm    : uint32_t[n_table]; out_perm[first + r] = index, relative to
+ *               first, of the instance's r-th smallest string (ties by index)
+ * out_lcp     : uint32_t[n_table]; the instance's LCP array (0 at r = 0)
+ * out_dist    : uint32_t[n_table] or NULL; dist of table string first + i
+ *               within its instance, at position first + i
+ * Positions outside every instance are left with identity order and LCP 0. */
+typedef struct sss_instance {
+    uint64_t first;
+    uint32_t n;
+    uint32_t p;
+} sss_instance;
+
+sss_status sss_sort_batch(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars,
+                          const uint64_t* offsets, const uint32_t* lengths, uint32_t n_table,
+                          const sss_instance* instances, uint32_t m, const sss_params* params,
+                          uint32_t* out_perm, uint32_t* out_lcp, uint32_t* out_dist);
+
 /* ------------------------------------------------------------------------ */
 /* Allocation-free prefix doubling (stage B) for small sets.  This call has no
  * counterpart in the paper; it exists for callers that cannot allocate device

@@ -46,6 +46,10 @@ class sss_params(C.Structure):
                 ("reserved", C.c_uint32 * 4)]
 
 
+class sss_instance(C.Structure):
+    _fields_ = [("first", C.c_uint64), ("n", C.c_uint32), ("p", C.c_uint32)]
+
+
 class sss_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char_p), ("launches", C.c_uint64), ("total_ms", C.c_double), ("timed", C.c_uint64)]
 
@@ -84,6 +88,7 @@ def lib():
             "sss_lcp_merge": (st, [vp, vp, u64, vp, vp, vp, vp, vp, u32, u32, P, vp, vp]),
             "sss_sort": (st, [vp, vp, u64, vp, vp, u32, u32, P, vp, vp, vp, vp]),
             "sss_dist_prefix_noalloc": (st, [vp, u64, vp, vp, u32, P, vp, vp]),
+            "sss_sort_batch": (st, [vp, vp, u64, vp, vp, u32, C.POINTER(sss_instance), u32, P, vp, vp, vp]),
             "sss_set_timing": (st, [vp, C.c_int, C.c_char_p]),
             "sss_kernel_stats": (st, [vp, C.POINTER(sss_kernel_stat), u32, C.POINTER(u32)]),
             "sss_reset_stats": (st, [vp]),
@@ -101,7 +106,7 @@ def exported_symbols() -> list[str]:
     return ["sss_params_default", "sss_create", "sss_destroy", "sss_set_stream", "sss_set_workspace",
             "sss_workspace_bytes", "sss_sync", "sss_status_string", "sss_last_error", "sss_local_sort",
             "sss_dist", "sss_dist_prefix", "sss_partition", "sss_lcp_merge", "sss_sort", "sss_set_timing",
-            "sss_kernel_stats", "sss_reset_stats", "sss_dist_prefix_noalloc"]
+            "sss_kernel_stats", "sss_reset_stats", "sss_dist_prefix_noalloc", "sss_sort_batch"]
 
 
 def params(kmin: int = 0, kmax: int = SSS_KMAX_AUTO, v: int = 2, flags: int = 0, hash_seed: int = 0,
@@ -299,6 +304,25 @@ def sss_dist_prefix_noalloc(chars, offs, lens, prm: sss_params | None = None, ou
     if status != 0:
         raise SssError(status, "sss_dist_prefix_noalloc failed")
     return a
+
+
+def sss_sort_batch(chars, offs, lens, first, sizes, prm: sss_params | None = None, out_perm=None, out_lcp=None,
+                   want_dist: bool = False, ctx: Context | None = None):
+    """Sort independent instances (strings first[k] .. first[k]+sizes[k]-1) of one
+    string table together; returns (perm, lcp, dist or None), perm instance-local."""
+    _check_strings(chars, offs, lens)
+    ctx = ctx or context(chars.device.index)
+    n = lens.numel()
+    m = len(first)
+    arr = (sss_instance * max(1, m))()
+    for k in range(m):
+        arr[k].first, arr[k].n, arr[k].p = int(first[k]), int(sizes[k]), 1
+    op, ol = _out(out_perm, n, chars.device), _out(out_lcp, n, chars.device)
+    d = torch.empty(n, dtype=torch.int32, device=chars.device) if want_dist else None
+    prm = prm or params()
+    ctx._check(lib().sss_sort_batch(ctx.h, _ptr(chars), chars.numel(), _ptr(offs), _ptr(lens), n, arr, m,
+                                    C.byref(prm), _ptr(op), _ptr(ol), _ptr(d)), ctx.h)
+    return op, ol, d
 
 
 def workspace_bytes(n: int, total_len: int, p: int = 1, prm: sss_params | None = None) -> int:

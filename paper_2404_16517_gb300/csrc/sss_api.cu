@@ -427,4 +427,46 @@ sss_status sss_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const 
     return SSS_OK;
 }
 
+sss_status sss_sort_batch(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,
+                          const uint32_t* lengths, uint32_t n_table, const sss_instance* instances, uint32_t m,
+                          const sss_params* params, uint32_t* out_perm, uint32_t* out_lcp, uint32_t* out_dist) {
+    SSS_TRY(check_common(ctx, chars, offsets, lengths, n_table, 1));
+    if (m > 0 && !instances) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "instances must be non-NULL");
+    if (n_table > 0 && (!out_perm || !out_lcp)) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "outputs must be non-NULL");
+    if (m == 0 || n_table == 0) return SSS_OK;
+    std::vector<Seg> segs(m);
+    for (uint32_t k = 0; k < m; ++k) {
+        const sss_instance& I = instances[k];
+        if (I.p > 1) return sss_fail(ctx, SSS_ERR_UNIMPLEMENTED, "batched instances with p > 1");
+        if (I.first > n_table || (uint64_t)I.n > n_table - I.first)
+            return sss_fail(ctx, SSS_ERR_INVALID_ARG, "instance " + std::to_string(k) + " exceeds the string table");
+        segs[k] = Seg{(uint32_t)I.first, I.n, 0, 0};
+    }
+    std::vector<Seg> sorted = segs;
+    std::sort(sorted.begin(), sorted.end(), [](const Seg& x, const Seg& y) { return x.start < y.start; });
+    for (uint32_t k = 1; k < m; ++k)
+        if ((uint64_t)sorted[k - 1].start + sorted[k - 1].size > sorted[k].start)
+            return sss_fail(ctx, SSS_ERR_INVALID_ARG, "instances overlap");
+    cudaSetDevice(ctx->device);
+    sss_params prm = resolve_params(params);
+    StrIn in{chars, n_chars, offsets, lengths, n_table};
+    if (prm.flags & SSS_FLAG_CHECKED) SSS_TRY(checked_input(ctx, in));
+    // work memory: the instance table, then the segment sort
+    Arena cnt;
+    cnt.take<Seg>(m);
+    size_t need = cnt.off + 256 + need_local_sort(n_table, 1, prm);
+    char* ws;
+    SSS_TRY(sss_workspace(ctx, need, &ws));
+    Arena ar{ws, need, 0};
+    Seg* d_inst = ar.take<Seg>(m);
+    void* pin;
+    SSS_TRY(sss_pinned(ctx, sizeof(Seg) * m, &pin));
+    std::copy(segs.begin(), segs.end(), static_cast<Seg*>(pin));
+    SSS_TRY(sss_upload(ctx, d_inst, pin, sizeof(Seg) * m));
+    size_t off = (ar.off + 255) & ~size_t(255);
+    Arena sa{ws + off, need - off, 0};
+    SSS_TRY(impl_sort_segments(ctx, sa, in, segs, prm, out_perm, out_lcp));
+    return impl_batch_finish(ctx, d_inst, m, lengths, out_perm, out_lcp, out_dist);
+}
+
 }  // extern "C"

@@ -155,6 +155,11 @@ struct StrIn {
 sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p, const sss_params& prm,
                            uint32_t* perm, uint32_t* lcp);
 size_t need_local_sort(uint32_t n, uint32_t p, const sss_params& prm);
+// Sort every given segment of positions (each starting at depth 0) independently.
+sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const std::vector<Seg>& init,
+                              const sss_params& prm, uint32_t* perm, uint32_t* lcp);
+sss_status impl_batch_finish(sss_ctx* ctx, const Seg* d_inst, uint32_t m, const uint32_t* lens, uint32_t* perm,
+                             const uint32_t* lcp, uint32_t* dist);
 
 // Finish segments of positions whose strings share their first `depth`
 // characters (stage A's CTA finisher): perm[start..start+size) is sorted by the

@@ -454,7 +454,7 @@ struct LsBufs {
 void carve_ls(Arena& ar, uint32_t n, uint32_t p, LsBufs& b) {
     b.cap_tiny = n / 2 + 2;
     b.cap_med = n / (TINY_CAP + 1) + 2;
-    b.cap_large = n / (MED_CAP + 1) + p + 2;
+    b.cap_large = n / (MED_CAP + 1) + p + 2;  // every large segment holds > MED_CAP strings
     b.K = ar.take<uint64_t>(n);
     b.tK = ar.take<uint64_t>(n);
     b.tV = ar.take<uint32_t>(n);
@@ -508,23 +508,30 @@ static sss_status set_ls_attributes(sss_ctx* ctx) {
 
 sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p, const sss_params& prm,
                            uint32_t* perm, uint32_t* lcp) {
+    std::vector<Seg> init;
+    for (uint32_t i = 0; i < p; ++i) {
+        uint32_t lo = part_lo(in.n, p, i), hi = part_lo(in.n, p, i + 1);
+        init.push_back(Seg{lo, hi - lo, 0, 0});
+    }
+    return impl_sort_segments(ctx, ar, in, init, prm, perm, lcp);
+}
+
+sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const std::vector<Seg>& init,
+                              const sss_params& prm, uint32_t* perm, uint32_t* lcp) {
     (void)prm;
     const uint32_t n = in.n;
     if (n == 0) return SSS_OK;
     LsBufs B;
-    carve_ls(ar, n, p, B);
+    carve_ls(ar, n, 1, B);
     SSS_TRY(set_ls_attributes(ctx));
     SSS_TRY(sss_launch(ctx, "ls_init", k_init_perm, dim3((n + 255) / 256), dim3(256), 0, perm, lcp, n));
 
-    // initial segments: the partitions
+    // initial segments (partitions or instances), by size class
     std::vector<Seg> tiny, med, large;
-    for (uint32_t i = 0; i < p; ++i) {
-        uint32_t lo = part_lo(n, p, i), hi = part_lo(n, p, i + 1);
-        uint32_t sz = hi - lo;
-        if (sz < 2) continue;
-        Seg s{lo, sz, 0, 0};
-        if (sz <= (uint32_t)TINY_CAP) tiny.push_back(s);
-        else if (sz <= (uint32_t)MED_CAP) med.push_back(s);
+    for (const Seg& s : init) {
+        if (s.size < 2) continue;
+        if (s.size <= (uint32_t)TINY_CAP) tiny.push_back(s);
+        else if (s.size <= (uint32_t)MED_CAP) med.push_back(s);
         else large.push_back(s);
     }
     // pinned staging: segment info + tiles + counters
@@ -618,6 +625,36 @@ sss_status impl_finish_segments(sss_ctx* ctx, const Seg* tiny, uint32_t ntiny, c
 
 uint32_t finish_cap_tiny() { return TINY_CAP; }
 uint32_t finish_cap_med() { return MED_CAP; }
+
+// Batched sorts: one CTA per instance turns table positions into
+// instance-local indices and (optionally) computes the instance's dist.
+__global__ void k_batch_finish(const Seg* __restrict__ inst, uint32_t m, const uint32_t* __restrict__ lens,
+                               uint32_t* __restrict__ perm, const uint32_t* __restrict__ lcp,
+                               uint32_t* __restrict__ dist) {
+    for (uint32_t k = blockIdx.x; k < m; k += gridDim.x) {
+        const Seg s = inst[k];
+        for (uint32_t r = threadIdx.x; r < s.size; r += blockDim.x) {
+            uint32_t q = s.start + r;
+            uint32_t g = perm[q];
+            if (dist) {
+                uint32_t left = r > 0 ? lcp[q] : 0;
+                uint32_t right = r + 1 < s.size ? lcp[q + 1] : 0;
+                uint32_t mx = left > right ? left : right;
+                uint64_t d = (uint64_t)mx + 1;
+                dist[g] = d < lens[g] ? (uint32_t)d : lens[g];
+            }
+        }
+        __syncthreads();
+        for (uint32_t r = threadIdx.x; r < s.size; r += blockDim.x) perm[s.start + r] -= s.start;
+        __syncthreads();
+    }
+}
+
+sss_status impl_batch_finish(sss_ctx* ctx, const Seg* d_inst, uint32_t m, const uint32_t* lens, uint32_t* perm,
+                             const uint32_t* lcp, uint32_t* dist) {
+    return sss_launch(ctx, "batch_finish", k_batch_finish, dim3(std::min<uint32_t>(m, 65535u)), dim3(256), 0, d_inst,
+                      m, lens, perm, lcp, dist);
+}
 
 sss_status impl_dist(sss_ctx* ctx, const uint32_t* lens, uint32_t n, const uint32_t* perm, const uint32_t* lcp,
                      uint32_t* dist) {
