@@ -108,6 +108,25 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, ws: int) -> float:
+    """Largest value of x over all ranks (x itself at world size 1).  NCCL
+    reduces a device tensor; gloo a host tensor."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, ws: int, seconds_max: float) -> float:
+    """Whole-job throughput of ws replicas: all ranks' units over the slowest
+    rank's time."""
+    return units_per_rank * ws / seconds_max
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -191,6 +210,14 @@ def main():
     ap.add_argument("--breakdown", action="store_true", help="per-kernel times to stderr")
     ap.add_argument("--merge-ms", type=int, default=0, help="merge segment spacing (0 = library default)")
     ap.add_argument("--p", type=int, default=P, help="partitions (profiling of smaller cases)")
+    ap.add_argument("--workload", default="all", choices=["all", "pdms", "batch", "serve"])
+    ap.add_argument("--batch-instances", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-warmup", type=int, default=1000)
+    ap.add_argument("--serve-load", type=float, default=0.8)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-max-batch", type=int, default=256)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, local = dist_env()
@@ -213,6 +240,13 @@ def main():
         if ws > 1:
             import torch.distributed as dist
             dist.barrier()
+
+    if args.workload in ("batch", "serve"):
+        ctx = sss.context(local)
+        res = bench_batch(args, dev, ctx) if args.workload == "batch" else bench_serve(args, dev)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "n_gpus": ws, **res}), flush=True)
+        return 0
 
     n = args.n
     chars, offs, lens = dgc.config2(n, 0, n)
@@ -266,13 +300,9 @@ def main():
     stats = ctx.kernel_stats()
     ctx.set_timing(False)
     launches = sum(v["launches"] for v in stats.values())
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws)
     ms_step = ms / args.steps
-    value = N * ws / (ms_step / 1e3)
+    value = job_rate(N, ws, ms_step / 1e3)
 
     # roofline of the dominant kernel
     hbm, peak_kind = peaks()
@@ -313,14 +343,9 @@ def main():
             e2e_step()
         a1.record(st)
         torch.cuda.synchronize()
-        ems = a0.elapsed_time(a1) / args.e2e_steps
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(a0.elapsed_time(a1) / args.e2e_steps, ws)
         ok = bool(np.array_equal(h_perm.numpy(), perm.cpu().numpy()))
-        e2e = {"value": N * ws / (ems / 1e3), "unit": "chars/s",
+        e2e = {"value": job_rate(N, ws, ems / 1e3), "unit": "chars/s",
                "h2d_bytes_per_step": int(chars.numel() + 8 * n + 4 * n), "d2h_bytes_per_step": int(8 * n),
                "ms_per_step": ems, "result_read_back": ok}
 
@@ -332,10 +357,7 @@ def main():
             cpu = {"error": str(ex)[:200]}
 
     if args.breakdown and rank == 0:
-        tot = sum(v["total_ms"] for v in stats_all.values())
-        for k, v in sorted(stats_all.items(), key=lambda kv: -kv[1]["total_ms"]):
-            print(f"{k:18s} launches {v['launches']:5d}  {v['total_ms']:8.3f} ms  {100 * v['total_ms'] / tot:5.1f}%",
-                  file=sys.stderr)
+        print_breakdown(stats_all, "pdms")
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "chars/s", "n_gpus": ws, "steps": args.steps,
@@ -352,11 +374,164 @@ def main():
                             "algorithmic_bytes_per_launch": algo, "avg_launch_ms": avg_ms},
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                "kernel_ms_per_step": {k: v["total_ms"] for k, v in stats_all.items()}}
+        if ws == 1 and args.workload == "all":
+            del chars, offs, lens, perm, lcp, dist_t, approx
+            out["batch"] = bench_batch(args, dev, ctx)
+            torch.cuda.empty_cache()
+            out["serving"] = bench_serve(args, dev)
+            out["p50_ms"] = out["serving"].get("p50_ms")
+            out["p99_ms"] = out["serving"].get("p99_ms")
         print(json.dumps(out), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def print_breakdown(stats: dict, title: str):
+    tot = sum(v["total_ms"] for v in stats.values()) or 1.0
+    print(f"-- {title}: {tot:.3f} ms in kernels", file=sys.stderr)
+    for k, v in sorted(stats.items(), key=lambda kv: -kv[1]["total_ms"]):
+        print(f"{k:18s} launches {v['launches']:6d}  {v['total_ms']:9.3f} ms  {100 * v['total_ms'] / tot:5.1f}%",
+              file=sys.stderr)
+
+
+def bench_batch(args, dev, ctx):
+    """4,096 independent instances (sizes log-uniform over 2^6..2^16 strings,
+    lengths 8..300 over ACGT, per-instance D/N ratio 0.1..0.9) sorted by one
+    sss_sort_batch call per step, against one sss_sort call per instance."""
+    import numpy as np
+    import torch
+
+    import datagen.cuda as dgc
+    import paper_2404_16517_gb300 as sss
+    tg = time.perf_counter()
+    chars, offs, lens, first = dgc.config4(args.batch_instances)
+    torch.cuda.synchronize()
+    tg = time.perf_counter() - tg
+    m = len(first) - 1
+    sizes = np.diff(first).astype(np.int64)
+    n = int(first[-1])
+    N = int(lens.to(torch.int64).sum().item())
+    prm = sss.params()
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp = torch.empty(n, dtype=torch.int32, device=dev)
+    _, _, d = sss.sss_sort_batch(chars, offs, lens, first[:-1], sizes, prm, perm, lcp, want_dist=True, ctx=ctx)
+    D = int(d.to(torch.int64).sum().item())
+    del d
+    arr, _ = sss.instance_table(first[:-1], sizes)
+
+    def step():
+        ctx._check(sss.lib().sss_sort_batch(ctx.h, sss._ptr(chars), chars.numel(), sss._ptr(offs), sss._ptr(lens), n,
+                                            arr, m, sss.C.byref(prm), sss._ptr(perm), sss._ptr(lcp), None), ctx.h)
+
+    st = torch.cuda.current_stream(dev)
+    ctx.reset_stats()
+    ctx.set_timing(True, "")
+    step()
+    torch.cuda.synchronize()
+    stats = ctx.kernel_stats()
+    ctx.set_timing(False)
+    launches = sum(v["launches"] for v in stats.values())
+    if args.breakdown:
+        print_breakdown(stats, "batch")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    p_batch = perm.cpu()
+
+    # one sss_sort call per instance (p = 1), same outputs
+    perm2 = torch.empty_like(perm)
+    lcp2 = torch.empty_like(lcp)
+    fi = [int(x) for x in first]
+
+    def per_instance():
+        for k in range(m):
+            a, b = fi[k], fi[k + 1]
+            sss.sss_sort(chars, offs[a:b], lens[a:b], 1, prm, perm2[a:b], lcp2[a:b], ctx=ctx)
+
+    ctx.reset_stats()
+    ctx.set_timing(True, "")
+    per_instance()
+    torch.cuda.synchronize()
+    stats1 = ctx.kernel_stats()
+    ctx.set_timing(False)
+    launches1 = sum(v["launches"] for v in stats1.values())
+    per_instance()
+    torch.cuda.synchronize()
+    steps1 = max(1, min(args.steps, 2))
+    e0.record(st)
+    for _ in range(steps1):
+        per_instance()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1) / steps1
+    same = bool(torch.equal(p_batch, perm2.cpu()) and torch.equal(lcp.cpu(), lcp2.cpu()))
+    hbm, peak_kind = peaks()
+    algo = D + 20 * n
+    return {"workload": f"batch_{m}_instances_2^6..2^16_len8..300_ACGT", "instances": m, "strings": n, "chars": N,
+            "D_over_N": D / N, "ms_per_step": ms, "chars_per_s": N / (ms / 1e3), "strings_per_s": n / (ms / 1e3),
+            "gpu_launches_per_step": launches,
+            "per_instance_calls": {"ms_per_step": ms1, "chars_per_s": N / (ms1 / 1e3), "gpu_launches_per_step": launches1,
+                                   "steps": steps1},
+            "speedup_vs_per_instance": ms1 / ms, "outputs_identical": same,
+            "roofline": {"bound": "hbm", "achieved": algo / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": algo / (ms / 1e3) / 1e9 / hbm, "peak_kind": peak_kind,
+                         "algorithmic_bytes": algo, "model": "D + 20n (dist chars, views, perm, lcp)"},
+            "steps": args.steps, "warmup": args.warmup, "generate_s": tg,
+            "l2": "inputs (%.1f GB of chars) larger than L2; no flush" % (N / 1e9)}
+
+
+def bench_serve(args, dev):
+    """Open-loop Poisson stream of sort requests (sizes lognormal, median 2^14
+    strings, sigma 1.5, capped at 2^24; lengths 16..1000 over A-Z; per-request
+    copy ratio 0.1..0.9) through the request loop under an HBM budget, at a rate
+    of `load` times the saturated rate of a closed-loop warm-up."""
+    import numpy as np
+    import torch
+
+    import datagen
+    import datagen.cuda as dgc
+    from paper_2404_16517_gb300.serve import Request, Server, summarize
+
+    def make(count, seed, rid0=0):
+        sz, rt, gaps, sd = datagen.config5_requests(count, seed=seed)
+        tot = dgc.request_totals(sd, sz)
+        return [Request(rid=rid0 + i, n=int(sz[i]), chars=int(tot[i]), seed=int(sd[i]), ratio=float(rt[i]))
+                for i in range(count)], gaps
+
+    reqs, gaps = make(args.serve_requests, 5)
+    warm, _ = make(args.serve_warmup, 6, rid0=1 << 30)
+    budget = int(args.serve_budget_gb * (1 << 30))
+    srv = Server(device=dev.index, budget_bytes=budget, slots=args.serve_slots,
+                 max_batch_requests=args.serve_max_batch)
+    t0 = srv.run_closed_loop(warm)
+    sat = summarize(warm, t0)
+    lam = args.serve_load * sat["requests_per_s"]
+    arrivals = list(np.cumsum(gaps) / lam)
+    t0 = srv.run_open_loop(reqs, arrivals)
+    st = summarize(reqs, t0)
+    hw = srv.sched.alloc.high_water
+    nb = srv.sched.n_batches
+    mean_batch = sum(srv.sched.batch_sizes) / max(1, nb)
+    srv.close()
+    torch.cuda.synchronize()
+    st.update({"workload": f"serve_{args.serve_requests}_requests_lognormal_2^14_s1.5_len16..1000_AZ",
+               "lambda_per_s": lam, "load": args.serve_load, "saturated_requests_per_s": sat["requests_per_s"],
+               "saturated_chars_per_s": sat["chars_per_s"], "warmup_requests": args.serve_warmup,
+               "budget_bytes": budget, "arena_high_water_bytes": hw, "slots": args.serve_slots,
+               "batches_total": nb, "mean_batch_requests": mean_batch,
+               "max_batch_requests": args.serve_max_batch,
+               "latency": "scheduled arrival to batch completion on the device (includes queueing, admission, "
+                          "on-device generation of the request's strings, sort)"})
+    return st
 
 
 def algorithmic_bytes(kernel: str, n: int, N: int, D: int, Dapprox: int, launches_per_step: float) -> float:

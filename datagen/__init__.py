@@ -283,3 +283,30 @@ def config4(m: int = 4096, size_cap: int | None = None) -> tuple[StringSet, np.n
     if size_cap is not None:
         sizes = np.minimum(sizes, size_cap)
     return instance_set(4, sizes, 8, 300, r, DNA)
+
+
+def config5_requests(count: int = 20000, seed: int = 5, median_log2: float = 14.0, sigma: float = 1.5,
+                     cap: int = 1 << 24):
+    """Serving workload shape: request sizes lognormal (median 2^14 strings,
+    sigma 1.5, capped at 2^24), copy ratio uniform over 0.1..0.9, and unit-rate
+    exponential inter-arrival gaps (scale them by 1/lambda).  Normal draws use
+    Box-Muller on counter-based uniforms.  Returns (sizes, ratios, gaps, seeds)."""
+    i = np.arange(count, dtype=np.uint64)
+    u1 = uniform_float(rng(seed, ST_SIZE, i))
+    u2 = uniform_float(rng(seed, ST_SIZE + 100, i))
+    z = np.sqrt(-2.0 * np.log(np.maximum(u1, 1e-300))) * np.cos(2.0 * np.pi * u2)
+    sizes = np.minimum(cap, np.maximum(1, np.rint(2.0 ** median_log2 * np.exp(sigma * z)))).astype(np.int64)
+    ratios = 0.1 + 0.8 * uniform_float(rng(seed, ST_RATIO, i))
+    gaps = -np.log(np.maximum(1.0 - uniform_float(rng(seed, ST_OFFSET, i)), 1e-300))
+    seeds = rng(seed, ST_TEMPLATE + 100, i)
+    return sizes, ratios, gaps, seeds
+
+
+def request_chars(seed: int, n: int, len_lo: int = 16, len_hi: int = 1000, chunk: int = 1 << 22) -> int:
+    """Total characters of a serving request of n strings (the sum of the same
+    length draws the device generator makes), computed on the host."""
+    tot = 0
+    for a in range(0, n, chunk):
+        i = np.arange(a, min(n, a + chunk), dtype=np.uint64)
+        tot += int((len_lo + uniform_index(rng(seed, ST_LEN, i), len_hi - len_lo + 1)).sum())
+    return tot

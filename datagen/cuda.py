@@ -5,6 +5,7 @@ checked against the numpy generator by the GPU tests."""
 from __future__ import annotations
 
 import ctypes as C
+import threading
 import os
 import subprocess
 import tempfile
@@ -29,18 +30,39 @@ def build(force: bool = False) -> str:
 _lib = None
 
 
+_lib_lock = threading.Lock()
+
+
 def lib():
+    """The generator library, loaded once; the handle is published only after
+    every signature is set (several threads may ask for it at once)."""
     global _lib
-    if _lib is None:
-        _lib = C.CDLL(build())
-        g = _lib.sssgen_instance_chars
-        g.restype = C.c_int
-        g.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64,
-                      C.c_char_p, C.c_uint32, C.c_void_p]
-        f = _lib.sssgen_template_set
-        f.restype = C.c_int
-        f.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
-                      C.c_uint32, C.c_char_p, C.c_uint32, C.c_uint64, C.c_uint64, C.c_void_p]
+    if _lib is not None:
+        return _lib
+    with _lib_lock:
+        if _lib is None:
+            _lib = _configure(C.CDLL(build()))
+    return _lib
+
+
+def _configure(_lib):
+    g = _lib.sssgen_instance_chars
+    g.restype = C.c_int
+    g.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64,
+                  C.c_char_p, C.c_uint32, C.c_void_p]
+    h = _lib.sssgen_request
+    h.restype = C.c_int
+    h.argtypes = [C.c_void_p] * 5 + [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_double, C.c_uint32,
+                                     C.c_char_p, C.c_uint32, C.c_uint64, C.c_void_p]
+    _lib.sssgen_request_scratch_words.restype = C.c_uint64
+    _lib.sssgen_request_totals.restype = C.c_int
+    _lib.sssgen_request_totals.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint32, C.c_uint32,
+                                           C.c_void_p, C.c_void_p]
+    _lib.sssgen_request_scratch_words.argtypes = [C.c_uint64]
+    f = _lib.sssgen_template_set
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
+                  C.c_uint32, C.c_char_p, C.c_uint32, C.c_uint64, C.c_uint64, C.c_void_p]
     return _lib
 
 
@@ -103,3 +125,52 @@ def config4(m: int = 4096, size_cap: int | None = None, device: str = "cuda"):
     if size_cap is not None:
         sizes = np.minimum(sizes, size_cap)
     return instance_set(4, sizes, 8, 300, r, b"ACGT", device)
+
+
+def request_scratch_words(n: int) -> int:
+    """uint64 words of sum scratch that request_into needs for n strings."""
+    return int(lib().sssgen_request_scratch_words(n))
+
+
+def request_into(chars, char_base: int, offs, lens, cp_scratch, sum_scratch, seed: int, n: int, ratio: float,
+                 len_lo: int = 16, len_hi: int = 1000, alphabet: bytes = b"ABCDEFGHIJKLMNOPQRSTUVWXYZ"):
+    """Generate one serving request (n strings, lengths uniform len_lo..len_hi,
+    template copy ratio `ratio`) on the device, on the current stream, without a
+    host synchronisation: lens[0:n], offs[0:n] (absolute, starting at
+    char_base) and chars[char_base : char_base + request_chars(seed, n)].
+    cp_scratch: >= n int32; sum_scratch: >= request_scratch_words(n) int64.
+    The characters depend on (seed, n, ratio) only, not on char_base."""
+    import math
+
+    import torch
+    if n == 0:
+        return
+    assert cp_scratch.numel() >= n and sum_scratch.numel() >= request_scratch_words(n)
+    assert offs.numel() >= n and lens.numel() >= n
+    st = torch.cuda.current_stream(lens.device).cuda_stream
+    logs = int(math.ceil(math.log(max(n, 2)) / math.log(len(alphabet))))
+    rc = lib().sssgen_request(C.c_void_p(chars.data_ptr()), C.c_void_p(offs.data_ptr()),
+                              C.c_void_p(lens.data_ptr()), C.c_void_p(cp_scratch.data_ptr()),
+                              C.c_void_p(sum_scratch.data_ptr()), n, seed & ((1 << 64) - 1), len_lo, len_hi,
+                              float(ratio), logs, alphabet, len(alphabet), char_base, C.c_void_p(st))
+    if rc != 0:
+        raise RuntimeError(f"sssgen_request failed ({rc})")
+
+
+def request_totals(seeds, sizes, len_lo: int = 16, len_hi: int = 1000, device: str = "cuda"):
+    """Total characters of each serving request (numpy int64[m]), computed on
+    the device with the generator's own length draws."""
+    import numpy as np
+    import torch
+    m = len(seeds)
+    if m == 0:
+        return np.zeros(0, dtype=np.int64)
+    t_seeds = torch.from_numpy(np.asarray(seeds, dtype=np.uint64).view(np.int64)).to(device)
+    t_ns = torch.from_numpy(np.asarray(sizes, dtype=np.int64)).to(device)
+    out = torch.empty(m, dtype=torch.int64, device=device)
+    st = torch.cuda.current_stream(out.device).cuda_stream
+    rc = lib().sssgen_request_totals(C.c_void_p(t_seeds.data_ptr()), C.c_void_p(t_ns.data_ptr()), m, len_lo, len_hi,
+                                     C.c_void_p(out.data_ptr()), C.c_void_p(st))
+    if rc != 0:
+        raise RuntimeError(f"sssgen_request_totals failed ({rc})")
+    return out.cpu().numpy()

@@ -57,21 +57,154 @@ __global__ void k_template_set(uint8_t* __restrict__ chars, uint64_t* __restrict
 
 // characters of instance-set strings: string g copies its first cp[g] characters
 // from its instance's template, the rest are uniform (counter = offs[g] + j)
+// (counters are relative to cbase, so a set placed at any offset of a larger
+// buffer gets the same characters; inst == NULL means instance 0 throughout)
 __global__ void k_instance_chars(uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
                                  const uint32_t* __restrict__ lens, const uint32_t* __restrict__ cp,
-                                 const uint32_t* __restrict__ inst, uint64_t n, uint64_t kt, uint64_t kc, Alpha al) {
+                                 const uint32_t* __restrict__ inst, uint64_t n, uint64_t kt, uint64_t kc, Alpha al,
+                                 uint64_t cbase) {
     for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t o = offs[g];
         uint32_t l = lens[g], c = cp[g];
-        uint64_t tb = (uint64_t)inst[g] << 20;
+        uint64_t tb = inst ? (uint64_t)inst[g] << 20 : 0;
         for (uint32_t j = 0; j < l; ++j) {
-            uint64_t r = j < c ? draw(kt, tb + j) : draw(kc, o + j);
+            uint64_t r = j < c ? draw(kt, tb + j) : draw(kc, o - cbase + j);
             chars[o + j] = al.c[uidx(r, al.n)];
         }
     }
 }
 
+// lengths and template-copy lengths of one request's strings (instance layout
+// of datagen.instance_layout for a single instance of ratio r)
+__global__ void k_request_layout(uint32_t* __restrict__ lens, uint32_t* __restrict__ cp, uint64_t n, uint64_t kl,
+                                 uint32_t len_lo, uint32_t span, double ratio, uint32_t logs) {
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t l = len_lo + uidx(draw(kl, g), span);
+        long long c = (long long)rint(ratio * (double)l) - (long long)logs - 1;
+        c = c < 0 ? 0 : c;
+        c = c > l ? l : c;
+        lens[g] = l;
+        cp[g] = (uint32_t)c;
+    }
+}
+
+// offsets = base + exclusive prefix sums of the lengths, in three passes over
+// chunks of CHUNK lengths (chunk sums, scan of the chunk sums, write)
+constexpr uint32_t SCAN_T = 256, SCAN_PER = 16, CHUNK = SCAN_T * SCAN_PER;
+
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* warp_tot, uint64_t* total) {
+    uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint64_t x = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= (uint32_t)d) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t run = 0;
+        for (uint32_t k = 0; k < blockDim.x / 32; ++k) {
+            uint64_t t = warp_tot[k];
+            warp_tot[k] = run;
+            run += t;
+        }
+        *total = run;
+    }
+    __syncthreads();
+    return warp_tot[w] + x - v;
+}
+
+__global__ void k_chunk_sums(const uint32_t* __restrict__ lens, uint64_t n, uint64_t* __restrict__ sums) {
+    __shared__ uint64_t wt[SCAN_T / 32], tot;
+    uint64_t i0 = (uint64_t)blockIdx.x * CHUNK + (uint64_t)threadIdx.x * SCAN_PER;
+    uint64_t s = 0;
+    for (uint32_t k = 0; k < SCAN_PER; ++k)
+        if (i0 + k < n) s += lens[i0 + k];
+    block_excl_scan(s, wt, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(uint64_t* __restrict__ sums, uint64_t nb) {
+    __shared__ uint64_t wt[SCAN_T / 32], tot;
+    uint64_t carry = 0;
+    for (uint64_t b0 = 0; b0 < nb; b0 += SCAN_T) {
+        uint64_t i = b0 + threadIdx.x;
+        uint64_t v = i < nb ? sums[i] : 0;
+        uint64_t e = block_excl_scan(v, wt, &tot);
+        if (i < nb) sums[i] = carry + e;
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void k_write_offs(const uint32_t* __restrict__ lens, uint64_t n, const uint64_t* __restrict__ sums,
+                             uint64_t* __restrict__ offs, uint64_t base) {
+    __shared__ uint64_t wt[SCAN_T / 32], tot;
+    uint64_t i0 = (uint64_t)blockIdx.x * CHUNK + (uint64_t)threadIdx.x * SCAN_PER;
+    uint64_t s = 0;
+    for (uint32_t k = 0; k < SCAN_PER; ++k)
+        if (i0 + k < n) s += lens[i0 + k];
+    uint64_t run = base + sums[blockIdx.x] + block_excl_scan(s, wt, &tot);
+    for (uint32_t k = 0; k < SCAN_PER; ++k)
+        if (i0 + k < n) {
+            offs[i0 + k] = run;
+            run += lens[i0 + k];
+        }
+}
+
+// total characters of each of m requests (one block per request)
+__global__ void k_request_totals(const uint64_t* __restrict__ seeds, const uint64_t* __restrict__ ns, uint64_t m,
+                                 uint32_t len_lo, uint32_t span, uint64_t* __restrict__ out) {
+    __shared__ uint64_t wt[SCAN_T / 32], tot;
+    for (uint64_t r = blockIdx.x; r < m; r += gridDim.x) {
+        uint64_t kl = stream_key(seeds[r], 4), n = ns[r], s = 0;
+        for (uint64_t g = threadIdx.x; g < n; g += blockDim.x) s += len_lo + uidx(draw(kl, g), span);
+        block_excl_scan(s, wt, &tot);
+        if (threadIdx.x == 0) out[r] = tot;
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+extern "C" int sssgen_request_totals(const uint64_t* seeds, const uint64_t* ns, uint64_t m, uint32_t len_lo,
+                                     uint32_t len_hi, uint64_t* out, void* stream) {
+    if (m == 0) return 0;
+    if (len_hi < len_lo) return 1;
+    uint32_t grid = (uint32_t)(m < 65536 ? m : 65536);
+    k_request_totals<<<grid, SCAN_T, 0, (cudaStream_t)stream>>>(seeds, ns, m, len_lo, len_hi - len_lo + 1, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+extern "C" uint64_t sssgen_request_scratch_words(uint64_t n) { return (n + CHUNK - 1) / CHUNK; }
+
+// One request of the serving workload: n strings with lengths uniform over
+// len_lo..len_hi, each copying its first max(0, round(ratio*len) - logs - 1)
+// characters from the request's template, written at chars[char_base ...] with
+// absolute offsets.  cp_scratch: uint32_t[n]; sum_scratch:
+// uint64_t[sssgen_request_scratch_words(n)].  No host synchronisation.
+extern "C" int sssgen_request(uint8_t* chars, uint64_t* offs, uint32_t* lens, uint32_t* cp_scratch,
+                              uint64_t* sum_scratch, uint64_t n, uint64_t seed, uint32_t len_lo, uint32_t len_hi,
+                              double ratio, uint32_t logs, const uint8_t* alphabet, uint32_t alen,
+                              uint64_t char_base, void* stream) {
+    if (alen == 0 || alen > 64 || len_hi < len_lo) return 1;
+    if (n == 0) return 0;
+    Alpha al{};
+    for (uint32_t k = 0; k < alen; ++k) al.c[k] = alphabet[k];
+    al.n = alen;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t grid = (uint32_t)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
+    k_request_layout<<<grid, 256, 0, st>>>(lens, cp_scratch, n, stream_key(seed, 4), len_lo, len_hi - len_lo + 1,
+                                           ratio, logs);
+    uint64_t nb = (n + CHUNK - 1) / CHUNK;
+    if (nb > 0x7fffffffull) return 1;
+    k_chunk_sums<<<(uint32_t)nb, SCAN_T, 0, st>>>(lens, n, sum_scratch);
+    k_scan_sums<<<1, SCAN_T, 0, st>>>(sum_scratch, nb);
+    k_write_offs<<<(uint32_t)nb, SCAN_T, 0, st>>>(lens, n, sum_scratch, offs, char_base);
+    k_instance_chars<<<grid, 256, 0, st>>>(chars, offs, lens, cp_scratch, nullptr, n, stream_key(seed, ST_TEMPLATE),
+                                           stream_key(seed, ST_CHARS), al, char_base);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
 
 extern "C" int sssgen_instance_chars(uint8_t* chars, const uint64_t* offs, const uint32_t* lens, const uint32_t* cp,
                                      const uint32_t* inst, uint64_t n, uint64_t seed, const uint8_t* alphabet,
@@ -84,7 +217,7 @@ extern "C" int sssgen_instance_chars(uint8_t* chars, const uint64_t* offs, const
     uint32_t grid = (uint32_t)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
     k_instance_chars<<<grid, 256, 0, (cudaStream_t)stream>>>(chars, offs, lens, cp, inst, n,
                                                              stream_key(seed, ST_TEMPLATE), stream_key(seed, ST_CHARS),
-                                                             al);
+                                                             al, 0);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 

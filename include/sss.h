@@ -214,6 +214,11 @@ sss_status sss_sort_batch(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars,
                           const sss_instance* instances, uint32_t m, const sss_params* params,
                           uint32_t* out_perm, uint32_t* out_lcp, uint32_t* out_dist);
 
+/* Work memory (bytes) that sss_sort_batch needs for a table of n_table strings
+ * holding m instances: the size a caller-owned workspace (sss_set_workspace)
+ * must have for that call.  Pure host arithmetic; no context needed. */
+size_t sss_batch_workspace_bytes(uint32_t n_table, uint32_t m, const sss_params* params);
+
 /* ------------------------------------------------------------------------ */
 /* Allocation-free prefix doubling (stage B) for small sets.  This call has no
  * counterpart in the paper; it exists for callers that cannot allocate device

@@ -78,6 +78,7 @@ def lib():
             "sss_set_stream": (st, [vp, vp]),
             "sss_set_workspace": (st, [vp, vp, C.c_size_t]),
             "sss_workspace_bytes": (C.c_size_t, [u32, u64, u32, P]),
+            "sss_batch_workspace_bytes": (C.c_size_t, [u32, u32, P]),
             "sss_sync": (st, [vp]),
             "sss_status_string": (C.c_char_p, [st]),
             "sss_last_error": (C.c_char_p, [vp]),
@@ -106,7 +107,8 @@ def exported_symbols() -> list[str]:
     return ["sss_params_default", "sss_create", "sss_destroy", "sss_set_stream", "sss_set_workspace",
             "sss_workspace_bytes", "sss_sync", "sss_status_string", "sss_last_error", "sss_local_sort",
             "sss_dist", "sss_dist_prefix", "sss_partition", "sss_lcp_merge", "sss_sort", "sss_set_timing",
-            "sss_kernel_stats", "sss_reset_stats", "sss_dist_prefix_noalloc", "sss_sort_batch"]
+            "sss_kernel_stats", "sss_reset_stats", "sss_dist_prefix_noalloc", "sss_sort_batch",
+            "sss_batch_workspace_bytes"]
 
 
 def params(kmin: int = 0, kmax: int = SSS_KMAX_AUTO, v: int = 2, flags: int = 0, hash_seed: int = 0,
@@ -306,6 +308,19 @@ def sss_dist_prefix_noalloc(chars, offs, lens, prm: sss_params | None = None, ou
     return a
 
 
+def instance_table(first, sizes):
+    """The sss_instance array (host) of instances (first[k], sizes[k], p = 1)."""
+    import numpy as np
+    m = len(first)
+    rec = np.zeros(max(1, m), dtype=np.dtype([("first", "<u8"), ("n", "<u4"), ("p", "<u4")]))
+    rec["first"][:m] = np.asarray(first, dtype=np.uint64)
+    rec["n"][:m] = np.asarray(sizes, dtype=np.int64).astype(np.uint32)
+    rec["p"][:m] = 1
+    arr = (sss_instance * max(1, m)).from_buffer(rec)
+    arr._keep = rec
+    return arr, m
+
+
 def sss_sort_batch(chars, offs, lens, first, sizes, prm: sss_params | None = None, out_perm=None, out_lcp=None,
                    want_dist: bool = False, ctx: Context | None = None):
     """Sort independent instances (strings first[k] .. first[k]+sizes[k]-1) of one
@@ -313,10 +328,7 @@ def sss_sort_batch(chars, offs, lens, first, sizes, prm: sss_params | None = Non
     _check_strings(chars, offs, lens)
     ctx = ctx or context(chars.device.index)
     n = lens.numel()
-    m = len(first)
-    arr = (sss_instance * max(1, m))()
-    for k in range(m):
-        arr[k].first, arr[k].n, arr[k].p = int(first[k]), int(sizes[k]), 1
+    arr, m = instance_table(first, sizes)
     op, ol = _out(out_perm, n, chars.device), _out(out_lcp, n, chars.device)
     d = torch.empty(n, dtype=torch.int32, device=chars.device) if want_dist else None
     prm = prm or params()
@@ -328,6 +340,11 @@ def sss_sort_batch(chars, offs, lens, first, sizes, prm: sss_params | None = Non
 def workspace_bytes(n: int, total_len: int, p: int = 1, prm: sss_params | None = None) -> int:
     prm = prm or params()
     return int(lib().sss_workspace_bytes(n, total_len, p, C.byref(prm)))
+
+
+def batch_workspace_bytes(n_table: int, m: int, prm: sss_params | None = None) -> int:
+    prm = prm or params()
+    return int(lib().sss_batch_workspace_bytes(n_table, m, C.byref(prm)))
 
 
 def to_device(ss, device="cuda"):

@@ -295,6 +295,16 @@ size_t sss_workspace_bytes(uint32_t n, uint64_t total_len, uint32_t p, const sss
     return need_pipeline(n, total_len, p, prm);
 }
 
+static size_t need_batch(uint32_t n_table, uint32_t m, const sss_params& prm) {
+    Arena cnt;
+    cnt.take<Seg>(m);
+    return cnt.off + 256 + need_local_sort(n_table, 1, prm);
+}
+
+size_t sss_batch_workspace_bytes(uint32_t n_table, uint32_t m, const sss_params* params) {
+    return need_batch(n_table, m, resolve_params(params));
+}
+
 sss_status sss_local_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,
                           const uint32_t* lengths, uint32_t n, uint32_t p, const sss_params* params,
                           uint32_t* out_run_perm, uint32_t* out_run_lcp) {
@@ -452,9 +462,7 @@ sss_status sss_sort_batch(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, 
     StrIn in{chars, n_chars, offsets, lengths, n_table};
     if (prm.flags & SSS_FLAG_CHECKED) SSS_TRY(checked_input(ctx, in));
     // work memory: the instance table, then the segment sort
-    Arena cnt;
-    cnt.take<Seg>(m);
-    size_t need = cnt.off + 256 + need_local_sort(n_table, 1, prm);
+    size_t need = need_batch(n_table, m, prm);
     char* ws;
     SSS_TRY(sss_workspace(ctx, need, &ws));
     Arena ar{ws, need, 0};
