@@ -84,51 +84,23 @@ struct WordStream {
     }
 };
 
-// Number of equal characters of a[d..] and b[d..], capped at min(la, lb) - d.
-// Stops early (returning some value >= *runmin) once it has passed *runmin: the
-// caller only needs the minimum over a group, and runmin only decreases.
-__device__ __forceinline__ uint32_t lcp_extend(const uint8_t* __restrict__ a, uint32_t la,
-                                               const uint8_t* __restrict__ b, uint32_t lb, uint32_t d,
-                                               const volatile uint32_t* runmin) {
-    uint32_t m = la < lb ? la : lb;
-    if (d >= m) return 0;
-    uint32_t cap = m - d;
-    WordStream A, B;
-    A.init(a, la, d);
-    B.init(b, lb, d);
-    for (uint32_t k = 0; k < cap; k += 8) {
-        if (runmin != nullptr && (k & 63) == 0 && k > 0 && k >= *runmin) return k;
-        uint64_t x = A.next() ^ B.next();
-        if (x) {
-            uint32_t r = k + ((uint32_t)__clzll((long long)x) >> 3);
-            return r < cap ? r : cap;
-        }
-    }
-    return cap;
-}
+// Full LCP of a[d..] and b[d..] (capped at min(la, lb) - d and at VCAP), in
+// blocks of 32 characters with independent loads; *w = the 8 characters of `a`
+// at d + v (zero past its end).
+constexpr uint32_t VCAP = (1u << 30) - 1;
 
-// lcp_extend for a member `a` against the segment's reference `b`, in blocks of
-// 32 characters with independent loads.  Besides the LCP v it reports the 8
-// characters of `a` at d + v in *w (then *w_ok = true); a thread that stops early
-// (v >= *runmin + 8, so it cannot set the minimum) reports *w_ok = false.
-__device__ __forceinline__ uint32_t lcp_extend_w(const uint8_t* __restrict__ a, uint32_t la,
-                                                 const uint8_t* __restrict__ b, uint32_t lb, uint32_t d,
-                                                 const volatile uint32_t* runmin, uint64_t* w, bool* w_ok) {
+__device__ __forceinline__ uint32_t lcp_full_w(const uint8_t* __restrict__ a, uint32_t la,
+                                               const uint8_t* __restrict__ b, uint32_t lb, uint32_t d,
+                                               uint64_t* w) {
     uint32_t m = la < lb ? la : lb;
-    uint32_t r;
-    if (d >= m) {
-        r = 0;
-    } else {
+    uint32_t r = 0;
+    if (d < m) {
         uint32_t cap = m - d;
         WordStream A, B;
         A.init(a, la, d);
         B.init(b, lb, d);
         r = cap;
-        for (uint32_t k = 0; k < cap; k += 32) {
-            if (k > 0 && (uint64_t)k >= (uint64_t)(*runmin) + 8u) {
-                *w_ok = false;
-                return k;
-            }
+        for (uint32_t k = 0; k < cap && k < VCAP; k += 32) {
             uint64_t xa[4], xb[4];
             A.next4(xa);
             B.next4(xb);
@@ -145,31 +117,24 @@ __device__ __forceinline__ uint32_t lcp_extend_w(const uint8_t* __restrict__ a, 
             if (hit) break;
         }
     }
+    if (r > VCAP) r = VCAP;
     *w = load_word_be(a, la, d + r);
-    *w_ok = true;
     return r;
 }
 
-// lcp_extend_w with the reference's words [d, d + 8*nref) already in shared
-// memory (refw, zero past the reference's end); only used when
-// min(la, lb) - d <= 8*nref, so every reference word it needs is there.
-__device__ __forceinline__ uint32_t lcp_extend_w_ref(const uint8_t* __restrict__ a, uint32_t la, uint32_t lb,
-                                                     const uint64_t* refw, uint32_t d,
-                                                     const volatile uint32_t* runmin, uint64_t* w, bool* w_ok) {
+// lcp_full_w with the reference's words [d, d + 8*nref) already in shared memory
+// (refw, zero past the reference's end); only used when min(la, lb) - d <=
+// 8*nref, so every reference word it needs is there.
+__device__ __forceinline__ uint32_t lcp_full_w_ref(const uint8_t* __restrict__ a, uint32_t la, uint32_t lb,
+                                                   const uint64_t* refw, uint32_t d, uint64_t* w) {
     uint32_t m = la < lb ? la : lb;
-    uint32_t r;
-    if (d >= m) {
-        r = 0;
-    } else {
+    uint32_t r = 0;
+    if (d < m) {
         uint32_t cap = m - d;
         WordStream A;
         A.init(a, la, d);
         r = cap;
         for (uint32_t k = 0; k < cap; k += 32) {
-            if (k > 0 && (uint64_t)k >= (uint64_t)(*runmin) + 8u) {
-                *w_ok = false;
-                return k;
-            }
             uint64_t xa[4];
             A.next4(xa);
             bool hit = false;
@@ -186,8 +151,81 @@ __device__ __forceinline__ uint32_t lcp_extend_w_ref(const uint8_t* __restrict__
         }
     }
     *w = load_word_be(a, la, d + r);
-    *w_ok = true;
     return r;
+}
+
+// ---------------------------------------------------------------------------
+// Reference-split keys.  All members of a segment share their first d
+// characters; r is the segment's reference member.  For a member s let v =
+// lcp(s[d..], r[d..]), c = s[d+v] and rho = r[d+v] (0 past an end).  Then s < r
+// when c < rho, s > r when c > rho, and c == rho only when s equals r (both
+// ended).  Among the members below r a larger v means closer to r; among those
+// above, a larger v means smaller.  So the 64-bit key
+//     side  (2 bits: 0 below, 1 equal, 2 above)
+//   | vk    (vb bits: v below and equal, vcap - v above)
+//   | chars (8*C bits: s[d+v .. d+v+C), zero past the end)
+// orders the members by string order on their first d + v + C characters.  Two
+// members with equal keys share d + v + C characters (or are equal strings when
+// the chars hold a zero byte); two adjacent distinct keys have lcp d + v + (first
+// differing byte of the chars) when side and v agree, else d + min(v, v').  Every
+// member advances by its own v, so a segment whose members leave a shared prefix
+// one by one (a staircase) splits in a few rounds instead of one round per word.
+//
+// The field widths depend on the reference's remaining length W = |r| - d,
+// which bounds v: vb = bit length of W (at most 30), C = 6, 5 or 4 characters
+// for vb <= 14, 22, 30.  When W >= 2^30 a member agreeing with r on 2^30 - 1
+// characters gets side 1 and v = vcap (its group continues from there).  The
+// format is packed as vb | C << 8.
+__device__ __forceinline__ uint32_t key_fmt(uint32_t rlen, uint32_t d) {
+    uint32_t w = rlen > d ? rlen - d : 0u;
+    uint32_t vb = w ? 32u - (uint32_t)__clz((int)w) : 1u;
+    vb = vb < 30u ? vb : 30u;
+    uint32_t c = vb <= 14u ? 6u : (vb <= 22u ? 5u : 4u);
+    return vb | (c << 8);
+}
+__device__ __forceinline__ uint32_t fmt_chars(uint32_t f) { return f >> 8; }
+
+__device__ __forceinline__ uint64_t ref_key(uint32_t v, uint64_t w, uint32_t rho, uint32_t f) {
+    const uint32_t vb = f & 31u, cb = 8u * (f >> 8);
+    const uint32_t vcap = (1u << vb) - 1u;
+    uint32_t c = (uint32_t)(w >> 56);
+    uint64_t side, vk;
+    if (v >= vcap || c == rho) {
+        side = 1;
+        vk = v < vcap ? v : vcap;
+    } else if (c < rho) {
+        side = 0;
+        vk = v;
+    } else {
+        side = 2;
+        vk = vcap - v;
+    }
+    return (side << 62) | (vk << (62 - vb)) | ((w >> (64 - cb)) << (62 - vb - cb));
+}
+
+__device__ __forceinline__ uint32_t key_v(uint64_t k, uint32_t f) {
+    const uint32_t vb = f & 31u;
+    const uint32_t vcap = (1u << vb) - 1u;
+    uint32_t vk = (uint32_t)(k >> (62 - vb)) & vcap;
+    return (k >> 62) == 2 ? vcap - vk : vk;
+}
+
+// lcp beyond the segment depth of two distinct keys of one segment
+__device__ __forceinline__ uint32_t key_lcp(uint64_t a, uint64_t b, uint32_t f) {
+    const uint32_t vb = f & 31u;
+    if ((a >> (62 - vb)) == (b >> (62 - vb))) {
+        uint64_t x = (a ^ b) << (2 + vb);
+        return key_v(a, f) + (x ? ((uint32_t)__clzll((long long)x) >> 3) : fmt_chars(f));
+    }
+    uint32_t va = key_v(a, f), vbb = key_v(b, f);
+    return va < vbb ? va : vbb;
+}
+
+// the strings of a key ended inside its characters (equal keys = equal strings)
+__device__ __forceinline__ bool key_ended(uint64_t k, uint32_t f) {
+    const uint32_t vb = f & 31u, cb = 8u * (f >> 8);
+    uint64_t x = (k << (2 + vb)) | (~0ull >> cb);
+    return ((x - 0x0101010101010101ull) & ~x & 0x8080808080808080ull) != 0;
 }
 
 // First differing character of two distinct words, counted from the word start.

@@ -2,20 +2,24 @@
 // (Section 3, "Initialization": each PE sorts its local strings; the LCP array
 // is a by-product of sorting).  A6: exact distinguishing prefixes (Section 2).
 //
-// Design (GB300): MSD radix sort over 8-byte big-endian character words.
+// Design (GB300): MSD radix sort with reference-split keys.
 //  * A segment is a run of positions whose strings share their first `depth`
-//    characters.  Before a segment is split, its common prefix beyond `depth` is
-//    found by comparing every member with the segment's first member (running
-//    minimum, early exit) and the depth jumps by that amount ("equal-word skip").
+//    characters.  Every member is compared with the segment's first member (the
+//    reference) from `depth` on: its full LCP v with the reference, its next
+//    characters and which side of the reference it falls on make a 64-bit key
+//    (ref_key in sss_device.cuh) whose order is string order on the first
+//    depth + v + C characters (C = 4..6, by the reference's length).  Each member thus skips its own shared prefix
+//    with the reference; a plain common-prefix skip would only advance the whole
+//    segment by the smallest v.
 //  * Segments of <= 2048 strings are finished inside one CTA: keys are gathered,
-//    sorted in shared memory as (group, word, index) and split, until every group
+//    sorted in shared memory as (group, key, index) and split, until every group
 //    is a single string or a run of equal strings.
-//  * Larger segments take a multi-CTA round: gather the word at the new depth,
-//    sample splitters, classify into range and equality buckets (equal words
-//    always share a bucket), stable scatter, sort each range bucket in shared
-//    memory, and emit the groups of equal words as new segments.
-//  * LCP values fall out at every split: depth + first differing byte of the
-//    two words; equal strings get lcp = their length.
+//  * Larger segments take a multi-CTA round: compute the keys, sample splitters,
+//    classify into range and equality buckets (equal keys always share a
+//    bucket), stable scatter, sort each range bucket in shared memory, and emit
+//    the groups of equal keys as new segments.
+//  * LCP values fall out at every split (key_lcp); equal strings get lcp = their
+//    length.
 #include <algorithm>
 #include <vector>
 
@@ -80,8 +84,9 @@ __global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs
     uint32_t* sV = reinterpret_cast<uint32_t*>(sLo + CAP);  // string index at local position
     uint32_t* sG = sV + CAP;                             // group start of element, DONE when final
     uint32_t* sGD = sG + CAP;                            // depth of group (at its start)
-    uint32_t* sGM = sGD + CAP;                           // running min / member count (at group start)
-    uint32_t* sA = sGM + CAP;                            // scan buffer
+    uint32_t* sGM = sGD + CAP;                           // member count (at group start)
+    uint32_t* sGF = sGM + CAP;                           // key format of the group (at its start)
+    uint32_t* sA = sGF + CAP;                            // scan buffer
     uint32_t* sC = sA + CAP;                             // compacted active positions
     __shared__ uint32_t sh_warp[32];
 
@@ -109,39 +114,35 @@ __global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs
         if (nact == 0) break;
         for (uint32_t i = tid; i < m; i += THREADS)
             if (sG[i] != DONE) sC[sA[i]] = i;
-        for (uint32_t i = tid; i < m; i += THREADS)
-            if (sG[i] == i) sGM[i] = INF32;
         __syncthreads();
 
-        // 2. common prefix of each group beyond its depth (compare with the group's first member)
+        // 2. reference-split key of every member against its group's first member;
+        //    pack (group, key, index)
         for (uint32_t j = tid; j < nact; j += THREADS) {
             uint32_t pos = sC[j];
             uint32_t g = sG[pos];
-            if (pos == g) continue;
+            uint32_t d = sGD[g];
             uint32_t e = sV[pos], r = sV[g];
-            uint32_t v = lcp_extend(chars + offs[e], lens[e], chars + offs[r], lens[r], sGD[g], &sGM[g]);
-            atomicMin(&sGM[g], v);
-        }
-        __syncthreads();
-
-        // 3. gather the word at the new depth; pack (group, word, index)
-        for (uint32_t j = tid; j < nact; j += THREADS) {
-            uint32_t pos = sC[j];
-            uint32_t g = sG[pos];
-            uint32_t d = sGD[g] + sGM[g];
-            uint32_t e = sV[pos];
-            uint64_t k = load_word_be(chars + offs[e], lens[e], d);
+            const uint8_t* rs = chars + offs[r];
+            uint32_t rl = lens[r];
+            uint64_t w;
+            uint32_t v;
+            const uint32_t f = key_fmt(rl, d);
+            if (pos == g) {
+                v = rl > d ? rl - d : 0u;
+                v = v < VCAP ? v : VCAP;
+                w = load_word_be(rs, rl, d + v);
+                sGF[g] = f;
+            } else {
+                v = lcp_full_w(chars + offs[e], lens[e], rs, rl, d, &w);
+            }
+            uint64_t k = ref_key(v, w, (uint32_t)(load_word_be(rs, rl, d + v) >> 56), f);
             sHi[j] = ((uint64_t)g << 48) | (k >> 16);
             sLo[j] = (k << 48) | (uint64_t)e;
         }
         __syncthreads();
-        for (uint32_t j = tid; j < nact; j += THREADS) {
-            uint32_t pos = sC[j];
-            if (sG[pos] == pos) sGD[pos] += sGM[pos];
-        }
-        __syncthreads();
 
-        // 4. sort (group, word, index)
+        // 3. sort (group, key, index)
         block_merge_sort128<THREADS, ITEMS>(sHi, sLo, nact);
 
         // 5. write back, find new group boundaries, LCP at new boundaries
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs
                 uint64_t kp = (hp << 16) | (lp >> 48);
                 if (gp == g) {
                     bnd = (kp != k);
-                    if (bnd) lcp[sg.start + pos] = sGD[g] + word_lcp(kp, k);
+                    if (bnd) lcp[sg.start + pos] = sGD[g] + key_lcp(kp, k, sGF[g]);
                 }
             }
             sA[j] = bnd ? pos : 0u;
@@ -174,11 +175,14 @@ __global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs
         __syncthreads();
 
         // 7. classify: single strings and runs of equal strings are final
-        uint32_t dnew[ITEMS];
+        uint32_t dnew[ITEMS], fnew[ITEMS];
 #pragma unroll
         for (int t = 0; t < ITEMS; ++t) {
             uint32_t j = tid + t * THREADS;
-            if (j < nact) dnew[t] = sGD[(uint32_t)(sHi[j] >> 48)];
+            if (j < nact) {
+                dnew[t] = sGD[(uint32_t)(sHi[j] >> 48)];
+                fnew[t] = sGF[(uint32_t)(sHi[j] >> 48)];
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -191,12 +195,12 @@ __global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs
             uint32_t cnt = sGM[ng];
             if (cnt == 1) {
                 sG[pos] = DONE;
-            } else if (word_has_zero(k)) {
+            } else if (key_ended(k, fnew[t])) {
                 sG[pos] = DONE;
                 if (pos != ng) lcp[sg.start + pos] = lens[(uint32_t)sLo[j]];
             } else {
                 sG[pos] = ng;
-                if (pos == ng) sGD[ng] = dnew[t] + 8;
+                if (pos == ng) sGD[ng] = dnew[t] + key_v(k, fnew[t]) + fmt_chars(fnew[t]);
             }
         }
         __syncthreads();
@@ -204,82 +208,53 @@ __global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs
     for (uint32_t i = tid; i < m; i += THREADS) perm[sg.start + i] = sV[i];
 }
 
-constexpr size_t finish_smem(int cap) { return (size_t)cap * (8 + 8 + 4 * 6); }
+constexpr size_t finish_smem(int cap) { return (size_t)cap * (8 + 8 + 4 * 7); }
 
 // ---------------------------------------------------------------------------
 // Large path.
 __global__ void __launch_bounds__(LG_T) k_lg_ext(const LgTile* __restrict__ tiles, const LgSegInfo* __restrict__ info,
                                                  const uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
                                                  const uint32_t* __restrict__ lens, const uint32_t* __restrict__ perm,
-                                                 uint32_t* segmin, uint32_t* __restrict__ extv,
-                                                 uint64_t* __restrict__ extw) {
+                                                 uint64_t* __restrict__ K, uint32_t* __restrict__ segfmt) {
     constexpr uint32_t NREF = 68;  // 64 words (512 chars) plus a 4-word block of slack
     __shared__ uint64_t refw[NREF];
     LgTile tl = tiles[blockIdx.x];
     LgSegInfo si = info[tl.s];
+    const uint32_t d = si.seg.depth;
     uint32_t r = perm[si.seg.start];
     const uint8_t* rs = chars + offs[r];
     uint32_t rl = lens[r];
-    for (uint32_t i = threadIdx.x; i < NREF; i += LG_T) refw[i] = load_word_be(rs, rl, si.seg.depth + 8 * i);
+    const uint32_t f = key_fmt(rl, d);
+    if (threadIdx.x == 0 && tl.begin == si.seg.start) segfmt[tl.s] = f;
+    for (uint32_t i = threadIdx.x; i < NREF; i += LG_T) refw[i] = load_word_be(rs, rl, d + 8 * i);
     __syncthreads();
-    uint32_t best = INF32;
     for (uint32_t q = tl.begin + threadIdx.x; q < tl.end; q += LG_T) {
-        if (q == si.seg.start) continue;
-        uint32_t e = perm[q];
-        uint32_t le = lens[e];
         uint64_t w;
-        bool ok;
-        uint32_t mlen = le < rl ? le : rl;
-        uint32_t v = (mlen <= si.seg.depth + 8 * (NREF - 4))
-                         ? lcp_extend_w_ref(chars + offs[e], le, rl, refw, si.seg.depth, &segmin[tl.s], &w, &ok)
-                         : lcp_extend_w(chars + offs[e], le, rs, rl, si.seg.depth, &segmin[tl.s], &w, &ok);
-        extv[q] = ok ? v : INF32;  // INF32: agrees with the reference well past the minimum
-        extw[q] = w;
-        best = v < best ? v : best;
-    }
-    best = __reduce_min_sync(SSS_FULL, best);
-    if ((threadIdx.x & 31) == 0 && best < *((volatile uint32_t*)&segmin[tl.s])) atomicMin(&segmin[tl.s], best);
-}
-
-// The word at the new depth d' = depth + min: a member agrees with the reference
-// on [depth, depth + v), so its word is the reference's word up to there and its
-// own recorded characters from there on -- no second read of the string.
-__global__ void __launch_bounds__(LG_T) k_lg_keys(const LgTile* __restrict__ tiles, const LgSegInfo* __restrict__ info,
-                                                  const uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
-                                                  const uint32_t* __restrict__ lens, const uint32_t* __restrict__ perm,
-                                                  const uint32_t* __restrict__ segmin,
-                                                  const uint32_t* __restrict__ extv,
-                                                  const uint64_t* __restrict__ extw, uint64_t* __restrict__ K) {
-    LgTile tl = tiles[blockIdx.x];
-    const LgSegInfo si = info[tl.s];
-    const uint32_t mn = segmin[tl.s];
-    const uint32_t d = si.seg.depth + mn;
-    const uint32_t r = perm[si.seg.start];
-    const uint64_t rw = load_word_be(chars + offs[r], lens[r], d);
-    for (uint32_t q = tl.begin + threadIdx.x; q < tl.end; q += LG_T) {
-        uint64_t k;
+        uint32_t v;
         if (q == si.seg.start) {
-            k = rw;
+            v = rl > d ? rl - d : 0u;
+            v = v < VCAP ? v : VCAP;
+            w = load_word_be(rs, rl, d + v);
         } else {
-            uint32_t v = extv[q];
-            if (v >= mn + 8) {
-                k = rw;
-            } else {
-                uint32_t o = v - mn;  // characters taken from the reference
-                k = o ? ((rw & (~0ull << (64 - 8 * o))) | (extw[q] >> (8 * o))) : extw[q];
-            }
+            uint32_t e = perm[q];
+            uint32_t le = lens[e];
+            uint32_t mlen = le < rl ? le : rl;
+            v = (mlen <= d + 8 * (NREF - 4)) ? lcp_full_w_ref(chars + offs[e], le, rl, refw, d, &w)
+                                             : lcp_full_w(chars + offs[e], le, rs, rl, d, &w);
         }
-        K[q] = k;
+        uint32_t rho = (v >> 3) < NREF ? (uint32_t)(refw[v >> 3] >> (56 - 8 * (v & 7))) & 0xFFu
+                                       : (uint32_t)(load_word_be(rs, rl, d + v) >> 56);
+        K[q] = ref_key(v, w, rho, f);
     }
 }
 
-// Sort positions [bs, bs+m) (m <= CAP) by (word, index) in one CTA, write the
-// words and indices back, set the LCP at every word change (depth d + first
-// differing byte) and emit the groups of equal words: runs of equal strings
-// get lcp = length, other groups become segments one word deeper.  The first
-// position's LCP is left alone.  Reads srcK/srcV fully before writing K/perm.
+// Sort positions [bs, bs+m) (m <= CAP) by (key, index) in one CTA, write the
+// keys and indices back, set the LCP at every key change (d + key_lcp) and emit
+// the groups of equal keys: runs of equal strings get lcp = length, other groups
+// become segments at depth d + v + C.  The first position's LCP is left alone.
+// Reads srcK/srcV fully before writing K/perm.
 template <int THREADS, int CAP>
-__device__ void sort_emit(unsigned char* smem, uint32_t bs, uint32_t m, uint32_t d, const uint64_t* srcK,
+__device__ void sort_emit(unsigned char* smem, uint32_t bs, uint32_t m, uint32_t d, uint32_t f, const uint64_t* srcK,
                           const uint32_t* srcV, const uint32_t* __restrict__ lens, uint64_t* K, uint32_t* perm,
                           uint32_t* __restrict__ lcp, const SegLists& L, unsigned* err) {
     constexpr int ITEMS = CAP / THREADS;
@@ -301,7 +276,7 @@ __device__ void sort_emit(unsigned char* smem, uint32_t bs, uint32_t m, uint32_t
             K[bs + i] = k;
             perm[bs + i] = (uint32_t)sLo[i];
             bool bnd = (i == 0) || (sHi[i - 1] != k);
-            if (bnd && i > 0) lcp[bs + i] = d + word_lcp(sHi[i - 1], k);
+            if (bnd && i > 0) lcp[bs + i] = d + key_lcp(sHi[i - 1], k, f);
             v = bnd ? i : 0u;
         }
         sA[i] = v;
@@ -318,19 +293,19 @@ __device__ void sort_emit(unsigned char* smem, uint32_t bs, uint32_t m, uint32_t
         uint32_t c = sN[g];
         if (c < 2) continue;
         uint64_t k = sHi[i];
-        if (word_has_zero(k)) {
+        if (key_ended(k, f)) {
             if (i != g) lcp[bs + i] = lens[(uint32_t)sLo[i]];
         } else if (i == g) {
-            push_seg(L, bs + g, c, d + 8, err);
+            push_seg(L, bs + g, c, d + key_v(k, f) + fmt_chars(f), err);
         }
     }
 }
 
 // One CTA per (segment, bucket).  Range buckets are sorted in shared memory;
-// groups of equal words become new segments one word deeper.
+// groups of equal keys become new segments at depth d + v + C.
 __global__ void __launch_bounds__(BK_T) k_lg_buckets(const LgSegInfo* __restrict__ info,
                                                      const uint32_t* __restrict__ bst,
-                                                     const uint32_t* __restrict__ segmin,
+                                                     const uint32_t* __restrict__ segfmt,
                                                      const uint64_t* __restrict__ tK, const uint32_t* __restrict__ tV,
                                                      const uint32_t* __restrict__ lens, uint64_t* __restrict__ K,
                                                      uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
@@ -354,7 +329,8 @@ __global__ void __launch_bounds__(BK_T) k_lg_buckets(const LgSegInfo* __restrict
     }
     uint32_t m = be - bs;
     if (m == 0) return;
-    uint32_t d = si.seg.depth + segmin[sidx];
+    uint32_t d = si.seg.depth;
+    const uint32_t f = segfmt[sidx];
     bool eq = (b & 1u) != 0;
     if (eq || m > (uint32_t)BK_CAP) {
         for (uint32_t q = bs + threadIdx.x; q < be; q += BK_T) {
@@ -364,45 +340,47 @@ __global__ void __launch_bounds__(BK_T) k_lg_buckets(const LgSegInfo* __restrict
         if (threadIdx.x == 0) {
             if (eq) {
                 uint64_t k = tK[bs];
-                if (m >= 2 && !word_has_zero(k)) push_seg(L, bs, m, d + 8, err);
+                if (m >= 2 && !key_ended(k, f)) push_seg(L, bs, m, d + key_v(k, f) + fmt_chars(f), err);
             } else {
                 push_seg(L, bs, m, d, err);  // oversized range bucket: another round at this depth
             }
         }
-        if (eq && m >= 2 && word_has_zero(tK[bs])) {
+        if (eq && m >= 2 && key_ended(tK[bs], f)) {
             // a run of equal strings: lcp = length inside the run
             for (uint32_t q = bs + 1 + threadIdx.x; q < be; q += BK_T) lcp[q] = lens[tV[q]];
         }
         return;
     }
-    sort_emit<BK_T, BK_CAP>(smem, bs, m, d, tK, tV, lens, K, perm, lcp, L, err);
+    sort_emit<BK_T, BK_CAP>(smem, bs, m, d, f, tK, tV, lens, K, perm, lcp, L, err);
 }
 
 // Large segments of at most DIRECT_CAP strings: one CTA sorts the whole segment
-// by its words (no sampling, classification or scatter).
+// by its keys (no sampling, classification or scatter).
 __global__ void __launch_bounds__(DIRECT_T) k_lg_direct(const LgSegInfo* __restrict__ info, uint32_t first,
-                                                        const uint32_t* __restrict__ segmin,
+                                                        const uint32_t* __restrict__ segfmt,
                                                         const uint32_t* __restrict__ lens, uint64_t* __restrict__ K,
                                                         uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
                                                         SegLists L, unsigned* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t sidx = first + blockIdx.x;
     const LgSegInfo si = info[sidx];
-    const uint32_t d = si.seg.depth + segmin[sidx];
-    sort_emit<DIRECT_T, DIRECT_CAP>(smem, si.seg.start, si.seg.size, d, K, perm, lens, K, perm, lcp, L, err);
+    const uint32_t d = si.seg.depth;
+    sort_emit<DIRECT_T, DIRECT_CAP>(smem, si.seg.start, si.seg.size, d, segfmt[sidx], K, perm, lens, K, perm, lcp,
+                                    L, err);
 }
 
 // LCP at the first position of every non-first, non-empty bucket.
 __global__ void __launch_bounds__(512) k_lg_seams(const LgSegInfo* __restrict__ info, const uint32_t* __restrict__ bst,
-                                                  const uint32_t* __restrict__ segmin, const uint64_t* __restrict__ K,
+                                                  const uint32_t* __restrict__ segfmt, const uint64_t* __restrict__ K,
                                                   uint32_t* __restrict__ lcp) {
     LgSegInfo si = info[blockIdx.x];
     uint32_t nbk = 2 * si.nb - 1;
-    uint32_t d = si.seg.depth + segmin[blockIdx.x];
+    uint32_t d = si.seg.depth;
+    const uint32_t f = segfmt[blockIdx.x];
     for (uint32_t b = threadIdx.x; b < nbk; b += 512) {
         uint32_t bs = bst[si.bst_base + b], be = bst[si.bst_base + b + 1];
         if (be > bs && bs > si.seg.start && be <= si.seg.start + si.seg.size)
-            lcp[bs] = d + word_lcp(K[bs - 1], K[bs]);
+            lcp[bs] = d + key_lcp(K[bs - 1], K[bs], f);
     }
 }
 
@@ -440,13 +418,11 @@ struct LsBufs {
     uint64_t* K;
     uint64_t* tK;
     uint32_t* tV;
-    uint32_t* extv;
-    uint64_t* extw;
     Seg* tiny;
     Seg* med;
     Seg* large;
     uint32_t* cnt;
-    uint32_t* segmin;
+    uint32_t* segfmt;
     SpBufs sp;
     uint32_t cap_tiny, cap_med, cap_large;
 };
@@ -458,13 +434,11 @@ void carve_ls(Arena& ar, uint32_t n, uint32_t p, LsBufs& b) {
     b.K = ar.take<uint64_t>(n);
     b.tK = ar.take<uint64_t>(n);
     b.tV = ar.take<uint32_t>(n);
-    b.extv = ar.take<uint32_t>(n);
-    b.extw = ar.take<uint64_t>(n);
     b.tiny = ar.take<Seg>(b.cap_tiny);
     b.med = ar.take<Seg>(b.cap_med);
     b.large = ar.take<Seg>(b.cap_large);
     b.cnt = ar.take<uint32_t>(4);
-    b.segmin = ar.take<uint32_t>(b.cap_large);
+    b.segfmt = ar.take<uint32_t>(b.cap_large);
     carve_sp(ar, n, b.cap_large, b.sp);
 }
 
@@ -571,28 +545,24 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
         const uint32_t pbuckets = npart < ns ? h_info[npart].bk_base : nbuckets;
         SSS_TRY(sss_upload(ctx, B.sp.info, h_info, sizeof(LgSegInfo) * ns));
         SSS_TRY(sss_upload(ctx, B.sp.tiles, h_tiles, sizeof(LgTile) * ntiles));
-        SSS_CUDA(cudaMemsetAsync(B.segmin, 0xFF, sizeof(uint32_t) * ns, ctx->stream));
         SSS_CUDA(cudaMemsetAsync(B.cnt, 0, sizeof(uint32_t) * 4, ctx->stream));
         SSS_TRY(sss_launch(ctx, "ls_lg_ext", k_lg_ext, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.sp.tiles,
-                           (const LgSegInfo*)B.sp.info, in.chars, in.offs, in.lens, (const uint32_t*)perm,
-                           B.segmin, B.extv, B.extw));
-        SSS_TRY(sss_launch(ctx, "ls_lg_keys", k_lg_keys, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.sp.tiles,
-                           (const LgSegInfo*)B.sp.info, in.chars, in.offs, in.lens, (const uint32_t*)perm,
-                           (const uint32_t*)B.segmin, (const uint32_t*)B.extv, (const uint64_t*)B.extw, B.K));
+                           (const LgSegInfo*)B.sp.info, in.chars, in.offs, in.lens, (const uint32_t*)perm, B.K,
+                           B.segfmt));
         if (npart > 0) {
             SSS_TRY(launch_sp(ctx, B.sp, npart, ptiles, B.K, perm, B.tK, B.tV, "ls_lg_samples", "ls_lg_classify",
                               "ls_lg_offsets", "ls_lg_scatter"));
             SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets, dim3(pbuckets), dim3(BK_T),
                                (size_t)BK_CAP * (8 + 8 + 4 + 4), (const LgSegInfo*)B.sp.info,
-                               (const uint32_t*)B.sp.bst, (const uint32_t*)B.segmin, (const uint64_t*)B.tK,
+                               (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt, (const uint64_t*)B.tK,
                                (const uint32_t*)B.tV, in.lens, B.K, perm, lcp, L, ctx->d_err, npart));
             SSS_TRY(sss_launch(ctx, "ls_lg_seams", k_lg_seams, dim3(npart), dim3(512), 0,
-                               (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst, (const uint32_t*)B.segmin,
+                               (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt,
                                (const uint64_t*)B.K, lcp));
         }
         SSS_TRY(sss_launch(ctx, "ls_lg_direct", k_lg_direct, dim3(ns - npart), dim3(DIRECT_T),
                            (size_t)DIRECT_CAP * (8 + 8 + 4 + 4), (const LgSegInfo*)B.sp.info, npart,
-                           (const uint32_t*)B.segmin, in.lens, B.K, perm, lcp, L, ctx->d_err));
+                           (const uint32_t*)B.segfmt, in.lens, B.K, perm, lcp, L, ctx->d_err));
         SSS_CUDA(cudaMemcpyAsync(h_cnt, B.cnt, sizeof(uint32_t) * 3, cudaMemcpyDeviceToHost, ctx->stream));
         SSS_CUDA(cudaMemcpyAsync(h_cnt + 3, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
         SSS_CUDA(cudaStreamSynchronize(ctx->stream));
