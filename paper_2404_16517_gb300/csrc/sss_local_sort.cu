@@ -30,10 +30,10 @@
 namespace {
 
 constexpr uint32_t DONE = 0xFFFFFFFFu;
-constexpr uint32_t INF32 = 0xFFFFFFFFu;
 
 // size classes
-constexpr int TINY_T = 64, TINY_CAP = 64;       // segments of 2..64 strings
+constexpr int WARP_CAP = 32, WF_WARPS = 8;      // segments of 2..32 strings: one warp each
+constexpr int TINY_T = 64, TINY_CAP = 64;       // segments of 33..64 strings
 constexpr int MED_T = 256, MED_CAP = 2048;      // segments of 65..2048 strings
 constexpr int BK_T = 512, BK_CAP = 4096;        // bucket sort CTA
 constexpr int DIRECT_T = 1024, DIRECT_CAP = 8192;  // whole-segment sort CTA
@@ -43,14 +43,19 @@ struct SegLists {
     Seg* tiny;
     Seg* med;
     Seg* large;
-    uint32_t* cnt;  // [0] tiny, [1] med, [2] large
+    uint32_t* cnt;  // [0] tiny, [1] med, [2] large, [3] warp
     uint32_t cap_tiny, cap_med, cap_large;
+    Seg* warp;
+    uint32_t cap_warp;
 };
 
 __device__ __forceinline__ void push_seg(const SegLists& L, uint32_t start, uint32_t size, uint32_t depth,
                                          unsigned* err) {
     Seg s{start, size, depth, 0};
-    if (size <= (uint32_t)TINY_CAP) {
+    if (size <= (uint32_t)WARP_CAP) {
+        uint32_t i = atomicAdd(&L.cnt[3], 1u);
+        if (i < L.cap_warp) L.warp[i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
+    } else if (size <= (uint32_t)TINY_CAP) {
         uint32_t i = atomicAdd(&L.cnt[0], 1u);
         if (i < L.cap_tiny) L.tiny[i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
     } else if (size <= (uint32_t)MED_CAP) {
@@ -208,6 +213,119 @@ __global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs
     for (uint32_t i = tid; i < m; i += THREADS) perm[sg.start + i] = sV[i];
 }
 
+// Warp finisher: one warp completely sorts one segment of <= 32 strings, lane i
+// holding position i.  Same rounds as the CTA finisher (reference-split key of
+// every unfinished member against its group's first member, sort by (group,
+// key, index), split), with the sort a 32-lane bitonic network in registers.
+__device__ __forceinline__ void warp_cas128(uint64_t& hi, uint64_t& lo, uint32_t lane, uint32_t j, bool up) {
+    uint64_t ohi = __shfl_xor_sync(SSS_FULL, hi, j), olo = __shfl_xor_sync(SSS_FULL, lo, j);
+    bool keep_min = (((lane & j) == 0) == up);
+    bool other_less = key128_less(ohi, olo, hi, lo);
+    if (keep_min ? other_less : key128_less(hi, lo, ohi, olo)) {
+        hi = ohi;
+        lo = olo;
+    }
+}
+
+__global__ void __launch_bounds__(32 * WF_WARPS) k_finish_warp(const Seg* __restrict__ segs, uint32_t nseg,
+                                                               const uint8_t* __restrict__ chars,
+                                                               const uint64_t* __restrict__ offs,
+                                                               const uint32_t* __restrict__ lens,
+                                                               uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
+                                                               unsigned* err) {
+    constexpr uint64_t DONE_BIT = 1ull << 47;  // in the low word, above the 32-bit index
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t sidx = blockIdx.x * WF_WARPS + (threadIdx.x >> 5);
+    if (sidx >= nseg) return;  // uniform per warp
+    const Seg sg = segs[sidx];
+    const uint32_t m = sg.size <= 32u ? sg.size : 32u;
+    const bool live = lane < m;
+    uint32_t e = live ? perm[sg.start + lane] : 0u;
+    uint32_t len = live ? lens[e] : 0u;
+    uint32_t g = 0, gd = sg.depth;
+    bool done = !live;
+    uint32_t iter = 0;
+    for (;; ++iter) {
+        if (__ballot_sync(SSS_FULL, !done) == 0) break;
+        if (iter > 4u * 32u + 8u) {
+            if (lane == 0) atomicOr(err, ERRBIT_OVERFLOW);
+            break;
+        }
+        const uint32_t r = __shfl_sync(SSS_FULL, e, g);
+        const uint32_t rl = __shfl_sync(SSS_FULL, len, g);
+        const uint32_t f = key_fmt(rl, gd);
+        uint64_t hi, lo;
+        if (!done) {
+            const uint8_t* rs = chars + offs[r];
+            uint64_t w;
+            uint32_t v;
+            if (lane == g) {
+                v = rl > gd ? rl - gd : 0u;
+                v = v < VCAP ? v : VCAP;
+                w = load_word_be(rs, rl, gd + v);
+            } else {
+                v = lcp_full_w(chars + offs[e], len, rs, rl, gd, &w);
+            }
+            uint64_t k = ref_key(v, w, (uint32_t)(load_word_be(rs, rl, gd + v) >> 56), f);
+            hi = ((uint64_t)g << 48) | (k >> 16);
+            lo = (k << 48) | (uint64_t)e;
+        } else if (live) {
+            hi = (uint64_t)lane << 48;  // a finished string is the only member of group `lane`
+            lo = DONE_BIT | (uint64_t)e;
+        } else {
+            hi = ~0ull;
+            lo = ~0ull;
+        }
+#pragma unroll
+        for (uint32_t kk = 2; kk <= 32; kk <<= 1) {
+            const bool up = (lane & kk) == 0 || kk == 32;
+#pragma unroll
+            for (uint32_t j = kk >> 1; j > 0; j >>= 1) warp_cas128(hi, lo, lane, j, up);
+        }
+        // lane j now holds the j-th position of the segment; groups kept their ranges
+        const uint32_t gg = (uint32_t)(hi >> 48);
+        const uint64_t k = (hi << 16) | (lo >> 48);
+        const bool fin = !live || (lo & DONE_BIT);
+        e = (uint32_t)lo;
+        len = live ? lens[e] : 0u;
+        const uint64_t hp = __shfl_up_sync(SSS_FULL, hi, 1), lp = __shfl_up_sync(SSS_FULL, lo, 1);
+        const uint32_t gp = (uint32_t)(hp >> 48);
+        const uint64_t kp = (hp << 16) | (lp >> 48);
+        bool bnd = true;
+        if (lane > 0 && !fin && gp == gg && !(lp & DONE_BIT)) {
+            bnd = (kp != k);
+            if (bnd) lcp[sg.start + lane] = gd + key_lcp(kp, k, f);
+        }
+        // new group start: inclusive max-scan of boundary positions
+        uint32_t ng = bnd ? lane : 0u;
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(SSS_FULL, ng, o);
+            if (lane >= o) ng = ng > y ? ng : y;
+        }
+        const unsigned bm = __ballot_sync(SSS_FULL, bnd);
+        const unsigned after = lane < 31 ? (bm & (~0u << (lane + 1))) : 0u;
+        const uint32_t end = after ? (uint32_t)(__ffs(after) - 1) : m;
+        const uint32_t cnt = (end > ng ? end : ng + 1) - ng;
+        if (!fin) {
+            if (cnt == 1) {
+                done = true;
+            } else if (key_ended(k, f)) {
+                done = true;
+                if (lane != ng) lcp[sg.start + lane] = len;
+            } else {
+                done = false;
+                g = ng;
+                gd = gd + key_v(k, f) + fmt_chars(f);
+            }
+        } else {
+            done = true;
+            g = lane;
+        }
+    }
+    if (live) perm[sg.start + lane] = e;
+}
+
 constexpr size_t finish_smem(int cap) { return (size_t)cap * (8 + 8 + 4 * 7); }
 
 // ---------------------------------------------------------------------------
@@ -310,13 +428,7 @@ __global__ void __launch_bounds__(BK_T) k_lg_buckets(const LgSegInfo* __restrict
                                                      const uint32_t* __restrict__ lens, uint64_t* __restrict__ K,
                                                      uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
                                                      SegLists L, unsigned* err, uint32_t ns) {
-    constexpr int ITEMS = BK_CAP / BK_T;
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* sHi = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* sLo = sHi + BK_CAP;
-    uint32_t* sA = reinterpret_cast<uint32_t*>(sLo + BK_CAP);
-    uint32_t* sN = sA + BK_CAP;
-    __shared__ uint32_t sh_warp[32];
     const uint32_t sidx = segment_of_bucket(info, ns, blockIdx.x);
     LgSegInfo si = info[sidx];
     uint32_t b = blockIdx.x - si.bk_base;
@@ -418,22 +530,25 @@ struct LsBufs {
     uint64_t* K;
     uint64_t* tK;
     uint32_t* tV;
+    Seg* warp;
     Seg* tiny;
     Seg* med;
     Seg* large;
     uint32_t* cnt;
     uint32_t* segfmt;
     SpBufs sp;
-    uint32_t cap_tiny, cap_med, cap_large;
+    uint32_t cap_warp, cap_tiny, cap_med, cap_large;
 };
 
 void carve_ls(Arena& ar, uint32_t n, uint32_t p, LsBufs& b) {
-    b.cap_tiny = n / 2 + 2;
+    b.cap_warp = n / 2 + 2;
+    b.cap_tiny = n / (WARP_CAP + 1) + 2;
     b.cap_med = n / (TINY_CAP + 1) + 2;
     b.cap_large = n / (MED_CAP + 1) + p + 2;  // every large segment holds > MED_CAP strings
     b.K = ar.take<uint64_t>(n);
     b.tK = ar.take<uint64_t>(n);
     b.tV = ar.take<uint32_t>(n);
+    b.warp = ar.take<Seg>(b.cap_warp);
     b.tiny = ar.take<Seg>(b.cap_tiny);
     b.med = ar.take<Seg>(b.cap_med);
     b.large = ar.take<Seg>(b.cap_large);
@@ -442,8 +557,11 @@ void carve_ls(Arena& ar, uint32_t n, uint32_t p, LsBufs& b) {
     carve_sp(ar, n, b.cap_large, b.sp);
 }
 
-sss_status run_finishers(sss_ctx* ctx, const LsBufs& B, uint32_t ntiny, uint32_t nmed, const StrIn& in,
-                         uint32_t* perm, uint32_t* lcp) {
+sss_status run_finishers(sss_ctx* ctx, const LsBufs& B, uint32_t nwarp, uint32_t ntiny, uint32_t nmed,
+                         const StrIn& in, uint32_t* perm, uint32_t* lcp) {
+    SSS_TRY(sss_launch(ctx, "ls_finish_warp", k_finish_warp, dim3((nwarp + WF_WARPS - 1) / WF_WARPS),
+                       dim3(32 * WF_WARPS), 0, (const Seg*)B.warp, nwarp, in.chars, in.offs, in.lens, perm, lcp,
+                       ctx->d_err));
     SSS_TRY(sss_launch(ctx, "ls_finish_tiny", k_finish<TINY_T, TINY_CAP>, dim3(ntiny), dim3(TINY_T),
                        finish_smem(TINY_CAP), (const Seg*)B.tiny, in.chars, in.offs, in.lens, perm, lcp,
                        ctx->d_err));
@@ -501,34 +619,42 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
     SSS_TRY(sss_launch(ctx, "ls_init", k_init_perm, dim3((n + 255) / 256), dim3(256), 0, perm, lcp, n));
 
     // initial segments (partitions or instances), by size class
-    std::vector<Seg> tiny, med, large;
+    std::vector<Seg> warp, tiny, med, large;
     for (const Seg& s : init) {
         if (s.size < 2) continue;
-        if (s.size <= (uint32_t)TINY_CAP) tiny.push_back(s);
+        if (s.size <= (uint32_t)WARP_CAP) warp.push_back(s);
+        else if (s.size <= (uint32_t)TINY_CAP) tiny.push_back(s);
         else if (s.size <= (uint32_t)MED_CAP) med.push_back(s);
         else large.push_back(s);
     }
     // pinned staging: segment info + tiles + counters
-    size_t pin_bytes = sizeof(uint32_t) * 16 + sizeof(Seg) * (size_t)(B.cap_large + B.cap_med + B.cap_tiny) +
+    const size_t nseg_stage = (size_t)B.cap_large + B.cap_med + B.cap_tiny + B.cap_warp;
+    size_t pin_bytes = sizeof(uint32_t) * 16 + sizeof(Seg) * nseg_stage +
                        sizeof(LgSegInfo) * B.cap_large + sizeof(LgTile) * B.sp.cap_tiles + 1024;
     void* pin;
     SSS_TRY(sss_pinned(ctx, pin_bytes, &pin));
     uint32_t* h_cnt = reinterpret_cast<uint32_t*>(pin);
     Seg* h_seg = reinterpret_cast<Seg*>(reinterpret_cast<char*>(pin) + 64);
-    LgSegInfo* h_info = reinterpret_cast<LgSegInfo*>(h_seg + (B.cap_large + B.cap_med + B.cap_tiny));
+    LgSegInfo* h_info = reinterpret_cast<LgSegInfo*>(h_seg + nseg_stage);
     LgTile* h_tiles = reinterpret_cast<LgTile*>(h_info + B.cap_large);
 
-    if (!tiny.empty() || !med.empty()) {
-        std::copy(tiny.begin(), tiny.end(), h_seg);
-        std::copy(med.begin(), med.end(), h_seg + tiny.size());
-        SSS_TRY(sss_upload(ctx, B.tiny, h_seg, sizeof(Seg) * tiny.size()));
-        SSS_TRY(sss_upload(ctx, B.med, h_seg + tiny.size(), sizeof(Seg) * med.size()));
-        SSS_TRY(run_finishers(ctx, B, (uint32_t)tiny.size(), (uint32_t)med.size(), in, perm, lcp));
+    if (!warp.empty() || !tiny.empty() || !med.empty()) {
+        Seg* hw = h_seg;
+        Seg* ht = hw + warp.size();
+        Seg* hm = ht + tiny.size();
+        std::copy(warp.begin(), warp.end(), hw);
+        std::copy(tiny.begin(), tiny.end(), ht);
+        std::copy(med.begin(), med.end(), hm);
+        SSS_TRY(sss_upload(ctx, B.warp, hw, sizeof(Seg) * warp.size()));
+        SSS_TRY(sss_upload(ctx, B.tiny, ht, sizeof(Seg) * tiny.size()));
+        SSS_TRY(sss_upload(ctx, B.med, hm, sizeof(Seg) * med.size()));
+        SSS_TRY(run_finishers(ctx, B, (uint32_t)warp.size(), (uint32_t)tiny.size(), (uint32_t)med.size(), in, perm,
+                              lcp));
         // staging is reused below: wait for the uploads
         SSS_CUDA(cudaStreamSynchronize(ctx->stream));
     }
 
-    SegLists L{B.tiny, B.med, B.large, B.cnt, B.cap_tiny, B.cap_med, B.cap_large};
+    SegLists L{B.tiny, B.med, B.large, B.cnt, B.cap_tiny, B.cap_med, B.cap_large, B.warp, B.cap_warp};
     uint32_t rounds = 0;
     while (!large.empty()) {
         if (++rounds > 100000u) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: round limit exceeded");
@@ -563,13 +689,13 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
         SSS_TRY(sss_launch(ctx, "ls_lg_direct", k_lg_direct, dim3(ns - npart), dim3(DIRECT_T),
                            (size_t)DIRECT_CAP * (8 + 8 + 4 + 4), (const LgSegInfo*)B.sp.info, npart,
                            (const uint32_t*)B.segfmt, in.lens, B.K, perm, lcp, L, ctx->d_err));
-        SSS_CUDA(cudaMemcpyAsync(h_cnt, B.cnt, sizeof(uint32_t) * 3, cudaMemcpyDeviceToHost, ctx->stream));
-        SSS_CUDA(cudaMemcpyAsync(h_cnt + 3, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+        SSS_CUDA(cudaMemcpyAsync(h_cnt, B.cnt, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        SSS_CUDA(cudaMemcpyAsync(h_cnt + 4, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
         SSS_CUDA(cudaStreamSynchronize(ctx->stream));
-        if (h_cnt[3] & ERRBIT_OVERFLOW) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: device capacity check failed");
+        if (h_cnt[4] & ERRBIT_OVERFLOW) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: device capacity check failed");
         uint32_t ct = std::min(h_cnt[0], B.cap_tiny), cm = std::min(h_cnt[1], B.cap_med),
-                 cl = std::min(h_cnt[2], B.cap_large);
-        SSS_TRY(run_finishers(ctx, B, ct, cm, in, perm, lcp));
+                 cl = std::min(h_cnt[2], B.cap_large), cw = std::min(h_cnt[3], B.cap_warp);
+        SSS_TRY(run_finishers(ctx, B, cw, ct, cm, in, perm, lcp));
         large.clear();
         if (cl > 0) {
             SSS_CUDA(cudaMemcpyAsync(h_seg, B.large, sizeof(Seg) * cl, cudaMemcpyDeviceToHost, ctx->stream));
