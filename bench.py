@@ -212,6 +212,8 @@ def main():
     ap.add_argument("--p", type=int, default=P, help="partitions (profiling of smaller cases)")
     ap.add_argument("--workload", default="all", choices=["all", "pdms", "batch", "serve"])
     ap.add_argument("--batch-instances", type=int, default=4096)
+    ap.add_argument("--per-instance-steps", type=int, default=2,
+                    help="timed passes of one sss_sort call per instance (0: skip that comparison)")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-warmup", type=int, default=1000)
     ap.add_argument("--serve-load", type=float, default=0.8)
@@ -447,7 +449,32 @@ def bench_batch(args, dev, ctx):
     ms = e0.elapsed_time(e1) / args.steps
     p_batch = perm.cpu()
 
-    # one sss_sort call per instance (p = 1), same outputs
+    if args.per_instance_steps <= 0:
+        per = None
+    else:
+        per = per_instance_calls(args, ctx, chars, offs, lens, first, perm, lcp, p_batch, prm, e0, e1, st)
+    hbm, peak_kind = peaks()
+    algo = D + 20 * n
+    return {"workload": f"batch_{m}_instances_2^6..2^16_len8..300_ACGT", "instances": m, "strings": n, "chars": N,
+            "D_over_N": D / N, "ms_per_step": ms, "chars_per_s": N / (ms / 1e3), "strings_per_s": n / (ms / 1e3),
+            "gpu_launches_per_step": launches,
+            "per_instance_calls": per,
+            "speedup_vs_per_instance": (per["ms_per_step"] / ms) if per else None,
+            "outputs_identical": per["outputs_identical"] if per else None,
+            "roofline": {"bound": "hbm", "achieved": algo / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": algo / (ms / 1e3) / 1e9 / hbm, "peak_kind": peak_kind,
+                         "algorithmic_bytes": algo, "model": "D + 20n (dist chars, views, perm, lcp)"},
+            "steps": args.steps, "warmup": args.warmup, "generate_s": tg,
+            "l2": "inputs (%.1f GB of chars) larger than L2; no flush" % (N / 1e9)}
+
+
+def per_instance_calls(args, ctx, chars, offs, lens, first, perm, lcp, p_batch, prm, e0, e1, st):
+    """The same instances sorted by one sss_sort call each (p = 1)."""
+    import torch
+
+    import paper_2404_16517_gb300 as sss
+    m = len(first) - 1
+    N = int(lens.to(torch.int64).sum().item())
     perm2 = torch.empty_like(perm)
     lcp2 = torch.empty_like(lcp)
     fi = [int(x) for x in first]
@@ -466,7 +493,7 @@ def bench_batch(args, dev, ctx):
     launches1 = sum(v["launches"] for v in stats1.values())
     per_instance()
     torch.cuda.synchronize()
-    steps1 = max(1, min(args.steps, 2))
+    steps1 = max(1, min(args.per_instance_steps, 2))
     e0.record(st)
     for _ in range(steps1):
         per_instance()
@@ -474,19 +501,8 @@ def bench_batch(args, dev, ctx):
     torch.cuda.synchronize()
     ms1 = e0.elapsed_time(e1) / steps1
     same = bool(torch.equal(p_batch, perm2.cpu()) and torch.equal(lcp.cpu(), lcp2.cpu()))
-    hbm, peak_kind = peaks()
-    algo = D + 20 * n
-    return {"workload": f"batch_{m}_instances_2^6..2^16_len8..300_ACGT", "instances": m, "strings": n, "chars": N,
-            "D_over_N": D / N, "ms_per_step": ms, "chars_per_s": N / (ms / 1e3), "strings_per_s": n / (ms / 1e3),
-            "gpu_launches_per_step": launches,
-            "per_instance_calls": {"ms_per_step": ms1, "chars_per_s": N / (ms1 / 1e3), "gpu_launches_per_step": launches1,
-                                   "steps": steps1},
-            "speedup_vs_per_instance": ms1 / ms, "outputs_identical": same,
-            "roofline": {"bound": "hbm", "achieved": algo / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                         "frac": algo / (ms / 1e3) / 1e9 / hbm, "peak_kind": peak_kind,
-                         "algorithmic_bytes": algo, "model": "D + 20n (dist chars, views, perm, lcp)"},
-            "steps": args.steps, "warmup": args.warmup, "generate_s": tg,
-            "l2": "inputs (%.1f GB of chars) larger than L2; no flush" % (N / 1e9)}
+    return {"ms_per_step": ms1, "chars_per_s": N / (ms1 / 1e3), "gpu_launches_per_step": launches1,
+            "steps": steps1, "outputs_identical": same}
 
 
 def bench_serve(args, dev):

@@ -409,27 +409,50 @@ __device__ void bitonic_sort64(uint64_t* a, uint32_t count) {
 }
 
 // ---------------------------------------------------------------------------
+// Shared-memory swizzle for the merge sort's blocked layout: thread t owns the
+// ITEMS logical slots t*ITEMS .. t*ITEMS+ITEMS-1, and when all threads access
+// their i-th slot at once a plain layout puts 16 lanes of a half-warp on the
+// same few 8-byte bank pairs.  XOR-ing the slot with a few bits of the thread
+// index spreads them over all 16; consecutive logical indices stay
+// conflict-free too.  A bijection on every block of ITEMS slots.
+template <int ITEMS>
+__device__ __forceinline__ uint32_t swz(uint32_t j) {
+    constexpr uint32_t PER_ROW = ITEMS >= 16 ? 1u : 16u / ITEMS;  // blocks per 128-byte row
+    return j ^ (((j / ITEMS) / PER_ROW) & (ITEMS - 1));
+}
+
 // Block merge sort of `count` 128-bit keys (hi, lo) held in shared memory arrays
-// of THREADS*ITEMS entries, ascending.  Each thread sorts ITEMS keys in
-// registers (odd-even transposition), then log2(THREADS) rounds merge pairs of
-// sorted lists: every thread finds its ITEMS outputs with a merge-path binary
-// search and merges them serially.  Slots past `count` are padded with all-ones
-// keys (the arrays are fully overwritten).  O(n log n) work and 2 barriers per
-// round, instead of the bitonic network's O(n log^2 n) and a barrier per stage.
+// of THREADS*ITEMS entries, ascending; input and output in plain index order.
+// Each thread sorts ITEMS keys in registers (odd-even transposition), then
+// log2(THREADS) rounds merge pairs of sorted lists: every thread finds its ITEMS
+// outputs with a merge-path binary search and merges them serially.  Inside, the
+// arrays use the swizzled layout (swz), entered and left through striped passes,
+// so no register<->shared transfer has bank conflicts.  Slots past `count` are
+// padded with all-ones keys (the arrays are fully overwritten).
 template <int THREADS, int ITEMS>
 __device__ void block_merge_sort128(uint64_t* sHi, uint64_t* sLo, uint32_t count) {
     const uint32_t tid = threadIdx.x;
     uint64_t h[ITEMS], l[ITEMS];
+    // plain -> swizzled, padding the tail
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        uint32_t idx = tid * ITEMS + i;
-        if (idx < count) {
-            h[i] = sHi[idx];
-            l[i] = sLo[idx];
-        } else {
-            h[i] = ~0ull;
-            l[i] = ~0ull;
-        }
+        uint32_t j = tid + i * THREADS;
+        h[i] = j < count ? sHi[j] : ~0ull;
+        l[i] = j < count ? sLo[j] : ~0ull;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t j = swz<ITEMS>(tid + i * THREADS);
+        sHi[j] = h[i];
+        sLo[j] = l[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t j = swz<ITEMS>(tid * ITEMS + i);
+        h[i] = sHi[j];
+        l[i] = sLo[j];
     }
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
@@ -449,48 +472,63 @@ __device__ void block_merge_sort128(uint64_t* sHi, uint64_t* sLo, uint32_t count
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
-            sHi[tid * ITEMS + i] = h[i];
-            sLo[tid * ITEMS + i] = l[i];
+            uint32_t j = swz<ITEMS>(tid * ITEMS + i);
+            sHi[j] = h[i];
+            sLo[j] = l[i];
         }
         __syncthreads();
         const uint32_t L = w * ITEMS;
         const uint32_t g0 = (tid / (2 * w)) * (2 * L);
         if (g0 >= count) continue;  // a pair of padding lists stays as it is
         const uint32_t diag = (tid % (2 * w)) * ITEMS;
-        const uint64_t* Ah = sHi + g0;
-        const uint64_t* Al = sLo + g0;
-        const uint64_t* Bh = Ah + L;
-        const uint64_t* Bl = Al + L;
+        const uint32_t A0 = g0, B0 = g0 + L;
         uint32_t lo = diag > L ? diag - L : 0, hi = diag < L ? diag : L;
         while (lo < hi) {
             uint32_t mid = (lo + hi) >> 1;
-            uint32_t bj = diag - 1 - mid;
-            if (!key128_less(Bh[bj], Bl[bj], Ah[mid], Al[mid])) lo = mid + 1;
+            uint32_t bj = swz<ITEMS>(B0 + diag - 1 - mid), aj = swz<ITEMS>(A0 + mid);
+            if (!key128_less(sHi[bj], sLo[bj], sHi[aj], sLo[aj])) lo = mid + 1;
             else hi = mid;
         }
         uint32_t a = lo, b = diag - lo;
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
+            uint32_t aj = swz<ITEMS>(A0 + a), bj = swz<ITEMS>(B0 + b);
             bool takeA;
             if (a >= L) takeA = false;
             else if (b >= L) takeA = true;
-            else takeA = !key128_less(Bh[b], Bl[b], Ah[a], Al[a]);
+            else takeA = !key128_less(sHi[bj], sLo[bj], sHi[aj], sLo[aj]);
             if (takeA) {
-                h[i] = Ah[a];
-                l[i] = Al[a];
+                h[i] = sHi[aj];
+                l[i] = sLo[aj];
                 ++a;
             } else {
-                h[i] = Bh[b];
-                l[i] = Bl[b];
+                h[i] = sHi[bj];
+                l[i] = sLo[bj];
                 ++b;
             }
         }
     }
+    // swizzled -> plain
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        sHi[tid * ITEMS + i] = h[i];
-        sLo[tid * ITEMS + i] = l[i];
+        uint32_t j = swz<ITEMS>(tid * ITEMS + i);
+        sHi[j] = h[i];
+        sLo[j] = l[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t j = swz<ITEMS>(tid + i * THREADS);
+        h[i] = sHi[j];
+        l[i] = sLo[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t j = tid + i * THREADS;
+        sHi[j] = h[i];
+        sLo[j] = l[i];
     }
     __syncthreads();
 }
