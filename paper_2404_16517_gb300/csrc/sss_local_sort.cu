@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(32 * WF_WARPS) k_finish_warp(const Seg* __rest
     const Seg sg = segs[sidx];
     const uint32_t m = sg.size <= 32u ? sg.size : 32u;
     const bool live = lane < m;
+    const uint32_t span = m <= 2u ? 2u : (1u << (32 - __clz((int)(m - 1))));
     uint32_t e = live ? perm[sg.start + lane] : 0u;
     uint32_t len = live ? lens[e] : 0u;
     uint32_t g = 0, gd = sg.depth;
@@ -276,10 +277,10 @@ __global__ void __launch_bounds__(32 * WF_WARPS) k_finish_warp(const Seg* __rest
             hi = ~0ull;
             lo = ~0ull;
         }
-#pragma unroll
-        for (uint32_t kk = 2; kk <= 32; kk <<= 1) {
-            const bool up = (lane & kk) == 0 || kk == 32;
-#pragma unroll
+        // bitonic network over the next power of two >= m lanes (warp-uniform);
+        // lanes past it hold padding and sit out
+        for (uint32_t kk = 2; kk <= span; kk <<= 1) {
+            const bool up = (lane & kk) == 0 || kk == span;
             for (uint32_t j = kk >> 1; j > 0; j >>= 1) warp_cas128(hi, lo, lane, j, up);
         }
         // lane j now holds the j-th position of the segment; groups kept their ranges
