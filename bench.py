@@ -532,10 +532,14 @@ def bench_serve(args, dev):
     sat = summarize(warm, t0)
     lam = args.serve_load * sat["requests_per_s"]
     arrivals = list(np.cumsum(gaps) / lam)
+    with srv.sched.cv:  # count the open-loop run only
+        srv.sched.n_batches, srv.sched.batch_sizes = 0, []
+        srv.sched.gen_ms = srv.sched.sort_ms = 0.0
     t0 = srv.run_open_loop(reqs, arrivals)
     st = summarize(reqs, t0)
     hw = srv.sched.alloc.high_water
     nb = srv.sched.n_batches
+    gen_ms, sort_ms = srv.sched.gen_ms, srv.sched.sort_ms
     mean_batch = sum(srv.sched.batch_sizes) / max(1, nb)
     srv.close()
     torch.cuda.synchronize()
@@ -544,6 +548,7 @@ def bench_serve(args, dev):
                "saturated_chars_per_s": sat["chars_per_s"], "warmup_requests": args.serve_warmup,
                "budget_bytes": budget, "arena_high_water_bytes": hw, "slots": args.serve_slots,
                "batches_total": nb, "mean_batch_requests": mean_batch,
+               "device_ms_generate_total": gen_ms, "device_ms_sort_total": sort_ms,
                "max_batch_requests": args.serve_max_batch,
                "latency": "scheduled arrival to batch completion on the device (includes queueing, admission, "
                           "on-device generation of the request's strings, sort)"})

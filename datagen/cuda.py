@@ -59,6 +59,11 @@ def _configure(_lib):
     _lib.sssgen_request_totals.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint32, C.c_uint32,
                                            C.c_void_p, C.c_void_p]
     _lib.sssgen_request_scratch_words.argtypes = [C.c_uint64]
+    _lib.sssgen_req_desc_bytes.restype = C.c_uint32
+    _lib.sssgen_req_desc_bytes.argtypes = []
+    _lib.sssgen_request_batch.restype = C.c_int
+    _lib.sssgen_request_batch.argtypes = [C.c_void_p] * 6 + [C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint32,
+                                                              C.c_char_p, C.c_uint32, C.c_void_p]
     f = _lib.sssgen_template_set
     f.restype = C.c_int
     f.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
@@ -174,3 +179,50 @@ def request_totals(seeds, sizes, len_lo: int = 16, len_hi: int = 1000, device: s
     if rc != 0:
         raise RuntimeError(f"sssgen_request_totals failed ({rc})")
     return out.cpu().numpy()
+
+
+def _req_desc_dtype():
+    import numpy as np
+    return np.dtype([("kl", "<u8"), ("kt", "<u8"), ("kc", "<u8"), ("char_base", "<u8"), ("ratio", "<f8"),
+                     ("first", "<u4"), ("n", "<u4"), ("logs", "<u4"), ("pad", "<u4")])
+
+
+def request_descs(seeds, sizes, ratios, char_bases, alphabet_len: int = 26):
+    """Host descriptor table (numpy) of a batch of requests packed back to back
+    into one string table, for request_batch_into."""
+    import math
+
+    import numpy as np
+
+    import datagen
+    dt = _req_desc_dtype()
+    assert dt.itemsize == int(lib().sssgen_req_desc_bytes())
+    m = len(seeds)
+    d = np.zeros(m, dtype=dt)
+    f = 0
+    for k in range(m):
+        sd, n = int(seeds[k]) & ((1 << 64) - 1), int(sizes[k])
+        d[k] = (datagen.stream_key(sd, datagen.ST_LEN), datagen.stream_key(sd, datagen.ST_TEMPLATE),
+                datagen.stream_key(sd, datagen.ST_CHARS), int(char_bases[k]), float(ratios[k]), f, n,
+                int(math.ceil(math.log(max(n, 2)) / math.log(alphabet_len))), 0)
+        f += n
+    return d
+
+
+def request_batch_into(chars, offs, lens, cp_scratch, sum_scratch, desc_dev, m: int, n: int, len_lo: int = 16,
+                       len_hi: int = 1000, alphabet: bytes = b"ABCDEFGHIJKLMNOPQRSTUVWXYZ"):
+    """Generate every request of a batch (descriptors already on the device,
+    desc_dev) into one table in a single launch sequence on the current stream;
+    request k gets the strings request_into would give it.  cp_scratch: >= n
+    int32; sum_scratch: >= request_scratch_words(n) + m int64."""
+    import torch
+    if n == 0:
+        return
+    assert cp_scratch.numel() >= n and sum_scratch.numel() >= request_scratch_words(n) + m
+    st = torch.cuda.current_stream(lens.device).cuda_stream
+    rc = lib().sssgen_request_batch(C.c_void_p(chars.data_ptr()), C.c_void_p(offs.data_ptr()),
+                                    C.c_void_p(lens.data_ptr()), C.c_void_p(cp_scratch.data_ptr()),
+                                    C.c_void_p(sum_scratch.data_ptr()), C.c_void_p(desc_dev.data_ptr()), m, n, len_lo,
+                                    len_hi, alphabet, len(alphabet), C.c_void_p(st))
+    if rc != 0:
+        raise RuntimeError(f"sssgen_request_batch failed ({rc})")

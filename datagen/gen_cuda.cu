@@ -59,15 +59,18 @@ __global__ void k_template_set(uint8_t* __restrict__ chars, uint64_t* __restrict
 // from its instance's template, the rest are uniform (counter = offs[g] + j)
 // (counters are relative to cbase, so a set placed at any offset of a larger
 // buffer gets the same characters; inst == NULL means instance 0 throughout)
+// (one warp per string, lanes on consecutive characters, so stores coalesce)
 __global__ void k_instance_chars(uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
                                  const uint32_t* __restrict__ lens, const uint32_t* __restrict__ cp,
                                  const uint32_t* __restrict__ inst, uint64_t n, uint64_t kt, uint64_t kc, Alpha al,
                                  uint64_t cbase) {
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t g = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < n; g += warps) {
         uint64_t o = offs[g];
         uint32_t l = lens[g], c = cp[g];
         uint64_t tb = inst ? (uint64_t)inst[g] << 20 : 0;
-        for (uint32_t j = 0; j < l; ++j) {
+        for (uint32_t j = lane; j < l; j += 32) {
             uint64_t r = j < c ? draw(kt, tb + j) : draw(kc, o - cbase + j);
             chars[o + j] = al.c[uidx(r, al.n)];
         }
@@ -165,7 +168,97 @@ __global__ void k_request_totals(const uint64_t* __restrict__ seeds, const uint6
     }
 }
 
+// ---- a batch of requests in one table (one launch sequence per batch) -------
+struct ReqDesc {
+    uint64_t kl, kt, kc;   // stream keys of the request: lengths, template, characters
+    uint64_t char_base;    // where the request's characters start
+    double ratio;          // template copy ratio
+    uint32_t first, n;     // the request's strings in the table
+    uint32_t logs, pad;    // ceil(log_a n)
+};
+
+__device__ __forceinline__ uint32_t req_of(const ReqDesc* __restrict__ R, uint32_t m, uint64_t g) {
+    uint32_t lo = 0, hi = m;  // last request with first <= g
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (R[mid].first <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_batch_layout(const ReqDesc* __restrict__ R, uint32_t m, uint64_t n, uint32_t* __restrict__ lens,
+                               uint32_t* __restrict__ cp, uint32_t len_lo, uint32_t span) {
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (uint64_t)gridDim.x * blockDim.x) {
+        const ReqDesc& q = R[req_of(R, m, g)];
+        uint32_t l = len_lo + uidx(draw(q.kl, g - q.first), span);
+        long long c = (long long)rint(q.ratio * (double)l) - (long long)q.logs - 1;
+        c = c < 0 ? 0 : c;
+        c = c > l ? l : c;
+        lens[g] = l;
+        cp[g] = (uint32_t)c;
+    }
+}
+
+// adj[k] = char_base_k - (prefix sum of the table's lengths at first_k)
+__global__ void k_batch_adj(const ReqDesc* __restrict__ R, uint32_t m, const uint64_t* __restrict__ P,
+                            uint64_t* __restrict__ adj) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m) adj[k] = R[k].char_base - P[R[k].first];
+}
+
+// one warp per string: offs[g] = P[g] + adj[k], then its characters
+__global__ void k_batch_chars(const ReqDesc* __restrict__ R, uint32_t m, uint64_t n, const uint64_t* __restrict__ adj,
+                              uint64_t* __restrict__ offs, const uint32_t* __restrict__ lens,
+                              const uint32_t* __restrict__ cp, uint8_t* __restrict__ chars, Alpha al) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t g = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < n; g += warps) {
+        uint32_t k = req_of(R, m, g);
+        const ReqDesc& q = R[k];
+        uint64_t o = offs[g] + adj[k];
+        uint64_t rel = o - q.char_base;
+        uint32_t l = lens[g], c = cp[g];
+        __syncwarp();
+        if (lane == 0) offs[g] = o;
+        for (uint32_t j = lane; j < l; j += 32) {
+            uint64_t r = j < c ? draw(q.kt, j) : draw(q.kc, rel + j);
+            chars[o + j] = al.c[uidx(r, al.n)];
+        }
+    }
+}
+
 }  // namespace
+
+extern "C" uint32_t sssgen_req_desc_bytes() { return (uint32_t)sizeof(ReqDesc); }
+
+// All requests of a batch in one table: request k (desc[k], a DEVICE array of m
+// descriptors sorted by `first`, covering [0, n) without gaps) gets the same
+// strings as sssgen_request with its seed, n, ratio and char_base.
+// cp_scratch: uint32_t[n]; sum_scratch: uint64_t[sssgen_request_scratch_words(n)
+// + m].  No host synchronisation.
+extern "C" int sssgen_request_batch(uint8_t* chars, uint64_t* offs, uint32_t* lens, uint32_t* cp_scratch,
+                                    uint64_t* sum_scratch, const void* desc, uint32_t m, uint64_t n, uint32_t len_lo,
+                                    uint32_t len_hi, const uint8_t* alphabet, uint32_t alen, void* stream) {
+    if (alen == 0 || alen > 64 || len_hi < len_lo || m == 0) return 1;
+    if (n == 0) return 0;
+    Alpha al{};
+    for (uint32_t k = 0; k < alen; ++k) al.c[k] = alphabet[k];
+    al.n = alen;
+    const ReqDesc* R = static_cast<const ReqDesc*>(desc);
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t grid = (uint32_t)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
+    k_batch_layout<<<grid, 256, 0, st>>>(R, m, n, lens, cp_scratch, len_lo, len_hi - len_lo + 1);
+    uint64_t nb = (n + CHUNK - 1) / CHUNK;
+    if (nb > 0x7fffffffull) return 1;
+    uint64_t* adj = sum_scratch + nb;
+    k_chunk_sums<<<(uint32_t)nb, SCAN_T, 0, st>>>(lens, n, sum_scratch);
+    k_scan_sums<<<1, SCAN_T, 0, st>>>(sum_scratch, nb);
+    k_write_offs<<<(uint32_t)nb, SCAN_T, 0, st>>>(lens, n, sum_scratch, offs, 0);
+    k_batch_adj<<<(m + 255) / 256, 256, 0, st>>>(R, m, offs, adj);
+    uint32_t cgrid = (uint32_t)((n + 7) / 8 < 65536 ? (n + 7) / 8 : 65536);
+    k_batch_chars<<<cgrid, 256, 0, st>>>(R, m, n, adj, offs, lens, cp_scratch, chars, al);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
 
 extern "C" int sssgen_request_totals(const uint64_t* seeds, const uint64_t* ns, uint64_t m, uint32_t len_lo,
                                      uint32_t len_hi, uint64_t* out, void* stream) {
@@ -201,8 +294,9 @@ extern "C" int sssgen_request(uint8_t* chars, uint64_t* offs, uint32_t* lens, ui
     k_chunk_sums<<<(uint32_t)nb, SCAN_T, 0, st>>>(lens, n, sum_scratch);
     k_scan_sums<<<1, SCAN_T, 0, st>>>(sum_scratch, nb);
     k_write_offs<<<(uint32_t)nb, SCAN_T, 0, st>>>(lens, n, sum_scratch, offs, char_base);
-    k_instance_chars<<<grid, 256, 0, st>>>(chars, offs, lens, cp_scratch, nullptr, n, stream_key(seed, ST_TEMPLATE),
-                                           stream_key(seed, ST_CHARS), al, char_base);
+    uint32_t cgrid = (uint32_t)((n + 7) / 8 < 65536 ? (n + 7) / 8 : 65536);
+    k_instance_chars<<<cgrid, 256, 0, st>>>(chars, offs, lens, cp_scratch, nullptr, n, stream_key(seed, ST_TEMPLATE),
+                                            stream_key(seed, ST_CHARS), al, char_base);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
@@ -214,7 +308,7 @@ extern "C" int sssgen_instance_chars(uint8_t* chars, const uint64_t* offs, const
     for (uint32_t k = 0; k < alen; ++k) al.c[k] = alphabet[k];
     al.n = alen;
     if (n == 0) return 0;
-    uint32_t grid = (uint32_t)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
+    uint32_t grid = (uint32_t)((n + 7) / 8 < 65536 ? (n + 7) / 8 : 65536);
     k_instance_chars<<<grid, 256, 0, (cudaStream_t)stream>>>(chars, offs, lens, cp, inst, n,
                                                              stream_key(seed, ST_TEMPLATE), stream_key(seed, ST_CHARS),
                                                              al, 0);

@@ -135,6 +135,8 @@ class Batch:
     temp_off: int        # arena range: generator scratch and sorter work memory (freed at batch end)
     temp_bytes: int
     live: int = 0        # requests of the batch not yet released
+    gen_ms: float = 0.0  # device time placing or generating the inputs
+    sort_ms: float = 0.0  # device time of the sort
 
 
 def batch_layout(n_table: int, sizes: list[int]):
@@ -167,6 +169,8 @@ class Scheduler:
         self.n_batches = 0
         self.inflight = 0
         self.batch_sizes: list[int] = []
+        self.gen_ms = 0.0
+        self.sort_ms = 0.0
 
     # -- request side ---------------------------------------------------------
     def min_bytes(self, req: Request) -> int:
@@ -263,6 +267,8 @@ class Scheduler:
         with self.cv:
             self.alloc.free(b.temp_off)
             self.inflight -= 1
+            self.gen_ms += b.gen_ms
+            self.sort_ms += b.sort_ms
             for r in b.reqs:
                 r.t_done = now
                 if error:
@@ -303,9 +309,10 @@ class DeviceEngine:
 
     @staticmethod
     def gen_bytes(n_table: int, m: int) -> int:
-        """Bound on the generator's scratch for a batch: one u64 per 4096 strings
-        of each request, rounded up per request to whole 256-byte ranges."""
-        return _align(8 * (n_table // 4096) + m * (8 + ALIGN))
+        """Bound on the generator's scratch for a batch: the request descriptors
+        (64 bytes each), then one u64 per 4096 strings of each request, rounded
+        up per request to whole 256-byte ranges."""
+        return _align(64 * m) + _align(8 * (n_table // 4096) + m * (8 + ALIGN) + ALIGN)
 
     def batch_temp(self, n_table: int, m: int) -> int:
         from . import batch_workspace_bytes
@@ -335,22 +342,40 @@ class DeviceEngine:
         lens = self._view(b.keep_off + lay["lens"], b.n_table, torch.int32)
         perm = self._view(b.keep_off + lay["perm"], b.n_table, torch.int32)
         lcp = self._view(b.keep_off + lay["lcp"], b.n_table, torch.int32)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        m = len(b.reqs)
         with torch.cuda.stream(st):
-            gen_off = b.temp_off
-            for r, f in zip(b.reqs, b.first):
-                words = dgc.request_scratch_words(r.n)
-                if r.payload is not None:
-                    self._place(r, f, offs, lens)
-                else:
-                    dgc.request_into(self.arena, r._chars_off, offs[f:f + r.n], lens[f:f + r.n],
-                                     perm[f:f + r.n], self._view(gen_off, words, torch.int64), r.seed, r.n, r.ratio)
-                gen_off += _align(8 * words)
+            ev[0].record(st)
+            gen_off = b.temp_off + _align(64 * m)
+            if all(r.payload is None for r in b.reqs):
+                # every request generated on the device in one launch sequence
+                desc = dgc.request_descs([r.seed for r in b.reqs], [r.n for r in b.reqs], [r.ratio for r in b.reqs],
+                                         [r._chars_off for r in b.reqs])
+                d_desc = self.arena[b.temp_off: b.temp_off + desc.nbytes]
+                d_desc.copy_(torch.from_numpy(desc.view("uint8")))
+                words = dgc.request_scratch_words(b.n_table) + m
+                dgc.request_batch_into(self.arena, offs, lens, perm, self._view(gen_off, words, torch.int64), d_desc,
+                                       m, b.n_table)
+            else:
+                for r, f in zip(b.reqs, b.first):
+                    words = dgc.request_scratch_words(r.n)
+                    if r.payload is not None:
+                        self._place(r, f, offs, lens)
+                    else:
+                        dgc.request_into(self.arena, r._chars_off, offs[f:f + r.n], lens[f:f + r.n],
+                                         perm[f:f + r.n], self._view(gen_off, words, torch.int64), r.seed, r.n,
+                                         r.ratio)
+                    gen_off += _align(8 * words)
+            ev[1].record(st)
             ws_off = b.temp_off + self.gen_bytes(b.n_table, len(b.reqs))
             ctx.set_workspace(self.arena[ws_off: ws_off + self._ws(b)])
             sss_sort_batch(self.arena, offs[:b.n_table], lens[:b.n_table], b.first, [r.n for r in b.reqs], self.prm,
                            out_perm=perm[:b.n_table], out_lcp=lcp[:b.n_table], ctx=ctx)
             ctx.set_workspace(None)
+            ev[2].record(st)
             st.synchronize()
+        b.gen_ms = ev[0].elapsed_time(ev[1])
+        b.sort_ms = ev[1].elapsed_time(ev[2])
         for r, f in zip(b.reqs, b.first):
             r.perm, r.lcp = perm[f:f + r.n], lcp[f:f + r.n]
 

@@ -144,3 +144,31 @@ def test_failed_batch_does_not_disturb_others():
             srv.release(r)
     srv.close()
     assert srv.sched.alloc.used == 0
+
+
+def test_batched_generator_equals_single_requests():
+    import datagen.cuda as dgc
+    reqs = _requests(9, seed=23, cap=9000)
+    gap = 1000  # characters left unused between requests
+    bases, b = [], 64
+    for r in reqs:
+        bases.append(b)
+        b += r.chars + gap
+    chars = torch.zeros(b, dtype=torch.uint8, device="cuda")
+    n = sum(r.n for r in reqs)
+    offs = torch.empty(n, dtype=torch.int64, device="cuda")
+    lens = torch.empty(n, dtype=torch.int32, device="cuda")
+    cp = torch.empty(n, dtype=torch.int32, device="cuda")
+    sc = torch.empty(dgc.request_scratch_words(n) + len(reqs), dtype=torch.int64, device="cuda")
+    desc = dgc.request_descs([r.seed for r in reqs], [r.n for r in reqs], [r.ratio for r in reqs], bases)
+    d_desc = torch.from_numpy(desc.view(np.uint8)).cuda()
+    dgc.request_batch_into(chars, offs, lens, cp, sc, d_desc, len(reqs), n)
+    torch.cuda.synchronize()
+    C, O, L = chars.cpu().numpy(), offs.cpu().numpy(), lens.cpu().numpy()
+    f = 0
+    for r, base in zip(reqs, bases):
+        ss = _request_strings(r)
+        assert np.array_equal(L[f:f + r.n], ss.lens.view(np.int32))
+        assert np.array_equal(O[f:f + r.n] - base, ss.offs.astype(np.int64))
+        assert np.array_equal(C[base:base + r.chars], ss.chars[:r.chars])
+        f += r.n
