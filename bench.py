@@ -212,6 +212,7 @@ def main():
     ap.add_argument("--p", type=int, default=P, help="partitions (profiling of smaller cases)")
     ap.add_argument("--workload", default="all", choices=["all", "pdms", "batch", "serve"])
     ap.add_argument("--batch-instances", type=int, default=4096)
+    ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner (default knobs)")
     ap.add_argument("--per-instance-steps", type=int, default=2,
                     help="timed passes of one sss_sort call per instance (0: skip that comparison)")
     ap.add_argument("--serve-requests", type=int, default=20000)
@@ -422,12 +423,43 @@ def bench_batch(args, dev, ctx):
     D = int(d.to(torch.int64).sum().item())
     del d
     arr, _ = sss.instance_table(first[:-1], sizes)
+    st = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def run(p_):
+        ctx._check(sss.lib().sss_sort_batch(ctx.h, sss._ptr(chars), chars.numel(), sss._ptr(offs), sss._ptr(lens), n,
+                                            arr, m, sss.C.byref(p_), sss._ptr(perm), sss._ptr(lcp), None), ctx.h)
+
+    def timed(p_, steps):
+        for _ in range(args.warmup):
+            run(p_)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(steps):
+            run(p_)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    # autotune the knobs on a sample of the instances (outside the timed region)
+    tuning = None
+    if not args.no_tune:
+        from paper_2404_16517_gb300 import autotune
+        t0 = time.perf_counter()
+        best, table = autotune.tune_batch(chars, offs, lens, first[:-1], sizes, max_strings=1 << 22, ctx=ctx)
+        ms_default = timed(prm, max(1, args.steps // 2))
+        prm_t = sss.params(**best)
+        ms_tuned = timed(prm_t, max(1, args.steps // 2))
+        if ms_tuned < ms_default:
+            prm = prm_t
+        tuning = {"chosen": best if ms_tuned < ms_default else "defaults", "candidates": len(table),
+                  "sample_strings_max": 1 << 22, "tune_s": time.perf_counter() - t0,
+                  "ms_default_knobs": ms_default, "ms_tuned_knobs": ms_tuned,
+                  "fastest_on_sample_ms": table[0][0], "slowest_on_sample_ms": table[-1][0]}
 
     def step():
-        ctx._check(sss.lib().sss_sort_batch(ctx.h, sss._ptr(chars), chars.numel(), sss._ptr(offs), sss._ptr(lens), n,
-                                            arr, m, sss.C.byref(prm), sss._ptr(perm), sss._ptr(lcp), None), ctx.h)
+        run(prm)
 
-    st = torch.cuda.current_stream(dev)
     ctx.reset_stats()
     ctx.set_timing(True, "")
     step()
@@ -440,7 +472,6 @@ def bench_batch(args, dev, ctx):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(args.steps):
         step()
@@ -457,7 +488,7 @@ def bench_batch(args, dev, ctx):
     algo = D + 20 * n
     return {"workload": f"batch_{m}_instances_2^6..2^16_len8..300_ACGT", "instances": m, "strings": n, "chars": N,
             "D_over_N": D / N, "ms_per_step": ms, "chars_per_s": N / (ms / 1e3), "strings_per_s": n / (ms / 1e3),
-            "gpu_launches_per_step": launches,
+            "gpu_launches_per_step": launches, "tuning": tuning,
             "per_instance_calls": per,
             "speedup_vs_per_instance": (per["ms_per_step"] / ms) if per else None,
             "outputs_identical": per["outputs_identical"] if per else None,

@@ -70,9 +70,16 @@ typedef struct sss_params {
     uint32_t v;         /* regular-sampling factor (default 2, Section 5) */
     uint32_t flags;     /* SSS_FLAG_* */
     uint64_t hash_seed; /* seed of the prefix hash (default 0) */
-    uint32_t cta_cap;   /* tuning: largest segment sorted inside one CTA (0 = default) */
-    uint32_t merge_ms;  /* tuning: merge segment spacing, a power of two 8..1024 (0 = default) */
-    uint32_t reserved[4];
+    /* Tuning knobs of the local sort and merge: they change speed, never results.
+     * 0 selects the default; other values are clamped into the stated range. */
+    uint32_t cta_cap;       /* largest segment finished inside one CTA, 64..2048 (default 2048) */
+    uint32_t merge_ms;      /* merge segment spacing, a power of two 8..1024 (default 32) */
+    uint32_t direct_cap;    /* largest segment of the multi-CTA path sorted whole by one CTA,
+                               cta_cap..8192 (default 8192) */
+    uint32_t bucket_target; /* target size of a sampled-partition range bucket, 256..4096
+                               (default 2048) */
+    uint32_t warp_cap;      /* largest segment finished by one warp, 2..32 (default 32) */
+    uint32_t reserved[1];
 } sss_params;
 
 #define SSS_KMAX_AUTO 0xFFFFFFFFu

@@ -43,7 +43,10 @@ class SssError(RuntimeError):
 class sss_params(C.Structure):
     _fields_ = [("kmin", C.c_uint32), ("kmax", C.c_uint32), ("v", C.c_uint32), ("flags", C.c_uint32),
                 ("hash_seed", C.c_uint64), ("cta_cap", C.c_uint32), ("merge_ms", C.c_uint32),
-                ("reserved", C.c_uint32 * 4)]
+                ("direct_cap", C.c_uint32), ("bucket_target", C.c_uint32), ("warp_cap", C.c_uint32),
+                ("reserved", C.c_uint32 * 1)]
+
+TUNING_FIELDS = ("cta_cap", "merge_ms", "direct_cap", "bucket_target", "warp_cap")
 
 
 class sss_instance(C.Structure):
@@ -112,11 +115,13 @@ def exported_symbols() -> list[str]:
 
 
 def params(kmin: int = 0, kmax: int = SSS_KMAX_AUTO, v: int = 2, flags: int = 0, hash_seed: int = 0,
-           cta_cap: int = 0, merge_ms: int = 0) -> sss_params:
+           cta_cap: int = 0, merge_ms: int = 0, direct_cap: int = 0, bucket_target: int = 0,
+           warp_cap: int = 0) -> sss_params:
+    """sss_params; the tuning knobs (0 = default) change speed, never results."""
     p = sss_params()
     lib().sss_params_default(C.byref(p))
     p.kmin, p.kmax, p.v, p.flags, p.hash_seed, p.cta_cap = kmin, kmax, v, flags, hash_seed, cta_cap
-    p.merge_ms = merge_ms
+    p.merge_ms, p.direct_cap, p.bucket_target, p.warp_cap = merge_ms, direct_cap, bucket_target, warp_cap
     return p
 
 

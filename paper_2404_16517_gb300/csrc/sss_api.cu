@@ -263,11 +263,20 @@ static sss_status checked_input(sss_ctx* ctx, const StrIn& in) {
     return sss_sync(ctx);
 }
 
+static uint32_t clamp_or(uint32_t x, uint32_t dflt, uint32_t lo, uint32_t hi) {
+    if (x == 0) return dflt;
+    return x < lo ? lo : (x > hi ? hi : x);
+}
+
 static sss_params resolve_params(const sss_params* p) {
     sss_params r;
     sss_params_default(&r);
     if (p) r = *p;
     if (r.v == 0) r.v = 2;
+    r.cta_cap = clamp_or(r.cta_cap, 2048, 64, 2048);
+    r.direct_cap = clamp_or(r.direct_cap, 8192, r.cta_cap, 8192);
+    r.bucket_target = clamp_or(r.bucket_target, 2048, 256, 4096);
+    r.warp_cap = clamp_or(r.warp_cap, 32, 2, 32);
     return r;
 }
 

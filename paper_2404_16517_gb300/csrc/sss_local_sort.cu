@@ -32,12 +32,11 @@ namespace {
 constexpr uint32_t DONE = 0xFFFFFFFFu;
 
 // size classes
-constexpr int WARP_CAP = 32, WF_WARPS = 8;      // segments of 2..32 strings: one warp each
-constexpr int TINY_T = 64, TINY_CAP = 64;       // segments of 33..64 strings
-constexpr int MED_T = 256, MED_CAP = 2048;      // segments of 65..2048 strings
+constexpr int WF_WARPS = 8;                     // warp finisher: segments of <= 32 strings, one warp each
+constexpr int TINY_T = 64, TINY_CAP = 64;       // segments of warp_cap+1 .. 64 strings
+constexpr int MED_T = 256, MED_CAP = 2048;      // segments of 65 .. cta_cap (<= 2048) strings
 constexpr int BK_T = 512, BK_CAP = 4096;        // bucket sort CTA
-constexpr int DIRECT_T = 1024, DIRECT_CAP = 8192;  // whole-segment sort CTA
-constexpr int LG_TARGET = BK_CAP / 2;           // target range-bucket size
+constexpr int DIRECT_T = 1024, DIRECT_CAP = 8192;  // whole-segment sort CTA (segments <= direct_cap)
 
 struct SegLists {
     Seg* tiny;
@@ -47,18 +46,19 @@ struct SegLists {
     uint32_t cap_tiny, cap_med, cap_large;
     Seg* warp;
     uint32_t cap_warp;
+    uint32_t warp_max, med_max;  // size classes: warp <= warp_max < tiny <= TINY_CAP < med <= med_max < large
 };
 
 __device__ __forceinline__ void push_seg(const SegLists& L, uint32_t start, uint32_t size, uint32_t depth,
                                          unsigned* err) {
     Seg s{start, size, depth, 0};
-    if (size <= (uint32_t)WARP_CAP) {
+    if (size <= L.warp_max) {
         uint32_t i = atomicAdd(&L.cnt[3], 1u);
         if (i < L.cap_warp) L.warp[i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
     } else if (size <= (uint32_t)TINY_CAP) {
         uint32_t i = atomicAdd(&L.cnt[0], 1u);
         if (i < L.cap_tiny) L.tiny[i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
-    } else if (size <= (uint32_t)MED_CAP) {
+    } else if (size <= L.med_max) {
         uint32_t i = atomicAdd(&L.cnt[1], 1u);
         if (i < L.cap_med) L.med[i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
     } else {
@@ -428,7 +428,8 @@ __global__ void __launch_bounds__(BK_T) k_lg_buckets(const LgSegInfo* __restrict
                                                      const uint64_t* __restrict__ tK, const uint32_t* __restrict__ tV,
                                                      const uint32_t* __restrict__ lens, uint64_t* __restrict__ K,
                                                      uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
-                                                     SegLists L, unsigned* err, uint32_t ns) {
+                                                     SegLists L, unsigned* err, uint32_t ns,
+                                                     uint8_t* __restrict__ fixmark) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t sidx = segment_of_bucket(info, ns, blockIdx.x);
     LgSegInfo si = info[sidx];
@@ -455,7 +456,12 @@ __global__ void __launch_bounds__(BK_T) k_lg_buckets(const LgSegInfo* __restrict
                 uint64_t k = tK[bs];
                 if (m >= 2 && !key_ended(k, f)) push_seg(L, bs, m, d + key_v(k, f) + fmt_chars(f), err);
             } else {
-                push_seg(L, bs, m, d, err);  // oversized range bucket: another round at this depth
+                // oversized range bucket: another round at this depth.  Its members
+                // have distinct keys, so the LCPs across its two ends depend on which
+                // members end up first and last: recomputed after the last round.
+                push_seg(L, bs, m, d, err);
+                if (bs > si.seg.start) fixmark[bs] = 1;
+                if (be < si.seg.start + si.seg.size) fixmark[be] = 1;
             }
         }
         if (eq && m >= 2 && key_ended(tK[bs], f)) {
@@ -494,6 +500,32 @@ __global__ void __launch_bounds__(512) k_lg_seams(const LgSegInfo* __restrict__ 
         uint32_t bs = bst[si.bst_base + b], be = bst[si.bst_base + b + 1];
         if (be > bs && bs > si.seg.start && be <= si.seg.start + si.seg.size)
             lcp[bs] = d + key_lcp(K[bs - 1], K[bs], f);
+    }
+}
+
+// LCP with the predecessor at the positions marked by k_lg_buckets, from the
+// final order (full comparison; there are at most two per oversized bucket).
+__global__ void k_fix_seams(const uint8_t* __restrict__ fixmark, uint32_t n, const uint8_t* __restrict__ chars,
+                            const uint64_t* __restrict__ offs, const uint32_t* __restrict__ lens,
+                            const uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        if (!fixmark[q] || q == 0) continue;
+        uint32_t a = perm[q - 1], b = perm[q];
+        uint32_t la = lens[a], lb = lens[b];
+        uint32_t m = la < lb ? la : lb;
+        WordStream A, B;
+        A.init(chars + offs[a], la, 0);
+        B.init(chars + offs[b], lb, 0);
+        uint32_t r = m;
+        for (uint32_t k = 0; k < m; k += 8) {
+            uint64_t x = A.next() ^ B.next();
+            if (x) {
+                uint32_t c = k + ((uint32_t)__clzll((long long)x) >> 3);
+                r = c < m ? c : m;
+                break;
+            }
+        }
+        lcp[q] = r;
     }
 }
 
@@ -537,15 +569,16 @@ struct LsBufs {
     Seg* large;
     uint32_t* cnt;
     uint32_t* segfmt;
+    uint8_t* fixmark;
     SpBufs sp;
     uint32_t cap_warp, cap_tiny, cap_med, cap_large;
 };
 
-void carve_ls(Arena& ar, uint32_t n, uint32_t p, LsBufs& b) {
+void carve_ls(Arena& ar, uint32_t n, uint32_t p, const sss_params& prm, LsBufs& b) {
     b.cap_warp = n / 2 + 2;
-    b.cap_tiny = n / (WARP_CAP + 1) + 2;
+    b.cap_tiny = n / (prm.warp_cap + 1) + 2;
     b.cap_med = n / (TINY_CAP + 1) + 2;
-    b.cap_large = n / (MED_CAP + 1) + p + 2;  // every large segment holds > MED_CAP strings
+    b.cap_large = n / (prm.cta_cap + 1) + p + 2;  // every large segment holds > cta_cap strings
     b.K = ar.take<uint64_t>(n);
     b.tK = ar.take<uint64_t>(n);
     b.tV = ar.take<uint32_t>(n);
@@ -555,6 +588,7 @@ void carve_ls(Arena& ar, uint32_t n, uint32_t p, LsBufs& b) {
     b.large = ar.take<Seg>(b.cap_large);
     b.cnt = ar.take<uint32_t>(4);
     b.segfmt = ar.take<uint32_t>(b.cap_large);
+    b.fixmark = ar.take<uint8_t>(n);
     carve_sp(ar, n, b.cap_large, b.sp);
 }
 
@@ -575,10 +609,9 @@ sss_status run_finishers(sss_ctx* ctx, const LsBufs& B, uint32_t nwarp, uint32_t
 }  // namespace
 
 size_t need_local_sort(uint32_t n, uint32_t p, const sss_params& prm) {
-    (void)prm;
     Arena ar;
     LsBufs b;
-    carve_ls(ar, n, p, b);
+    carve_ls(ar, n, p, prm, b);
     return ar.off + 256;
 }
 
@@ -611,21 +644,22 @@ sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p,
 
 sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const std::vector<Seg>& init,
                               const sss_params& prm, uint32_t* perm, uint32_t* lcp) {
-    (void)prm;
     const uint32_t n = in.n;
     if (n == 0) return SSS_OK;
     LsBufs B;
-    carve_ls(ar, n, 1, B);
+    carve_ls(ar, n, 1, prm, B);
+    const uint32_t warp_max = prm.warp_cap, med_max = prm.cta_cap, direct_max = prm.direct_cap;
     SSS_TRY(set_ls_attributes(ctx));
     SSS_TRY(sss_launch(ctx, "ls_init", k_init_perm, dim3((n + 255) / 256), dim3(256), 0, perm, lcp, n));
+    bool any_partition = false;
 
     // initial segments (partitions or instances), by size class
     std::vector<Seg> warp, tiny, med, large;
     for (const Seg& s : init) {
         if (s.size < 2) continue;
-        if (s.size <= (uint32_t)WARP_CAP) warp.push_back(s);
+        if (s.size <= warp_max) warp.push_back(s);
         else if (s.size <= (uint32_t)TINY_CAP) tiny.push_back(s);
-        else if (s.size <= (uint32_t)MED_CAP) med.push_back(s);
+        else if (s.size <= med_max) med.push_back(s);
         else large.push_back(s);
     }
     // pinned staging: segment info + tiles + counters
@@ -655,18 +689,18 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
         SSS_CUDA(cudaStreamSynchronize(ctx->stream));
     }
 
-    SegLists L{B.tiny, B.med, B.large, B.cnt, B.cap_tiny, B.cap_med, B.cap_large, B.warp, B.cap_warp};
+    SegLists L{B.tiny, B.med, B.large, B.cnt, B.cap_tiny, B.cap_med, B.cap_large, B.warp, B.cap_warp, warp_max, med_max};
     uint32_t rounds = 0;
     while (!large.empty()) {
         if (++rounds > 100000u) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: round limit exceeded");
         // segments that need the sampled partition first, whole-segment sorts after
         std::stable_partition(large.begin(), large.end(),
-                              [](const Seg& g) { return g.size > (uint32_t)DIRECT_CAP; });
+                              [direct_max](const Seg& g) { return g.size > direct_max; });
         uint32_t ns = (uint32_t)large.size();
         uint32_t npart = 0;
-        while (npart < ns && large[npart].size > (uint32_t)DIRECT_CAP) ++npart;
+        while (npart < ns && large[npart].size > direct_max) ++npart;
         uint32_t ntiles = 0, nbuckets = 0;
-        if (!plan_sp(large, LG_TARGET, B.sp, h_info, h_tiles, &ntiles, &nbuckets))
+        if (!plan_sp(large, prm.bucket_target, B.sp, h_info, h_tiles, &ntiles, &nbuckets))
             return sss_fail(ctx, SSS_ERR_CUDA, "local sort: internal capacity exceeded");
         const uint32_t ptiles = npart < ns ? h_info[npart].tile0 : ntiles;
         const uint32_t pbuckets = npart < ns ? h_info[npart].bk_base : nbuckets;
@@ -677,12 +711,14 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
                            (const LgSegInfo*)B.sp.info, in.chars, in.offs, in.lens, (const uint32_t*)perm, B.K,
                            B.segfmt));
         if (npart > 0) {
+            if (!any_partition) SSS_CUDA(cudaMemsetAsync(B.fixmark, 0, n, ctx->stream));
+            any_partition = true;
             SSS_TRY(launch_sp(ctx, B.sp, npart, ptiles, B.K, perm, B.tK, B.tV, "ls_lg_samples", "ls_lg_classify",
                               "ls_lg_offsets", "ls_lg_scatter"));
             SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets, dim3(pbuckets), dim3(BK_T),
                                (size_t)BK_CAP * (8 + 8 + 4 + 4), (const LgSegInfo*)B.sp.info,
                                (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt, (const uint64_t*)B.tK,
-                               (const uint32_t*)B.tV, in.lens, B.K, perm, lcp, L, ctx->d_err, npart));
+                               (const uint32_t*)B.tV, in.lens, B.K, perm, lcp, L, ctx->d_err, npart, B.fixmark));
             SSS_TRY(sss_launch(ctx, "ls_lg_seams", k_lg_seams, dim3(npart), dim3(512), 0,
                                (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt,
                                (const uint64_t*)B.K, lcp));
@@ -707,6 +743,9 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
             SSS_CUDA(cudaStreamSynchronize(ctx->stream));
         }
     }
+    if (any_partition)
+        SSS_TRY(sss_launch(ctx, "ls_fix_seams", k_fix_seams, dim3(std::min((n + 255) / 256, 4096u)), dim3(256), 0,
+                           (const uint8_t*)B.fixmark, n, in.chars, in.offs, in.lens, (const uint32_t*)perm, lcp));
     return SSS_OK;
 }
 
