@@ -65,3 +65,57 @@ def test_config1_full_size_plain():
     want = oracle.sort(ss)
     assert np.array_equal(m.u32(perm), want)
     assert np.array_equal(m.u32(lcp), oracle.lcp_array(ss, want))
+
+
+def test_config4_full_size_batch():
+    """All 4,096 instances (37.5M strings) in one batched call, every adjacent
+    pair of every instance checked (order, ties by index, lcp)."""
+    import datagen.cuda as dgc
+    import paper_2404_16517_gb300 as m
+    chars, offs, lens, first = dgc.config4()
+    sizes = np.diff(first).astype(np.int64)
+    perm, lcp, _ = m.sss_sort_batch(chars, offs, lens, first[:-1], sizes)
+    m.context().sync()
+    P, L = m.u32(perm), m.u32(lcp)
+    C, O, Ln = chars.cpu().numpy(), offs.cpu().numpy().view(np.uint64), lens.cpu().numpy().view(np.uint32)
+    del chars, offs, lens
+    for k in range(len(sizes)):
+        a, b = int(first[k]), int(first[k + 1])
+        sub = datagen.StringSet(C, O[a:b], Ln[a:b])
+        p = P[a:b]
+        assert np.array_equal(np.sort(p.astype(np.int64)), np.arange(b - a)), f"instance {k}: not a permutation"
+        assert oracle.check_sorted(sub, p, L[a:b]) == b - a, f"instance {k}"
+
+
+def test_largest_serving_request():
+    """One request of the largest size (2^24 strings, about 8.5 GB) through the
+    request loop, every adjacent pair checked."""
+    import datagen.cuda as dgc
+    from paper_2404_16517_gb300.serve import Request, Server
+    n, seed, ratio = 1 << 24, 0x5EED5, 0.5
+    tot = int(dgc.request_totals([seed], [n])[0])
+    got = {}
+
+    def grab(r):
+        got["perm"] = r.perm.cpu().numpy().view(np.uint32).copy()
+        got["lcp"] = r.lcp.cpu().numpy().view(np.uint32).copy()
+        got["chars"] = srv.engine.arena[r._chars_off: r._chars_off + r.chars].cpu().numpy()
+
+    srv = Server(budget_bytes=16 << 30, slots=1, on_done=grab)
+    r = Request(rid=0, n=n, chars=tot, seed=seed, ratio=ratio)
+    srv.run_closed_loop([r])
+    srv.close()
+    assert r.state == "done", r.error
+    # the request's own table: regenerate offsets/lengths relative to its first character
+    lens = torch.empty(n, dtype=torch.int32, device="cuda")
+    offs = torch.empty(n, dtype=torch.int64, device="cuda")
+    cp = torch.empty(n, dtype=torch.int32, device="cuda")
+    sc = torch.empty(dgc.request_scratch_words(n), dtype=torch.int64, device="cuda")
+    scratch_chars = torch.empty(tot, dtype=torch.uint8, device="cuda")
+    dgc.request_into(scratch_chars, 0, offs, lens, cp, sc, seed, n, ratio)
+    torch.cuda.synchronize()
+    C = scratch_chars.cpu().numpy()
+    assert np.array_equal(C, got["chars"]), "arena characters differ from the request's definition"
+    ss = datagen.StringSet(C, offs.cpu().numpy().view(np.uint64), lens.cpu().numpy().view(np.uint32))
+    assert np.array_equal(np.sort(got["perm"].astype(np.int64)), np.arange(n))
+    assert oracle.check_sorted(ss, got["perm"], got["lcp"]) == n
