@@ -84,6 +84,67 @@ struct WordStream {
     }
 };
 
+// WordStream with 16-byte loads: the next 4 words cost two aligned 16-byte
+// loads (half the load instructions, and half the L1 wavefronts of a gather
+// where every lane reads its own string).  A 16-byte-aligned chunk never
+// crosses a page, and only chunks that start before the string's end are
+// loaded, so it touches no memory the string's own pages do not hold.
+struct WordStream16 {
+    const ulonglong2* p;  // next aligned chunk to load
+    const uint8_t* end;
+    uint64_t a0;          // current aligned word (big-endian)
+    uint64_t a1;          // the word after it, when it came with a0's chunk (hi == 0)
+    uint32_t hi;          // 0: a0 is the low half of its chunk (a1 valid); 1: the high half
+    uint32_t sh;          // misalignment in bits
+    uint32_t rem;         // characters left from the current position
+    __device__ __forceinline__ void init(const uint8_t* __restrict__ s, uint32_t len, uint32_t d) {
+        rem = len > d ? len - d : 0;
+        uintptr_t a = (uintptr_t)(s + d);
+        const ulonglong2* c = reinterpret_cast<const ulonglong2*>(a & ~uintptr_t(15));
+        sh = (uint32_t)(a & 7) * 8;
+        hi = (uint32_t)((a >> 3) & 1);
+        end = s + len;
+        ulonglong2 v = rem ? __ldg(c) : make_ulonglong2(0ull, 0ull);
+        a0 = bswap64(hi ? v.y : v.x);
+        a1 = bswap64(v.y);
+        p = c + 1;
+    }
+    // the next 4 words (32 characters)
+    __device__ __forceinline__ void next4(uint64_t* w) {
+        ulonglong2 c1 = make_ulonglong2(0ull, 0ull), c2 = make_ulonglong2(0ull, 0ull);
+        if (rem > 0 && reinterpret_cast<const uint8_t*>(p) < end) c1 = __ldg(p);
+        if (rem > 16 - 8 * hi && reinterpret_cast<const uint8_t*>(p + 1) < end) c2 = __ldg(p + 1);
+        p += 2;
+        uint64_t x[5];
+        x[0] = a0;
+        if (hi) {  // a0 was the high half: the next words are c1.x, c1.y, c2.x, c2.y
+            x[1] = bswap64(c1.x);
+            x[2] = bswap64(c1.y);
+            x[3] = bswap64(c2.x);
+            x[4] = bswap64(c2.y);
+            a0 = x[4];
+        } else {   // a0 was the low half: a1 came with it
+            x[1] = a1;
+            x[2] = bswap64(c1.x);
+            x[3] = bswap64(c1.y);
+            x[4] = bswap64(c2.x);
+            a0 = x[4];
+            a1 = bswap64(c2.y);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            uint64_t v = sh ? ((x[i] << sh) | (x[i + 1] >> (64 - sh))) : x[i];
+            if (rem < 8) {
+                v = rem ? (v & (~0ull << (8 * (8 - rem)))) : 0ull;
+                rem = 0;
+            } else {
+                rem -= 8;
+            }
+            w[i] = v;
+        }
+    }
+};
+
 // Full LCP of a[d..] and b[d..] (capped at min(la, lb) - d and at VCAP), in
 // blocks of 32 characters with independent loads; *w = the 8 characters of `a`
 // at d + v (zero past its end).
@@ -131,7 +192,7 @@ __device__ __forceinline__ uint32_t lcp_full_w_ref(const uint8_t* __restrict__ a
     uint32_t r = 0;
     if (d < m) {
         uint32_t cap = m - d;
-        WordStream A;
+        WordStream16 A;
         A.init(a, la, d);
         r = cap;
         for (uint32_t k = 0; k < cap; k += 32) {

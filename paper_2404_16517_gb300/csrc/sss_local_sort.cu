@@ -574,11 +574,27 @@ struct LsBufs {
     uint32_t cap_warp, cap_tiny, cap_med, cap_large;
 };
 
+// The size-class knobs of the local sort; 0 (e.g. internal callers passing
+// sss_params{}) means the default.  Values are clamped by the API already.
+struct LsKnobs {
+    uint32_t warp_cap, cta_cap, direct_cap, bucket_target;
+};
+static LsKnobs ls_knobs(const sss_params& prm) {
+    LsKnobs k;
+    k.warp_cap = prm.warp_cap ? std::min(prm.warp_cap, 32u) : 32u;
+    k.cta_cap = prm.cta_cap ? std::min(std::max(prm.cta_cap, (uint32_t)TINY_CAP), (uint32_t)MED_CAP) : (uint32_t)MED_CAP;
+    k.direct_cap = prm.direct_cap ? std::min(std::max(prm.direct_cap, k.cta_cap), (uint32_t)DIRECT_CAP)
+                                  : (uint32_t)DIRECT_CAP;
+    k.bucket_target = prm.bucket_target ? std::min(std::max(prm.bucket_target, 256u), (uint32_t)BK_CAP) : 2048u;
+    return k;
+}
+
 void carve_ls(Arena& ar, uint32_t n, uint32_t p, const sss_params& prm, LsBufs& b) {
+    const LsKnobs kn = ls_knobs(prm);
     b.cap_warp = n / 2 + 2;
-    b.cap_tiny = n / (prm.warp_cap + 1) + 2;
+    b.cap_tiny = n / (kn.warp_cap + 1) + 2;
     b.cap_med = n / (TINY_CAP + 1) + 2;
-    b.cap_large = n / (prm.cta_cap + 1) + p + 2;  // every large segment holds > cta_cap strings
+    b.cap_large = n / (kn.cta_cap + 1) + p + 2;  // every large segment holds > cta_cap strings
     b.K = ar.take<uint64_t>(n);
     b.tK = ar.take<uint64_t>(n);
     b.tV = ar.take<uint32_t>(n);
@@ -648,7 +664,8 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
     if (n == 0) return SSS_OK;
     LsBufs B;
     carve_ls(ar, n, 1, prm, B);
-    const uint32_t warp_max = prm.warp_cap, med_max = prm.cta_cap, direct_max = prm.direct_cap;
+    const LsKnobs kn = ls_knobs(prm);
+    const uint32_t warp_max = kn.warp_cap, med_max = kn.cta_cap, direct_max = kn.direct_cap;
     SSS_TRY(set_ls_attributes(ctx));
     SSS_TRY(sss_launch(ctx, "ls_init", k_init_perm, dim3((n + 255) / 256), dim3(256), 0, perm, lcp, n));
     bool any_partition = false;
@@ -700,7 +717,7 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
         uint32_t npart = 0;
         while (npart < ns && large[npart].size > direct_max) ++npart;
         uint32_t ntiles = 0, nbuckets = 0;
-        if (!plan_sp(large, prm.bucket_target, B.sp, h_info, h_tiles, &ntiles, &nbuckets))
+        if (!plan_sp(large, kn.bucket_target, B.sp, h_info, h_tiles, &ntiles, &nbuckets))
             return sss_fail(ctx, SSS_ERR_CUDA, "local sort: internal capacity exceeded");
         const uint32_t ptiles = npart < ns ? h_info[npart].tile0 : ntiles;
         const uint32_t pbuckets = npart < ns ? h_info[npart].bk_base : nbuckets;
