@@ -331,7 +331,14 @@ constexpr size_t finish_smem(int cap) { return (size_t)cap * (8 + 8 + 4 * 7); }
 
 // ---------------------------------------------------------------------------
 // Large path.
-__global__ void __launch_bounds__(LG_T) k_lg_ext(const LgTile* __restrict__ tiles, const LgSegInfo* __restrict__ info,
+// the uncached LCP scan, kept out of line: it is the rare path of k_lg_ext
+// (shared prefixes longer than the 512 cached reference characters)
+__device__ __noinline__ uint32_t lcp_full_w_outline(const uint8_t* a, uint32_t la, const uint8_t* b, uint32_t lb,
+                                                    uint32_t d, uint64_t* w) {
+    return lcp_full_w(a, la, b, lb, d, w);
+}
+
+__global__ void __launch_bounds__(LG_T, 6) k_lg_ext(const LgTile* __restrict__ tiles, const LgSegInfo* __restrict__ info,
                                                  const uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
                                                  const uint32_t* __restrict__ lens, const uint32_t* __restrict__ perm,
                                                  uint64_t* __restrict__ K, uint32_t* __restrict__ segfmt) {
@@ -359,7 +366,7 @@ __global__ void __launch_bounds__(LG_T) k_lg_ext(const LgTile* __restrict__ tile
             uint32_t le = lens[e];
             uint32_t mlen = le < rl ? le : rl;
             v = (mlen <= d + 8 * (NREF - 4)) ? lcp_full_w_ref(chars + offs[e], le, rl, refw, d, &w)
-                                             : lcp_full_w(chars + offs[e], le, rs, rl, d, &w);
+                                             : lcp_full_w_outline(chars + offs[e], le, rs, rl, d, &w);
         }
         uint32_t rho = (v >> 3) < NREF ? (uint32_t)(refw[v >> 3] >> (56 - 8 * (v & 7))) & 0xFFu
                                        : (uint32_t)(load_word_be(rs, rl, d + v) >> 56);
