@@ -210,7 +210,7 @@ def main():
     ap.add_argument("--breakdown", action="store_true", help="per-kernel times to stderr")
     ap.add_argument("--merge-ms", type=int, default=0, help="merge segment spacing (0 = library default)")
     ap.add_argument("--p", type=int, default=P, help="partitions (profiling of smaller cases)")
-    ap.add_argument("--workload", default="all", choices=["all", "pdms", "batch", "serve"])
+    ap.add_argument("--workload", default="all", choices=["all", "pdms", "batch", "serve", "charsample"])
     ap.add_argument("--batch-instances", type=int, default=4096)
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner (default knobs)")
     ap.add_argument("--per-instance-steps", type=int, default=2,
@@ -244,9 +244,10 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    if args.workload in ("batch", "serve"):
+    if args.workload in ("batch", "serve", "charsample"):
         ctx = sss.context(local)
-        res = bench_batch(args, dev, ctx) if args.workload == "batch" else bench_serve(args, dev)
+        res = {"batch": bench_batch, "charsample": bench_charsample}.get(args.workload, None)
+        res = res(args, dev, ctx) if res else bench_serve(args, dev)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "n_gpus": ws, **res}), flush=True)
         return 0
@@ -380,6 +381,8 @@ def main():
         if ws == 1 and args.workload == "all":
             del chars, offs, lens, perm, lcp, dist_t, approx
             out["batch"] = bench_batch(args, dev, ctx)
+            torch.cuda.empty_cache()
+            out["char_sampling"] = bench_charsample(args, dev, ctx)
             torch.cuda.empty_cache()
             out["serving"] = bench_serve(args, dev)
             out["p50_ms"] = out["serving"].get("p50_ms")
@@ -584,6 +587,62 @@ def bench_serve(args, dev):
                "latency": "scheduled arrival to batch completion on the device (includes queueing, admission, "
                           "on-device generation of the request's strings, sort)"})
     return st
+
+
+def bench_charsample(args, dev, ctx):
+    """String-based against character-based regular sampling (Section 3.1.2) on a
+    set whose distinguishing prefixes are skewed and sort last: 4,194,304
+    strings over A-Z; those starting with Z are 1000 characters long and share
+    992 of them, the others are 20 uniform characters; p = 16, v = 16.  Reports
+    the step time and the characters (approx-truncated) of the largest bucket
+    over the mean bucket."""
+    import torch
+
+    import datagen.cuda as dgc
+    import paper_2404_16517_gb300 as sss
+    n, p = args.n, args.p
+    chars, offs, lens = dgc.skew_set(6, n)
+    N = int(lens.to(torch.int64).sum().item())
+    st = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rp, _ = sss.sss_local_sort(chars, offs, lens, p, ctx=ctx)
+    out = {"workload": f"skew_{n}x(20|1000, Z-strings share 992)_AZ_p{p}", "strings": n, "chars": N}
+    perms = {}
+    v = 16
+    out["v"] = v
+    for name, flags in (("string_based", 0), ("char_based", sss.SSS_FLAG_CHAR_SAMPLING)):
+        prm = sss.params(v=v, flags=flags)
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        lcp = torch.empty(n, dtype=torch.int32, device=dev)
+        ap = torch.empty(n, dtype=torch.int32, device=dev)
+
+        def step():
+            sss.sss_sort(chars, offs, lens, p, prm, perm, lcp, out_approx=ap, ctx=ctx)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.steps):
+            step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        # bucket characters from this flag's partition of the approx-truncated runs
+        _, bnd = sss.sss_partition(chars, offs, lens, rp, p, trunc=ap, prm=prm, ctx=ctx)
+        tl = ap.to(torch.int64)[rp.to(torch.int64)]
+        cs = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+        cs[1:] = torch.cumsum(tl, 0)
+        lo = torch.tensor([i * n // p for i in range(p)], dtype=torch.int64, device=dev)
+        b = bnd.to(torch.int64) + lo[:, None]
+        per = (cs[b[:, 1:]] - cs[b[:, :-1]]).sum(0)
+        Nt = int(tl.sum().item())
+        out[name] = {"ms_per_step": ms, "chars_per_s": N / (ms / 1e3),
+                     "bucket_chars_max_over_mean": float(per.max().item()) / (Nt / p),
+                     "bucket_chars_min_over_mean": float(per.min().item()) / (Nt / p)}
+        perms[name] = (perm.clone(), lcp.clone())
+    out["outputs_identical"] = bool(torch.equal(perms["string_based"][0], perms["char_based"][0]) and
+                                    torch.equal(perms["string_based"][1], perms["char_based"][1]))
+    return out
 
 
 def algorithmic_bytes(kernel: str, n: int, N: int, D: int, Dapprox: int, launches_per_step: float) -> float:

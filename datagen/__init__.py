@@ -310,3 +310,35 @@ def request_chars(seed: int, n: int, len_lo: int = 16, len_hi: int = 1000, chunk
         i = np.arange(a, min(n, a + chunk), dtype=np.uint64)
         tot += int((len_lo + uniform_index(rng(seed, ST_LEN, i), len_hi - len_lo + 1)).sum())
     return tot
+
+
+def skew_layout(seed: int, n: int, short: int = 20, long: int = 1000, a: int = 26):
+    """Length-skewed set layout: string i starts with letter uniform_index(rng(seed,
+    ST_PICK, i), a); strings starting with the last letter have `long`
+    characters, the others `short`.  Returns (first letter index, lens, offs)."""
+    first = uniform_index(rng(seed, ST_PICK, np.arange(n, dtype=np.uint64)), a).astype(np.uint32)
+    lens = np.where(first == a - 1, long, short).astype(np.uint32)
+    offs = np.zeros(n, dtype=np.uint64)
+    if n > 1:
+        offs[1:] = np.cumsum(lens[:-1].astype(np.uint64))
+    return first, lens, offs
+
+
+def skew_set(seed: int = 6, n: int = 1 << 22, short: int = 20, long: int = 1000,
+             alphabet: np.ndarray = UPPER) -> StringSet:
+    """Strings whose sort order and distinguishing-prefix length are correlated,
+    the case character-based sampling is for: first letter as in skew_layout;
+    a long string (last letter first) copies characters 1 .. long-9 from one
+    seeded template and ends in 8 uniform characters, so all long strings share
+    long-8 characters and sort last; short strings are uniform after their
+    first letter (counter = offset + j; template counter = j)."""
+    a = int(alphabet.shape[0])
+    first, lens, offs = skew_layout(seed, n, short, long, a)
+    N = int(lens.astype(np.uint64).sum())
+    chars = alphabet[uniform_index(rng(seed, ST_CHARS, np.arange(N, dtype=np.uint64)), a)]
+    tmpl = alphabet[uniform_index(rng(seed, ST_TEMPLATE, np.arange(long, dtype=np.uint64)), a)]
+    for i in np.nonzero(first == a - 1)[0]:
+        o = int(offs[i])
+        chars[o + 1: o + long - 8] = tmpl[1: long - 8]
+    chars[offs.astype(np.int64)] = alphabet[first]
+    return StringSet(chars, offs, lens, f"skew(seed={seed},n={n})")

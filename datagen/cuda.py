@@ -59,6 +59,9 @@ def _configure(_lib):
     _lib.sssgen_request_totals.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint32, C.c_uint32,
                                            C.c_void_p, C.c_void_p]
     _lib.sssgen_request_scratch_words.argtypes = [C.c_uint64]
+    _lib.sssgen_skew_chars.restype = C.c_int
+    _lib.sssgen_skew_chars.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint32,
+                                       C.c_char_p, C.c_uint32, C.c_void_p]
     _lib.sssgen_req_desc_bytes.restype = C.c_uint32
     _lib.sssgen_req_desc_bytes.argtypes = []
     _lib.sssgen_request_batch.restype = C.c_int
@@ -226,3 +229,24 @@ def request_batch_into(chars, offs, lens, cp_scratch, sum_scratch, desc_dev, m: 
                                     len_hi, alphabet, len(alphabet), C.c_void_p(st))
     if rc != 0:
         raise RuntimeError(f"sssgen_request_batch failed ({rc})")
+
+
+def skew_set(seed: int = 6, n: int = 1 << 22, short: int = 20, long: int = 1000, device: str = "cuda"):
+    """Device tensors (chars, offs, lens) of datagen.skew_set, byte-identical."""
+    import numpy as np
+    import torch
+
+    import datagen
+    alphabet = b"ABCDEFGHIJKLMNOPQRSTUVWXYZ"
+    _, lens, offs = datagen.skew_layout(seed, n, short, long, len(alphabet))
+    N = int(lens.astype(np.uint64).sum())
+    chars = torch.empty(max(1, N), dtype=torch.uint8, device=device)
+    t_offs = torch.from_numpy(offs.view(np.int64)).to(device)
+    t_lens = torch.from_numpy(lens.view(np.int32)).to(device)
+    st = torch.cuda.current_stream(chars.device).cuda_stream
+    rc = lib().sssgen_skew_chars(C.c_void_p(chars.data_ptr()), C.c_void_p(t_offs.data_ptr()),
+                                 C.c_void_p(t_lens.data_ptr()), n, seed, long, alphabet, len(alphabet),
+                                 C.c_void_p(st))
+    if rc != 0:
+        raise RuntimeError(f"sssgen_skew_chars failed ({rc})")
+    return chars, t_offs, t_lens

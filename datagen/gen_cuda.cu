@@ -227,7 +227,45 @@ __global__ void k_batch_chars(const ReqDesc* __restrict__ R, uint32_t m, uint64_
     }
 }
 
+// length-skewed set: first character from the pick stream, the rest uniform
+// (counter = offset + j); one warp per string
+// (strings of length `lng` whose first letter is the last one copy characters
+// 1 .. lng-9 from the template stream)
+__global__ void k_skew_chars(uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
+                             const uint32_t* __restrict__ lens, uint64_t n, uint64_t kp, uint64_t kc, uint64_t kt,
+                             uint32_t lng, Alpha al) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t g = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < n; g += warps) {
+        uint64_t o = offs[g];
+        uint32_t l = lens[g];
+        uint32_t f = uidx(draw(kp, g), al.n);
+        bool tm = (f == al.n - 1) && l == lng;
+        for (uint32_t j = lane; j < l; j += 32) {
+            uint32_t c;
+            if (j == 0) c = f;
+            else if (tm && j + 8 < lng) c = uidx(draw(kt, j), al.n);
+            else c = uidx(draw(kc, o + j), al.n);
+            chars[o + j] = al.c[c];
+        }
+    }
+}
+
 }  // namespace
+
+extern "C" int sssgen_skew_chars(uint8_t* chars, const uint64_t* offs, const uint32_t* lens, uint64_t n,
+                                 uint64_t seed, uint32_t lng, const uint8_t* alphabet, uint32_t alen, void* stream) {
+    if (alen == 0 || alen > 64) return 1;
+    if (n == 0) return 0;
+    Alpha al{};
+    for (uint32_t k = 0; k < alen; ++k) al.c[k] = alphabet[k];
+    al.n = alen;
+    uint32_t grid = (uint32_t)((n + 7) / 8 < 65536 ? (n + 7) / 8 : 65536);
+    k_skew_chars<<<grid, 256, 0, (cudaStream_t)stream>>>(chars, offs, lens, n, stream_key(seed, ST_PICK),
+                                                         stream_key(seed, ST_CHARS), stream_key(seed, ST_TEMPLATE),
+                                                         lng, al);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
 
 extern "C" uint32_t sssgen_req_desc_bytes() { return (uint32_t)sizeof(ReqDesc); }
 

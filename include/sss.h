@@ -63,6 +63,11 @@ typedef enum sss_status {
 #define SSS_FLAG_MERGE_TREE 0x10u /* merge: pairwise LCP-merge tree over whole
                                   buckets instead of second-level sub-buckets
                                   merged inside one CTA each */
+#define SSS_FLAG_CHAR_SAMPLING 0x20u /* partition: character-based regular sampling
+                                  (Section 3.1.2): about p(v+1) samples at equally
+                                  spaced character positions of the runs (truncated
+                                  lengths), so buckets balance characters rather than
+                                  strings; string-based (Section 3.1.1) otherwise */
 
 typedef struct sss_params {
     uint32_t kmin;      /* first doubling round: prefix length 2^kmin (default 0) */
@@ -160,6 +165,12 @@ sss_status sss_dist_prefix(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars,
  * ranks ceil(t*n_i/(v+1)) - 1 (t = 1..v+1); the samples are sorted (truncated
  * strings, then index) and f_j = V[floor(j*|V|/p) - 1] for 0 < j < p
  * (UINT32_MAX = minus infinity when the index is negative).
+ * With SSS_FLAG_CHAR_SAMPLING (Section 3.1.2): with N the total truncated
+ * length and want = p(v+1), partition i (C_i characters in its run) draws
+ * ceil(C_i*want/N) - 1 samples, the strings of its run covering the character
+ * positions floor(t*N/want), t = 1, 2, ...; while fewer than want samples
+ * exist, the first non-empty partitions add their last string, one each.
+ * Splitters are then chosen as above.  N == 0 falls back to string-based.
  * trunc        : uint32_t[n] or NULL; string i is compared as its first
  *                trunc[i] chars (trunc[i] <= lengths[i]).
  * out_splitters: uint32_t[p-1] input indices of f_1..f_{p-1} (may be NULL if p==1)

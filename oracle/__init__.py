@@ -63,6 +63,7 @@ def lib():
             "oracle_part_lo": (u32, [u32, u32, u32]),
             "oracle_local_sort": (None, [P8, P64, P32, P32, u32, u32, P32, P32]),
             "oracle_samples": (u32, [P32, u32, u32, u32, P32]),
+            "oracle_samples_char": (u32, [P32, P32, P32, u32, u32, u32, P32]),
             "oracle_splitters": (None, [P8, P64, P32, P32, P32, u32, u32, P32]),
             "oracle_bounds": (None, [P8, P64, P32, P32, P32, u32, u32, P32, P32]),
             "oracle_merge": (None, [P8, P64, P32, P32, P32, u32, u32, P32, P32, P32]),
@@ -175,6 +176,14 @@ def samples(run_perm, n: int, p: int, v: int) -> np.ndarray:
     return out[:ns].copy()
 
 
+def samples_char(ss, run_perm, p: int, v: int, trunc=None) -> np.ndarray:
+    """Character-based regular sampling (Section 3.1.2)."""
+    out = np.empty(p * (v + 1), np.uint32)
+    t = None if trunc is None else _u32(trunc)
+    ns = lib().oracle_samples_char(_p(_u32(ss.lens)), _p(t), _p(_u32(run_perm)), ss.n, p, v, _p(out))
+    return out[:ns].copy()
+
+
 def splitters(ss, smp, p: int, trunc=None):
     """Returns (sorted samples, splitters u32[p-1], UINT32_MAX = minus infinity)."""
     c, o, l = _views(ss)
@@ -209,16 +218,18 @@ def check_sorted(ss, perm, lcp) -> int:
     return int(lib().oracle_check_sorted(_p(c), _p(o), _p(l), _p(_u32(perm)), _p(_u32(lcp)), ss.n))
 
 
-def pdms(ss, p: int, v: int = 2, kmin: int = 0, kmax: int | None = None, seed: int = 0):
+def pdms(ss, p: int, v: int = 2, kmin: int = 0, kmax: int | None = None, seed: int = 0,
+         char_sampling: bool = False):
     """The prefix-doubling merge sort pipeline step by step (Sections 3 and 4):
-    local sort of each partition, prefix doubling, string-based regular sampling,
+    local sort of each partition, prefix doubling, regular sampling (string-based,
+    or character-based on the approx-truncated lengths, Section 3.1.2),
     splitters, bucket bounds, and the merge of the buckets on approx-truncated
     strings.  Returns a dict with every intermediate array."""
     if kmax is None:
         kmax = default_kmax(ss)
     run_perm, run_lcp = local_sort(ss, p)
     approx = doubling(ss, kmin, kmax, seed)
-    smp = samples(run_perm, ss.n, p, v)
+    smp = samples_char(ss, run_perm, p, v, approx) if char_sampling else samples(run_perm, ss.n, p, v)
     sorted_smp, spl = splitters(ss, smp, p, approx)
     bnd = bounds(ss, run_perm, p, spl, approx)
     perm, lcp = merge(ss, run_perm, p, bnd, approx)

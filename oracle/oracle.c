@@ -279,6 +279,62 @@ uint32_t oracle_samples(const uint32_t* run_perm, uint32_t n, uint32_t p, uint32
     return ns;
 }
 
+/* Character-based regular sampling (Section 3.1.2; appendix "Character Based
+ * Sampling").  Sampling distance w = N / (p (v+1)) with N the total number of
+ * (truncated) characters of all partitions.  Partition i, whose sorted run has
+ * C_i characters, draws ceil(C_i / w) - 1 samples at the character positions
+ * floor(t * w), t = 1, 2, ..., of its run's character array (the run's strings
+ * concatenated in sorted order); each position is moved back to the start of
+ * the string holding it, i.e. the sample is that string.  If all partitions
+ * together draw fewer than p (v+1) samples, the first non-empty partitions draw
+ * one additional sample each, their last string, until there are p (v+1).
+ * With N = 0 (no characters at all) this falls back to oracle_samples.
+ * Integer arithmetic: ceil(C_i p (v+1) / N) - 1 and floor(t N / (p (v+1))).
+ * samples_out: up to p*(v+1) indices (returns the count). */
+uint32_t oracle_samples_char(const uint32_t* lens, const uint32_t* trunc, const uint32_t* run_perm, uint32_t n,
+                             uint32_t p, uint32_t v, uint32_t* samples_out) {
+    const uint64_t want = (uint64_t)p * (v + 1);
+    uint64_t N = 0;
+    for (uint32_t q = 0; q < n; ++q) N += trunc ? trunc[q] : lens[q];
+    if (N == 0) return oracle_samples(run_perm, n, p, v, samples_out);
+    uint32_t ns = 0;
+    uint64_t total = 0;
+    for (uint32_t i = 0; i < p; ++i) {  /* how many each partition draws */
+        uint32_t lo = oracle_part_lo(n, p, i), hi = oracle_part_lo(n, p, i + 1);
+        uint64_t Ci = 0;
+        for (uint32_t q = lo; q < hi; ++q) Ci += trunc ? trunc[run_perm[q]] : lens[run_perm[q]];
+        uint64_t cnt = (Ci * want + N - 1) / N;  /* ceil(C_i / w) */
+        total += cnt ? cnt - 1 : 0;
+    }
+    uint64_t extra = total < want ? want - total : 0;
+    for (uint32_t i = 0; i < p; ++i) {
+        uint32_t lo = oracle_part_lo(n, p, i), hi = oracle_part_lo(n, p, i + 1);
+        if (hi == lo) continue;
+        uint64_t Ci = 0;
+        for (uint32_t q = lo; q < hi; ++q) Ci += trunc ? trunc[run_perm[q]] : lens[run_perm[q]];
+        uint64_t cnt = (Ci * want + N - 1) / N;
+        cnt = cnt ? cnt - 1 : 0;
+        for (uint64_t t = 1; t <= cnt; ++t) {
+            uint64_t x = (t * N) / want;  /* character position floor(t w) in the run */
+            /* the string of the run whose characters contain position x */
+            uint64_t start = 0;
+            for (uint32_t q = lo; q < hi; ++q) {
+                uint64_t len = trunc ? trunc[run_perm[q]] : lens[run_perm[q]];
+                if (x < start + len) {
+                    samples_out[ns++] = run_perm[q];
+                    break;
+                }
+                start += len;
+            }
+        }
+        if (extra > 0) {
+            samples_out[ns++] = run_perm[hi - 1];
+            --extra;
+        }
+    }
+    return ns;
+}
+
 /* Splitter computation (Section 3.1.1): sort the samples, then
  * f_j = V[j*|V|/r - 1] for 0 < j < r (here r = p).  When |V| is not a multiple of
  * p the index is floor(j*|V|/p) - 1; a negative index means f_j = minus infinity

@@ -90,6 +90,11 @@ void oracle_local_sort(const uint8_t* chars, const uint64_t* offs, const uint32_
  * splitters_out: p-1 entries, UINT32_MAX for "minus infinity". */
 uint32_t oracle_samples(const uint32_t* run_perm, uint32_t n, uint32_t p, uint32_t v,
                         uint32_t* samples_out);
+/* Character-based regular sampling (Section 3.1.2): about p*(v+1) samples taken
+ * at equally spaced character positions of the runs' character arrays (trunc
+ * lengths when given).  samples_out: up to p*(v+1) indices (returns the count). */
+uint32_t oracle_samples_char(const uint32_t* lens, const uint32_t* trunc, const uint32_t* run_perm, uint32_t n,
+                             uint32_t p, uint32_t v, uint32_t* samples_out);
 void oracle_splitters(const uint8_t* chars, const uint64_t* offs, const uint32_t* lens,
                       const uint32_t* trunc, uint32_t* samples, uint32_t ns, uint32_t p,
                       uint32_t* splitters_out);

@@ -372,7 +372,7 @@ sss_status sss_partition(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, c
     char* ws;
     SSS_TRY(sss_workspace(ctx, need_partition(n, p, prm.v), &ws));
     Arena ar{ws, 0, 0};
-    return impl_partition(ctx, ar, in, trunc, run_perm, p, prm.v, out_splitters, out_bounds);
+    return impl_partition(ctx, ar, in, trunc, run_perm, p, prm.v, prm.flags, out_splitters, out_bounds);
 }
 
 sss_status sss_lcp_merge(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,

@@ -175,7 +175,7 @@ sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& in, const uint
 
 size_t need_partition(uint32_t n, uint32_t p, uint32_t v);
 sss_status impl_partition(sss_ctx* ctx, Arena& ar, const StrIn& in, const uint32_t* trunc, const uint32_t* run_perm,
-                          uint32_t p, uint32_t v, uint32_t* out_spl, uint32_t* out_bounds);
+                          uint32_t p, uint32_t v, uint32_t flags, uint32_t* out_spl, uint32_t* out_bounds);
 size_t need_merge(uint32_t n, uint32_t p, uint32_t v, uint64_t nrecchars);
 sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, const uint32_t* trunc,
                       const uint32_t* run_perm, const uint32_t* run_lcp, uint32_t p, uint32_t v, uint32_t ms,

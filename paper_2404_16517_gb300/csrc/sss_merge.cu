@@ -121,6 +121,122 @@ __global__ void k_c_splitters(const uint32_t* __restrict__ smp, const uint32_t* 
     spl[j - 1] = k < 0 ? MINF : smp[sperm[k]];
 }
 
+// ---- character-based regular sampling (Section 3.1.2) ----------------------
+// C_i = characters (truncated lengths) of partition i: input indices [lo_i, hi_i)
+__global__ void k_c_chartot(Strs S, uint32_t n, uint32_t p, unsigned long long* __restrict__ tot) {
+    const uint32_t i = blockIdx.y;
+    const uint32_t lo = part_lo(n, p, i), hi = part_lo(n, p, i + 1);
+    uint64_t v = 0;
+    for (uint32_t q = lo + blockIdx.x * blockDim.x + threadIdx.x; q < hi; q += gridDim.x * blockDim.x) v += tlen(S, q);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(SSS_FULL, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&tot[i], (unsigned long long)v);
+}
+
+// P[q] = characters of the run positions before q (runs in position order), in
+// three passes over chunks of CP_CHUNK positions
+constexpr uint32_t CP_T = 256, CP_PER = 16, CP_CHUNK = CP_T * CP_PER;
+
+__device__ __forceinline__ uint64_t cp_block_excl(uint64_t v, uint64_t* wt, uint64_t* total) {
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint64_t x = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t y = __shfl_up_sync(SSS_FULL, x, d);
+        if (lane >= (uint32_t)d) x += y;
+    }
+    if (lane == 31) wt[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t run = 0;
+        for (uint32_t k = 0; k < CP_T / 32; ++k) {
+            uint64_t t = wt[k];
+            wt[k] = run;
+            run += t;
+        }
+        *total = run;
+    }
+    __syncthreads();
+    return wt[w] + x - v;
+}
+
+__global__ void __launch_bounds__(CP_T) k_c_psum(Strs S, const uint32_t* __restrict__ run_perm, uint32_t n,
+                                                  uint64_t* __restrict__ csum) {
+    __shared__ uint64_t wt[CP_T / 32], tot;
+    const uint64_t q0 = (uint64_t)blockIdx.x * CP_CHUNK + (uint64_t)threadIdx.x * CP_PER;
+    uint64_t v = 0;
+    for (uint32_t k = 0; k < CP_PER; ++k)
+        if (q0 + k < n) v += tlen(S, run_perm[q0 + k]);
+    cp_block_excl(v, wt, &tot);
+    if (threadIdx.x == 0) csum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(CP_T) k_c_pscan(uint64_t* __restrict__ csum, uint32_t nc) {
+    __shared__ uint64_t wt[CP_T / 32], tot;
+    uint64_t carry = 0;
+    for (uint32_t b0 = 0; b0 < nc; b0 += CP_T) {
+        const uint32_t i = b0 + threadIdx.x;
+        uint64_t v = i < nc ? csum[i] : 0;
+        uint64_t e = cp_block_excl(v, wt, &tot);
+        if (i < nc) csum[i] = carry + e;
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(CP_T) k_c_pwrite(Strs S, const uint32_t* __restrict__ run_perm, uint32_t n,
+                                                    const uint64_t* __restrict__ csum, uint64_t* __restrict__ P) {
+    __shared__ uint64_t wt[CP_T / 32], tot;
+    const uint64_t q0 = (uint64_t)blockIdx.x * CP_CHUNK + (uint64_t)threadIdx.x * CP_PER;
+    uint32_t l[CP_PER];
+    uint64_t v = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < CP_PER; ++k) {
+        l[k] = q0 + k < n ? tlen(S, run_perm[q0 + k]) : 0u;
+        v += l[k];
+    }
+    uint64_t run = csum[blockIdx.x] + cp_block_excl(v, wt, &tot);
+#pragma unroll
+    for (uint32_t k = 0; k < CP_PER; ++k) {
+        if (q0 + k < n) P[q0 + k] = run;
+        run += l[k];
+        if (q0 + k + 1 == n) P[n] = run;
+    }
+}
+
+// sample g of partition i: the string of run i that covers character position
+// floor(t N / want) of the run's character array, t = g - so[i] + 1 (t <= cnt[i]),
+// else the run's last string (the additional sample of the first partitions)
+__global__ void k_c_csamples(const uint32_t* __restrict__ run_perm, uint32_t n, uint32_t p, Strs S,
+                             const uint64_t* __restrict__ P, const uint32_t* __restrict__ so,
+                             const uint32_t* __restrict__ cnt, uint64_t N, uint64_t want, uint32_t* __restrict__ smp,
+                             uint64_t* __restrict__ s_offs, uint32_t* __restrict__ s_lens) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= so[p]) return;
+    uint32_t a = 0, b = p;  // last i with so[i] <= g
+    while (b - a > 1) {
+        uint32_t mid = (a + b) >> 1;
+        if (so[mid] <= g) a = mid; else b = mid;
+    }
+    const uint32_t i = a;
+    const uint32_t lo = part_lo(n, p, i), hi = part_lo(n, p, i + 1);
+    const uint64_t t = (uint64_t)(g - so[i]) + 1;
+    uint32_t q;
+    if (t <= cnt[i]) {
+        const uint64_t X = P[lo] + (t * N) / want;
+        uint32_t x0 = lo, x1 = hi;  // last q in [lo, hi) with P[q] <= X
+        while (x1 - x0 > 1) {
+            uint32_t mid = (x0 + x1) >> 1;
+            if (P[mid] <= X) x0 = mid; else x1 = mid;
+        }
+        q = x0;
+    } else {
+        q = hi - 1;
+    }
+    const uint32_t s = run_perm[q];
+    smp[g] = s;
+    s_offs[g] = S.offs[s];
+    s_lens[g] = tlen(S, s);
+}
+
 // bounds[i*(p+1)+j] = #{ s in run i : s <= f_j }, LCP-aware binary search (one
 // warp per search, warp-wide comparisons)
 __global__ void k_c_bounds(const uint32_t* __restrict__ run_perm, uint32_t n, uint32_t p, Strs S,
@@ -899,6 +1015,11 @@ struct MgBufs {
     uint32_t* sl0;
     uint32_t* sl1;
     uint32_t* cnt;
+    unsigned long long* ctot;  // character totals of the partitions (character-based sampling)
+    uint64_t* cpre;            // character prefix over run positions, n + 1
+    uint64_t* csum;            // chunk sums of cpre
+    uint32_t* so;              // sample offsets per partition, p + 1
+    uint32_t* scnt;            // equally spaced samples per partition
     Arena sub;  // work memory for sorting the samples
     // second level
     uint32_t cap_s2, cap_nsb;
@@ -934,10 +1055,14 @@ void carve_mg_small(Arena& ar, uint32_t n, uint32_t p, uint32_t v, MgBufs& b) {
     b.spl = ar.take<uint32_t>(p);
     b.bounds = ar.take<uint32_t>((size_t)p * (p + 1));
     b.cnt = ar.take<uint32_t>(4);
+    b.ctot = ar.take<unsigned long long>(p);
+    b.cpre = ar.take<uint64_t>((size_t)n + 1);
+    b.csum = ar.take<uint64_t>((size_t)n / CP_CHUNK + 2);
+    b.so = ar.take<uint32_t>(p + 1);
+    b.scnt = ar.take<uint32_t>(p);
     size_t sub = need_local_sort(ns, 1, sss_params{});
     char* base = ar.take<char>(sub);
     b.sub = Arena{base, sub, 0};
-    (void)n;
 }
 
 constexpr uint32_t MAX_P_TWO_LEVEL = 256;
@@ -1022,16 +1147,73 @@ __global__ void k_iota(uint32_t* a, uint32_t n) {
 }  // namespace
 
 // Stage C into b (splitters and bounds on the device).
+// Character-based samples (Section 3.1.2) into b.smp/s_offs/s_lens; *ns_out =
+// their count, or 0 when the strings hold no characters (string-based then).
+static sss_status char_samples(sss_ctx* ctx, const uint32_t* run_perm, uint32_t n, uint32_t p, uint32_t v,
+                               const Strs& S, MgBufs& b, uint32_t* ns_out) {
+    *ns_out = 0;
+    SSS_CUDA(cudaMemsetAsync(b.ctot, 0, sizeof(unsigned long long) * p, ctx->stream));
+    const uint32_t per_part = (n / p + 1 + 8191) / 8192;
+    SSS_TRY(sss_launch(ctx, "c_chartot", k_c_chartot, dim3(std::max(1u, std::min(per_part, 1024u)), p), dim3(256), 0,
+                       S, n, p, b.ctot));
+    const uint32_t nc = (n + CP_CHUNK - 1) / CP_CHUNK;
+    SSS_TRY(sss_launch(ctx, "c_psum", k_c_psum, dim3(nc), dim3(CP_T), 0, S, run_perm, n, b.csum));
+    SSS_TRY(sss_launch(ctx, "c_pscan", k_c_pscan, dim3(1), dim3(CP_T), 0, b.csum, nc));
+    SSS_TRY(sss_launch(ctx, "c_pwrite", k_c_pwrite, dim3(nc), dim3(CP_T), 0, S, run_perm, n, (const uint64_t*)b.csum,
+                       b.cpre));
+    void* pin;
+    SSS_TRY(sss_pinned(ctx, sizeof(uint64_t) * p + sizeof(uint32_t) * (2 * p + 2), &pin));
+    uint64_t* hc = static_cast<uint64_t*>(pin);
+    SSS_CUDA(cudaMemcpyAsync(hc, b.ctot, sizeof(uint64_t) * p, cudaMemcpyDeviceToHost, ctx->stream));
+    SSS_CUDA(cudaStreamSynchronize(ctx->stream));
+    uint64_t N = 0;
+    for (uint32_t i = 0; i < p; ++i) N += hc[i];
+    if (N == 0) return SSS_OK;
+    const uint64_t want = (uint64_t)p * (v + 1);
+    if (N > UINT64_MAX / want) return sss_fail(ctx, SSS_ERR_UNIMPLEMENTED, "character-based sampling: too many characters");
+    uint32_t* hso = reinterpret_cast<uint32_t*>(hc + p);
+    uint32_t* hcnt = hso + p + 1;
+    uint64_t total = 0;
+    for (uint32_t i = 0; i < p; ++i) {
+        uint64_t c = (hc[i] * want + N - 1) / N;  // ceil(C_i / w), w = N / want
+        hcnt[i] = (uint32_t)(c ? c - 1 : 0);
+        total += hcnt[i];
+    }
+    uint64_t extra = total < want ? want - total : 0;
+    uint32_t o = 0;
+    for (uint32_t i = 0; i < p; ++i) {
+        hso[i] = o;
+        o += hcnt[i];
+        if (extra > 0 && part_lo(n, p, i + 1) > part_lo(n, p, i)) {  // the first partitions' extra sample
+            ++o;
+            --extra;
+        }
+    }
+    hso[p] = o;
+    if (o > want) return sss_fail(ctx, SSS_ERR_CUDA, "character-based sampling: sample count");
+    SSS_TRY(sss_upload(ctx, b.so, hso, sizeof(uint32_t) * (p + 1)));
+    SSS_TRY(sss_upload(ctx, b.scnt, hcnt, sizeof(uint32_t) * p));
+    SSS_TRY(sss_launch(ctx, "c_csamples", k_c_csamples, dim3((o + 127) / 128), dim3(128), 0, run_perm, n, p, S,
+                       (const uint64_t*)b.cpre, (const uint32_t*)b.so, (const uint32_t*)b.scnt, N, want, b.smp,
+                       b.s_offs, b.s_lens));
+    *ns_out = o;
+    return SSS_OK;
+}
+
 static sss_status run_partition(sss_ctx* ctx, const StrIn& in, const uint32_t* trunc, const uint32_t* run_perm,
-                                uint32_t p, uint32_t v, MgBufs& b) {
+                                uint32_t p, uint32_t v, uint32_t flags, MgBufs& b) {
     const uint32_t n = in.n;
     Strs S{in.chars, in.offs, in.lens, trunc};
     uint32_t ne = 0;
     for (uint32_t i = 0; i < p; ++i) ne += part_lo(n, p, i + 1) > part_lo(n, p, i) ? 1u : 0u;
-    uint32_t ns = ne * (v + 1);
-    uint32_t tot = p * (v + 1);
-    SSS_TRY(sss_launch(ctx, "c_samples", k_c_samples, dim3((tot + 127) / 128), dim3(128), 0, run_perm, n, p, v, S,
-                       b.smp, b.s_offs, b.s_lens, b.cnt));
+    uint32_t ns = 0;
+    if ((flags & SSS_FLAG_CHAR_SAMPLING) && n > 0) SSS_TRY(char_samples(ctx, run_perm, n, p, v, S, b, &ns));
+    if (ns == 0) {
+        ns = ne * (v + 1);
+        uint32_t tot = p * (v + 1);
+        SSS_TRY(sss_launch(ctx, "c_samples", k_c_samples, dim3((tot + 127) / 128), dim3(128), 0, run_perm, n, p, v, S,
+                           b.smp, b.s_offs, b.s_lens, b.cnt));
+    }
     // sort the samples (views of the same characters, truncated) with stage A;
     // equal truncated samples keep sample order, which is input-index order
     StrIn sin{in.chars, in.n_chars, b.s_offs, b.s_lens, ns};
@@ -1053,10 +1235,10 @@ size_t need_partition(uint32_t n, uint32_t p, uint32_t v) {
 }
 
 sss_status impl_partition(sss_ctx* ctx, Arena& ar, const StrIn& in, const uint32_t* trunc, const uint32_t* run_perm,
-                          uint32_t p, uint32_t v, uint32_t* out_spl, uint32_t* out_bounds) {
+                          uint32_t p, uint32_t v, uint32_t flags, uint32_t* out_spl, uint32_t* out_bounds) {
     MgBufs b;
     carve_mg_small(ar, in.n, p, v, b);
-    SSS_TRY(run_partition(ctx, in, trunc, run_perm, p, v, b));
+    SSS_TRY(run_partition(ctx, in, trunc, run_perm, p, v, flags, b));
     if (p > 1 && out_spl)
         SSS_CUDA(cudaMemcpyAsync(out_spl, b.spl, sizeof(uint32_t) * (p - 1), cudaMemcpyDeviceToDevice, ctx->stream));
     SSS_CUDA(cudaMemcpyAsync(out_bounds, b.bounds, sizeof(uint32_t) * p * (p + 1), cudaMemcpyDeviceToDevice,
@@ -1171,7 +1353,7 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
     MgBufs b;
     carve_mg(ar, n, p, v, nrecchars, b);
     Strs S{in.chars, in.offs, in.lens, trunc};
-    SSS_TRY(run_partition(ctx, in, trunc, run_perm, p, v, b));
+    SSS_TRY(run_partition(ctx, in, trunc, run_perm, p, v, flags, b));
     const bool two_level = p <= MAX_P_TWO_LEVEL && !(flags & SSS_FLAG_MERGE_TREE);
 
     // level-1 bounds and splitters to the host

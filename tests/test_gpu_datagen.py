@@ -25,3 +25,12 @@ def test_config2_slices_identical():
         ss = datagen.config2(4194304, first, count)
         assert np.array_equal(c.cpu().numpy(), ss.chars)
         assert np.array_equal(l.cpu().numpy().view(np.uint32), ss.lens)
+
+
+def test_device_skew_set_identical():
+    import datagen.cuda as dgc
+    ss = datagen.skew_set(6, 5000)
+    c, o, l = dgc.skew_set(6, 5000)
+    assert np.array_equal(c.cpu().numpy()[:ss.N], ss.chars)
+    assert np.array_equal(o.cpu().numpy().view(np.uint64), ss.offs)
+    assert np.array_equal(l.cpu().numpy().view(np.uint32), ss.lens)

@@ -148,3 +148,104 @@ def test_pdms_config2_scaled():
     strs = ss.strings()
     want = py_sort(strs)
     assert list(res["perm"]) == want
+
+
+# --- character-based sampling (Section 3.1.2; appendix "Character Based Sampling")
+
+def skewed_strings(seed, n):
+    """Lengths spread over two orders of magnitude, so string counts and character
+    counts of a partition differ a lot."""
+    rnd = random.Random(seed)
+    out = []
+    for _ in range(n):
+        ln = rnd.choice([0, 1, 2, 3, 5, 8, 20, 60, 150])
+        out.append(bytes(rnd.choice(b"ACGT") for _ in range(ln)))
+    return out
+
+
+def _char_case(seed, n, p, v):
+    ss = datagen.from_strings(skewed_strings(seed, n))
+    run_perm, _ = oracle.local_sort(ss, p)
+    smp = oracle.samples_char(ss, run_perm, p, v)
+    return ss, run_perm, smp
+
+
+@pytest.mark.parametrize("seed,n,p,v", [(1, 60, 4, 2), (2, 200, 8, 2), (3, 97, 3, 5), (4, 40, 16, 1), (5, 7, 5, 2)])
+def test_char_sampling_count_and_density(seed, n, p, v):
+    ss, run_perm, smp = _char_case(seed, n, p, v)
+    lens = ss.lens.astype(np.int64)
+    N = int(lens.sum())
+    if N == 0:
+        return
+    assert len(smp) == p * (v + 1)  # deficits are made up by the first partitions
+    omega = N / (p * (v + 1))
+    lmax = int(lens.max())
+    sampled = set(int(s) for s in smp)
+    # sample-density lemma: a contiguous piece of a run holding k sample strings
+    # has at most (k+1)(omega + lmax) characters
+    for i in range(p):
+        lo, hi = oracle.part_lo(n, p, i), oracle.part_lo(n, p, i + 1)
+        run = [int(x) for x in run_perm[lo:hi]]
+        for a in range(len(run)):
+            chars, k = 0, 0
+            for b in range(a, len(run)):
+                chars += int(lens[run[b]])
+                k += run[b] in sampled
+                assert chars <= (k + 1) * (omega + lmax) + 1e-9, (i, a, b)
+
+
+@pytest.mark.parametrize("seed,n,p,v", [(11, 300, 4, 2), (12, 500, 8, 2), (13, 400, 8, 8), (14, 64, 16, 2)])
+def test_char_sampling_bucket_bound(seed, n, p, v):
+    """Every bucket holds at most (1 + p/v) N/p + (1 + (v+1)/p) p lmax characters
+    (appendix theorem on character-based partitioning, r = p' = p)."""
+    ss, run_perm, smp = _char_case(seed, n, p, v)
+    lens = ss.lens.astype(np.int64)
+    N, lmax = int(lens.sum()), int(lens.max())
+    _, spl = oracle.splitters(ss, smp, p)
+    bnd = oracle.bounds(ss, run_perm, p, spl).reshape(p, p + 1)
+    bound = (1 + p / v) * N / p + (1 + (v + 1) / p) * p * lmax
+    for j in range(p):
+        chars = 0
+        for i in range(p):
+            lo = oracle.part_lo(n, p, i)
+            for q in range(lo + int(bnd[i][j]), lo + int(bnd[i][j + 1])):
+                chars += int(lens[run_perm[q]])
+        assert chars <= bound + 1e-9, (j, chars, bound)
+    # and the buckets still partition the sorted order: merge == Python's sort
+    perm, lcp = oracle.merge(ss, run_perm, p, bnd.reshape(-1))
+    assert [ss.string(int(x)) for x in perm] == sorted(ss.strings())
+
+
+def test_char_sampling_positions_by_search():
+    """Each sample is the string whose characters cover floor(t N / (p (v+1)))
+    in its run's character array, found here by a prefix-sum search; the
+    partitions that make up the deficit add their last string."""
+    ss, run_perm, smp = _char_case(21, 150, 6, 3)
+    p, v, n = 6, 3, 150
+    lens = ss.lens.astype(np.int64)
+    N, want = int(lens.sum()), p * (v + 1)
+    exp, total = [], 0
+    counts = []
+    for i in range(p):
+        lo, hi = oracle.part_lo(n, p, i), oracle.part_lo(n, p, i + 1)
+        Ci = int(lens[run_perm[lo:hi]].sum())
+        counts.append(max(0, -(-Ci * want // N) - 1))
+    extra = max(0, want - sum(counts))
+    for i in range(p):
+        lo, hi = oracle.part_lo(n, p, i), oracle.part_lo(n, p, i + 1)
+        if hi == lo:
+            continue
+        ends = np.cumsum(lens[run_perm[lo:hi]])
+        for t in range(1, counts[i] + 1):
+            x = t * N // want
+            exp.append(int(run_perm[lo + int(np.searchsorted(ends, x, side="right"))]))
+        if extra:
+            exp.append(int(run_perm[hi - 1]))
+            extra -= 1
+    assert [int(s) for s in smp] == exp
+
+
+def test_char_sampling_all_empty_falls_back():
+    ss = datagen.from_strings([b""] * 20)
+    run_perm, _ = oracle.local_sort(ss, 4)
+    assert np.array_equal(oracle.samples_char(ss, run_perm, 4, 2), oracle.samples(run_perm, 20, 4, 2))
