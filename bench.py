@@ -210,7 +210,7 @@ def main():
     ap.add_argument("--breakdown", action="store_true", help="per-kernel times to stderr")
     ap.add_argument("--merge-ms", type=int, default=0, help="merge segment spacing (0 = library default)")
     ap.add_argument("--p", type=int, default=P, help="partitions (profiling of smaller cases)")
-    ap.add_argument("--workload", default="all", choices=["all", "pdms", "batch", "serve", "charsample"])
+    ap.add_argument("--workload", default="all", choices=["all", "pdms", "batch", "serve", "charsample", "suffix"])
     ap.add_argument("--batch-instances", type=int, default=4096)
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner (default knobs)")
     ap.add_argument("--per-instance-steps", type=int, default=2,
@@ -244,9 +244,9 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    if args.workload in ("batch", "serve", "charsample"):
+    if args.workload in ("batch", "serve", "charsample", "suffix"):
         ctx = sss.context(local)
-        res = {"batch": bench_batch, "charsample": bench_charsample}.get(args.workload, None)
+        res = {"batch": bench_batch, "charsample": bench_charsample, "suffix": bench_suffix}.get(args.workload, None)
         res = res(args, dev, ctx) if res else bench_serve(args, dev)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "n_gpus": ws, **res}), flush=True)
@@ -383,6 +383,8 @@ def main():
             out["batch"] = bench_batch(args, dev, ctx)
             torch.cuda.empty_cache()
             out["char_sampling"] = bench_charsample(args, dev, ctx)
+            torch.cuda.empty_cache()
+            out["suffix_sort"] = bench_suffix(args, dev, ctx)
             torch.cuda.empty_cache()
             out["serving"] = bench_serve(args, dev)
             out["p50_ms"] = out["serving"].get("p50_ms")
@@ -643,6 +645,38 @@ def bench_charsample(args, dev, ctx):
     out["outputs_identical"] = bool(torch.equal(perms["string_based"][0], perms["char_based"][0]) and
                                     torch.equal(perms["string_based"][1], perms["char_based"][1]))
     return out
+
+
+def bench_suffix(args, dev, ctx):
+    """Suffix array and LCP array of the 2^22-byte order-2 Markov text of the
+    suffix workload (64 symbols, Dirichlet(0.1) rows), all 4,194,304 suffixes
+    whole, by sss_suffix_sort (suffix views, no characters copied)."""
+    import torch
+
+    import datagen
+    import paper_2404_16517_gb300 as sss
+    text = torch.from_numpy(datagen.markov_text(3, 1 << 22)).to(dev)
+    n = text.numel()
+    sa = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def step():
+        sss.sss_suffix_sort(text, 0, None, sa, lcp, ctx=ctx)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    l64 = lcp.to(torch.int64)
+    return {"workload": "suffix_array_markov_order2_2^22_sigma64", "text_bytes": n, "ms_per_step": ms,
+            "suffixes_per_s": n / (ms / 1e3), "mean_lcp": float(l64.float().mean().item()),
+            "max_lcp": int(l64.max().item()), "steps": args.steps}
 
 
 def algorithmic_bytes(kernel: str, n: int, N: int, D: int, Dapprox: int, launches_per_step: float) -> float:

@@ -238,6 +238,26 @@ sss_status sss_sort_batch(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars,
 size_t sss_batch_workspace_bytes(uint32_t n_table, uint32_t m, const sss_params* params);
 
 /* ------------------------------------------------------------------------ */
+/* Suffix sorting as space-efficient string sorting (the extension named in the
+ * paper's Section 6, "Conclusion and Future Work": the suffixes of a text sorted
+ * as strings without materialising them).  String i is the view
+ * text[i .. i + min(n_text - i, max_len)) (max_len 0 = whole suffixes); the
+ * views take 12 bytes per suffix of work memory, the characters are never
+ * copied.  The sort is stage A (p = 1), so the work grows with the total length
+ * of the distinguishing prefixes: fine for texts with short repeats, slow for
+ * highly repetitive ones (a text of one repeated character costs n^2/2 reads).
+ * text         : DEVICE array of n_text bytes, no 0x00 byte (checked with
+ *                SSS_FLAG_CHECKED); n_text < 2^32
+ * out_sa       : uint32_t[n_text]; the suffix array (start positions in sorted
+ *                order; with max_len, equal truncated suffixes by position)
+ * out_lcp      : uint32_t[n_text]; LCP of consecutive suffixes (0 first),
+ *                truncated suffixes when max_len > 0
+ * Work memory: sss_suffix_workspace_bytes(n_text, params). */
+size_t sss_suffix_workspace_bytes(uint64_t n_text, const sss_params* params);
+sss_status sss_suffix_sort(sss_ctx* ctx, const uint8_t* text, uint64_t n_text, uint32_t max_len,
+                           const sss_params* params, uint32_t* out_sa, uint32_t* out_lcp);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free prefix doubling (stage B) for small sets.  This call has no
  * counterpart in the paper; it exists for callers that cannot allocate device
  * memory at the moment they need the result -- e.g. code running inside a host

@@ -83,6 +83,8 @@ def lib():
             "sss_set_workspace": (st, [vp, vp, C.c_size_t]),
             "sss_workspace_bytes": (C.c_size_t, [u32, u64, u32, P]),
             "sss_batch_workspace_bytes": (C.c_size_t, [u32, u32, P]),
+            "sss_suffix_workspace_bytes": (C.c_size_t, [u64, P]),
+            "sss_suffix_sort": (st, [vp, vp, u64, u32, P, vp, vp]),
             "sss_sync": (st, [vp]),
             "sss_status_string": (C.c_char_p, [st]),
             "sss_last_error": (C.c_char_p, [vp]),
@@ -112,7 +114,7 @@ def exported_symbols() -> list[str]:
             "sss_workspace_bytes", "sss_sync", "sss_status_string", "sss_last_error", "sss_local_sort",
             "sss_dist", "sss_dist_prefix", "sss_partition", "sss_lcp_merge", "sss_sort", "sss_set_timing",
             "sss_kernel_stats", "sss_reset_stats", "sss_dist_prefix_noalloc", "sss_sort_batch",
-            "sss_batch_workspace_bytes"]
+            "sss_batch_workspace_bytes", "sss_suffix_workspace_bytes", "sss_suffix_sort"]
 
 
 def params(kmin: int = 0, kmax: int = SSS_KMAX_AUTO, v: int = 2, flags: int = 0, hash_seed: int = 0,
@@ -346,6 +348,19 @@ def sss_sort_batch(chars, offs, lens, first, sizes, prm: sss_params | None = Non
 def workspace_bytes(n: int, total_len: int, p: int = 1, prm: sss_params | None = None) -> int:
     prm = prm or params()
     return int(lib().sss_workspace_bytes(n, total_len, p, C.byref(prm)))
+
+
+def sss_suffix_sort(text, max_len: int = 0, prm: sss_params | None = None, out_sa=None, out_lcp=None,
+                    ctx: Context | None = None):
+    """Suffix array and LCP array of a device uint8 text (suffix views, stage A)."""
+    if not text.is_cuda or text.dtype != torch.uint8 or not text.is_contiguous():
+        raise ValueError("text must be a contiguous CUDA uint8 tensor")
+    ctx = ctx or context(text.device.index)
+    n = text.numel()
+    sa, lcp = _out(out_sa, n, text.device), _out(out_lcp, n, text.device)
+    prm = prm or params()
+    ctx._check(lib().sss_suffix_sort(ctx.h, _ptr(text), n, max_len, C.byref(prm), _ptr(sa), _ptr(lcp)), ctx.h)
+    return sa, lcp
 
 
 def batch_workspace_bytes(n_table: int, m: int, prm: sss_params | None = None) -> int:

@@ -486,4 +486,36 @@ sss_status sss_sort_batch(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, 
     return impl_batch_finish(ctx, d_inst, m, lengths, out_perm, out_lcp, out_dist);
 }
 
+size_t sss_suffix_workspace_bytes(uint64_t n_text, const sss_params* params) {
+    if (n_text > UINT32_MAX) return 0;
+    const uint32_t n = (uint32_t)n_text;
+    Arena a;
+    a.take<uint64_t>(n);
+    a.take<uint32_t>(n);
+    return a.off + 256 + need_local_sort(n, 1, resolve_params(params));
+}
+
+sss_status sss_suffix_sort(sss_ctx* ctx, const uint8_t* text, uint64_t n_text, uint32_t max_len,
+                           const sss_params* params, uint32_t* out_sa, uint32_t* out_lcp) {
+    if (!ctx) return SSS_ERR_INVALID_ARG;
+    if (n_text > UINT32_MAX) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "text longer than 2^32 - 1 characters");
+    if (n_text == 0) return SSS_OK;
+    if (!text || !out_sa || !out_lcp) return sss_fail(ctx, SSS_ERR_INVALID_ARG, "NULL pointer");
+    cudaSetDevice(ctx->device);
+    sss_params prm = resolve_params(params);
+    const uint32_t n = (uint32_t)n_text;
+    const size_t need = sss_suffix_workspace_bytes(n_text, &prm);
+    char* ws;
+    SSS_TRY(sss_workspace(ctx, need, &ws));
+    Arena ar{ws, need, 0};
+    uint64_t* offs = ar.take<uint64_t>(n);
+    uint32_t* lens = ar.take<uint32_t>(n);
+    size_t off = (ar.off + 255) & ~size_t(255);
+    Arena sa{ws + off, need - off, 0};
+    SSS_TRY(impl_suffix_views(ctx, n, max_len ? max_len : UINT32_MAX, offs, lens));
+    StrIn in{text, n_text, offs, lens, n};
+    if (prm.flags & SSS_FLAG_CHECKED) SSS_TRY(checked_input(ctx, in));
+    return impl_local_sort(ctx, sa, in, 1, prm, out_sa, out_lcp);
+}
+
 }  // extern "C"

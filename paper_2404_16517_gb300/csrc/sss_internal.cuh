@@ -158,6 +158,7 @@ size_t need_local_sort(uint32_t n, uint32_t p, const sss_params& prm);
 // Sort every given segment of positions (each starting at depth 0) independently.
 sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const std::vector<Seg>& init,
                               const sss_params& prm, uint32_t* perm, uint32_t* lcp);
+sss_status impl_suffix_views(sss_ctx* ctx, uint32_t n, uint32_t max_len, uint64_t* offs, uint32_t* lens);
 sss_status impl_batch_finish(sss_ctx* ctx, const Seg* d_inst, uint32_t m, const uint32_t* lens, uint32_t* perm,
                              const uint32_t* lcp, uint32_t* dist);
 

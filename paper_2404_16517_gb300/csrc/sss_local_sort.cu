@@ -786,6 +786,21 @@ sss_status impl_finish_segments(sss_ctx* ctx, const Seg* tiny, uint32_t ntiny, c
 uint32_t finish_cap_tiny() { return TINY_CAP; }
 uint32_t finish_cap_med() { return MED_CAP; }
 
+// Suffix views of a text: string i is text[i .. i + min(n - i, max_len)).
+__global__ void k_suffix_views(uint32_t n, uint32_t max_len, uint64_t* __restrict__ offs,
+                               uint32_t* __restrict__ lens) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t r = n - i;
+        offs[i] = i;
+        lens[i] = r < max_len ? r : max_len;
+    }
+}
+
+sss_status impl_suffix_views(sss_ctx* ctx, uint32_t n, uint32_t max_len, uint64_t* offs, uint32_t* lens) {
+    return sss_launch(ctx, "sfx_views", k_suffix_views, dim3(std::min((n + 255) / 256, 65535u)), dim3(256), 0, n,
+                      max_len, offs, lens);
+}
+
 // Batched sorts: one CTA per instance turns table positions into
 // instance-local indices and (optionally) computes the instance's dist.
 __global__ void k_batch_finish(const Seg* __restrict__ inst, uint32_t m, const uint32_t* __restrict__ lens,

@@ -150,3 +150,17 @@ def test_truncated_compare():
     assert oracle.lcp_pair(ss, 0, 1) == 3
     assert oracle.cmp(ss, 1, 0) == 1
     assert list(oracle.sort_idx(ss, [2, 1, 0], trunc)) == [0, 1, 2]
+
+
+def test_oracle_sorts_suffix_views_like_python():
+    """Suffix views of one text (strings overlapping in the character array):
+    the oracle's order equals Python's sort of the suffixes."""
+    import random as _r
+    for seed in range(4):
+        rnd = _r.Random(seed)
+        text = bytes(rnd.choice(b"AB") for _ in range(rnd.randint(1, 200)))
+        n = len(text)
+        offs = np.arange(n, dtype=np.uint64)
+        ss = datagen.StringSet(np.frombuffer(text, np.uint8).copy(), offs, (n - offs).astype(np.uint32))
+        want = sorted(range(n), key=lambda i: text[i:])
+        assert list(oracle.sort(ss)) == want
