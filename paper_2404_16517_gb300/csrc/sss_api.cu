@@ -154,6 +154,12 @@ sss_status sss_create(sss_ctx** out, int device, void* stream) {
         delete ctx;
         return SSS_ERR_OOM;
     }
+    if (cudaMallocHost(&ctx->h_small, 64) != cudaSuccess) {
+        cudaFree(ctx->d_small);
+        cudaFree(ctx->d_err);
+        delete ctx;
+        return SSS_ERR_OOM;
+    }
     cudaEventCreateWithFlags(&ctx->pin_event, cudaEventDisableTiming);
     cudaEventRecord(ctx->pin_event, ctx->stream);
     cudaDeviceSynchronize();
@@ -171,6 +177,7 @@ sss_status sss_destroy(sss_ctx* ctx) {
     if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->d_small) cudaFree(ctx->d_small);
+    if (ctx->h_small) cudaFreeHost(ctx->h_small);
     if (ctx->pin_event) cudaEventDestroy(ctx->pin_event);
     delete ctx;
     return SSS_OK;

@@ -73,6 +73,7 @@ struct sss_ctx {
     unsigned* d_err = nullptr;
     // small device scratch for counters and reductions (never inside the workspace)
     unsigned long long* d_small = nullptr;
+    uint32_t* h_small = nullptr;  // pinned: per-round readbacks (16 words)
     std::string last_error;
     // instrumentation
     KStat stats[SSS_MAX_KERNELS];

@@ -67,6 +67,16 @@ __device__ __forceinline__ void push_seg(const SegLists& L, uint32_t start, uint
     }
 }
 
+// Dynamic work distribution: the next unit for the whole CTA (units vary a lot
+// in cost, so a static block-to-unit map leaves a long tail).
+__device__ __forceinline__ uint32_t cta_next_unit(uint32_t* counter) {
+    __shared__ uint32_t s_unit;
+    __syncthreads();
+    if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
+    __syncthreads();
+    return s_unit;
+}
+
 __global__ void k_init_perm(uint32_t* perm, uint32_t* lcp, uint32_t n) {
     uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q < n) {
@@ -78,10 +88,9 @@ __global__ void k_init_perm(uint32_t* perm, uint32_t* lcp, uint32_t n) {
 // ---------------------------------------------------------------------------
 // CTA finisher: completely sorts one segment of <= CAP strings.
 template <int THREADS, int CAP>
-__global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs, const uint8_t* __restrict__ chars,
-                                                    const uint64_t* __restrict__ offs,
-                                                    const uint32_t* __restrict__ lens, uint32_t* __restrict__ perm,
-                                                    uint32_t* __restrict__ lcp, unsigned* err) {
+__device__ __forceinline__ void finish_segment(const Seg sg, const uint8_t* __restrict__ chars,
+                                               const uint64_t* __restrict__ offs, const uint32_t* __restrict__ lens,
+                                               uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp, unsigned* err) {
     constexpr int ITEMS = CAP / THREADS;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* sHi = reinterpret_cast<uint64_t*>(smem);  // sort keys (group:16 | word>>16)
@@ -95,7 +104,6 @@ __global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs
     uint32_t* sC = sA + CAP;                             // compacted active positions
     __shared__ uint32_t sh_warp[32];
 
-    const Seg sg = segs[blockIdx.x];
     const uint32_t m = sg.size;
     const int tid = threadIdx.x;
     for (uint32_t i = tid; i < m; i += THREADS) {
@@ -213,6 +221,19 @@ __global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs
     for (uint32_t i = tid; i < m; i += THREADS) perm[sg.start + i] = sV[i];
 }
 
+// Segments segs[0 .. count) (count from the device when d_count is given,
+// clamped to count), one CTA at a time.
+template <int THREADS, int CAP>
+__global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs, const uint32_t* __restrict__ d_count,
+                                                    uint32_t count, uint32_t* work, const uint8_t* __restrict__ chars,
+                                                    const uint64_t* __restrict__ offs,
+                                                    const uint32_t* __restrict__ lens, uint32_t* __restrict__ perm,
+                                                    uint32_t* __restrict__ lcp, unsigned* err) {
+    const uint32_t nseg = d_count ? min(*d_count, count) : count;
+    for (uint32_t i = cta_next_unit(work); i < nseg; i = cta_next_unit(work))
+        finish_segment<THREADS, CAP>(segs[i], chars, offs, lens, perm, lcp, err);
+}
+
 // Warp finisher: one warp completely sorts one segment of <= 32 strings, lane i
 // holding position i.  Same rounds as the CTA finisher (reference-split key of
 // every unfinished member against its group's first member, sort by (group,
@@ -227,17 +248,12 @@ __device__ __forceinline__ void warp_cas128(uint64_t& hi, uint64_t& lo, uint32_t
     }
 }
 
-__global__ void __launch_bounds__(32 * WF_WARPS) k_finish_warp(const Seg* __restrict__ segs, uint32_t nseg,
-                                                               const uint8_t* __restrict__ chars,
-                                                               const uint64_t* __restrict__ offs,
-                                                               const uint32_t* __restrict__ lens,
-                                                               uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
-                                                               unsigned* err) {
+__device__ __forceinline__ void finish_warp_segment(const Seg sg, const uint8_t* __restrict__ chars,
+                                                    const uint64_t* __restrict__ offs,
+                                                    const uint32_t* __restrict__ lens, uint32_t* __restrict__ perm,
+                                                    uint32_t* __restrict__ lcp, unsigned* err) {
     constexpr uint64_t DONE_BIT = 1ull << 47;  // in the low word, above the 32-bit index
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t sidx = blockIdx.x * WF_WARPS + (threadIdx.x >> 5);
-    if (sidx >= nseg) return;  // uniform per warp
-    const Seg sg = segs[sidx];
     const uint32_t m = sg.size <= 32u ? sg.size : 32u;
     const bool live = lane < m;
     const uint32_t span = m <= 2u ? 2u : (1u << (32 - __clz((int)(m - 1))));
@@ -327,6 +343,26 @@ __global__ void __launch_bounds__(32 * WF_WARPS) k_finish_warp(const Seg* __rest
     if (live) perm[sg.start + lane] = e;
 }
 
+// segs[0 .. count) (count from the device when d_count is given, clamped to
+// count), one warp per segment
+__global__ void __launch_bounds__(32 * WF_WARPS) k_finish_warp(const Seg* __restrict__ segs,
+                                                               const uint32_t* __restrict__ d_count, uint32_t count,
+                                                               uint32_t* work, const uint8_t* __restrict__ chars,
+                                                               const uint64_t* __restrict__ offs,
+                                                               const uint32_t* __restrict__ lens,
+                                                               uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
+                                                               unsigned* err) {
+    const uint32_t nseg = d_count ? min(*d_count, count) : count;
+    const uint32_t lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t i = 0;
+        if (lane == 0) i = atomicAdd(work, 1u);
+        i = __shfl_sync(SSS_FULL, i, 0);
+        if (i >= nseg) break;
+        finish_warp_segment(segs[i], chars, offs, lens, perm, lcp, err);
+    }
+}
+
 constexpr size_t finish_smem(int cap) { return (size_t)cap * (8 + 8 + 4 * 7); }
 
 // ---------------------------------------------------------------------------
@@ -338,13 +374,12 @@ __device__ __noinline__ uint32_t lcp_full_w_outline(const uint8_t* a, uint32_t l
     return lcp_full_w(a, la, b, lb, d, w);
 }
 
-__global__ void __launch_bounds__(LG_T, 6) k_lg_ext(const LgTile* __restrict__ tiles, const LgSegInfo* __restrict__ info,
-                                                 const uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
-                                                 const uint32_t* __restrict__ lens, const uint32_t* __restrict__ perm,
-                                                 uint64_t* __restrict__ K, uint32_t* __restrict__ segfmt) {
+__device__ __forceinline__ void lg_ext_tile(const LgTile tl, const LgSegInfo* __restrict__ info,
+                                            const uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
+                                            const uint32_t* __restrict__ lens, const uint32_t* __restrict__ perm,
+                                            uint64_t* __restrict__ K, uint32_t* __restrict__ segfmt) {
     constexpr uint32_t NREF = 68;  // 64 words (512 chars) plus a 4-word block of slack
     __shared__ uint64_t refw[NREF];
-    LgTile tl = tiles[blockIdx.x];
     LgSegInfo si = info[tl.s];
     const uint32_t d = si.seg.depth;
     uint32_t r = perm[si.seg.start];
@@ -371,6 +406,18 @@ __global__ void __launch_bounds__(LG_T, 6) k_lg_ext(const LgTile* __restrict__ t
         uint32_t rho = (v >> 3) < NREF ? (uint32_t)(refw[v >> 3] >> (56 - 8 * (v & 7))) & 0xFFu
                                        : (uint32_t)(load_word_be(rs, rl, d + v) >> 56);
         K[q] = ref_key(v, w, rho, f);
+    }
+}
+
+__global__ void __launch_bounds__(LG_T, 6) k_lg_ext(const LsPlan* __restrict__ plan, const LgTile* __restrict__ tiles,
+                                                 const LgSegInfo* __restrict__ info,
+                                                 const uint8_t* __restrict__ chars, const uint64_t* __restrict__ offs,
+                                                 const uint32_t* __restrict__ lens, const uint32_t* __restrict__ perm,
+                                                 uint64_t* __restrict__ K, uint32_t* __restrict__ segfmt) {
+    const uint32_t nt = plan->ntiles;
+    for (uint32_t g = blockIdx.x; g < nt; g += gridDim.x) {
+        __syncthreads();
+        lg_ext_tile(tiles[g], info, chars, offs, lens, perm, K, segfmt);
     }
 }
 
@@ -429,18 +476,16 @@ __device__ void sort_emit(unsigned char* smem, uint32_t bs, uint32_t m, uint32_t
 
 // One CTA per (segment, bucket).  Range buckets are sorted in shared memory;
 // groups of equal keys become new segments at depth d + v + C.
-__global__ void __launch_bounds__(BK_T) k_lg_buckets(const LgSegInfo* __restrict__ info,
-                                                     const uint32_t* __restrict__ bst,
-                                                     const uint32_t* __restrict__ segfmt,
-                                                     const uint64_t* __restrict__ tK, const uint32_t* __restrict__ tV,
-                                                     const uint32_t* __restrict__ lens, uint64_t* __restrict__ K,
-                                                     uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
-                                                     SegLists L, unsigned* err, uint32_t ns,
-                                                     uint8_t* __restrict__ fixmark) {
+__device__ __forceinline__ void lg_bucket(uint32_t g, uint32_t ns, const LgSegInfo* __restrict__ info,
+                                          const uint32_t* __restrict__ bst, const uint32_t* __restrict__ segfmt,
+                                          const uint64_t* __restrict__ tK, const uint32_t* __restrict__ tV,
+                                          const uint32_t* __restrict__ lens, uint64_t* __restrict__ K,
+                                          uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp, const SegLists& L,
+                                          unsigned* err, uint8_t* __restrict__ fixmark) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const uint32_t sidx = segment_of_bucket(info, ns, blockIdx.x);
+    const uint32_t sidx = segment_of_bucket(info, ns, g);
     LgSegInfo si = info[sidx];
-    uint32_t b = blockIdx.x - si.bk_base;
+    uint32_t b = g - si.bk_base;
     uint32_t nbk = 2 * si.nb - 1;
     if (b >= nbk) return;
     uint32_t bs = bst[si.bst_base + b], be = bst[si.bst_base + b + 1];
@@ -480,33 +525,52 @@ __global__ void __launch_bounds__(BK_T) k_lg_buckets(const LgSegInfo* __restrict
     sort_emit<BK_T, BK_CAP>(smem, bs, m, d, f, tK, tV, lens, K, perm, lcp, L, err);
 }
 
+__global__ void __launch_bounds__(BK_T) k_lg_buckets(const LsPlan* __restrict__ plan,
+                                                     const LgSegInfo* __restrict__ info,
+                                                     const uint32_t* __restrict__ bst,
+                                                     const uint32_t* __restrict__ segfmt,
+                                                     const uint64_t* __restrict__ tK, const uint32_t* __restrict__ tV,
+                                                     const uint32_t* __restrict__ lens, uint64_t* __restrict__ K,
+                                                     uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
+                                                     SegLists L, unsigned* err, uint8_t* __restrict__ fixmark,
+                                                     uint32_t* work) {
+    const uint32_t nb = plan->pbuckets, npart = plan->npart;
+    for (uint32_t g = cta_next_unit(work); g < nb; g = cta_next_unit(work))
+        lg_bucket(g, npart, info, bst, segfmt, tK, tV, lens, K, perm, lcp, L, err, fixmark);
+}
+
 // Large segments of at most DIRECT_CAP strings: one CTA sorts the whole segment
 // by its keys (no sampling, classification or scatter).
-__global__ void __launch_bounds__(DIRECT_T) k_lg_direct(const LgSegInfo* __restrict__ info, uint32_t first,
+__global__ void __launch_bounds__(DIRECT_T) k_lg_direct(const LsPlan* __restrict__ plan,
+                                                        const LgSegInfo* __restrict__ info,
                                                         const uint32_t* __restrict__ segfmt,
                                                         const uint32_t* __restrict__ lens, uint64_t* __restrict__ K,
                                                         uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
-                                                        SegLists L, unsigned* err) {
+                                                        SegLists L, unsigned* err, uint32_t* work) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const uint32_t sidx = first + blockIdx.x;
-    const LgSegInfo si = info[sidx];
-    const uint32_t d = si.seg.depth;
-    sort_emit<DIRECT_T, DIRECT_CAP>(smem, si.seg.start, si.seg.size, d, segfmt[sidx], K, perm, lens, K, perm, lcp,
-                                    L, err);
+    const uint32_t ns = plan->ns, npart = plan->npart;
+    for (uint32_t sidx = npart + cta_next_unit(work); sidx < ns; sidx = npart + cta_next_unit(work)) {
+        const LgSegInfo si = info[sidx];
+        sort_emit<DIRECT_T, DIRECT_CAP>(smem, si.seg.start, si.seg.size, si.seg.depth, segfmt[sidx], K, perm, lens, K,
+                                        perm, lcp, L, err);
+    }
 }
 
 // LCP at the first position of every non-first, non-empty bucket.
-__global__ void __launch_bounds__(512) k_lg_seams(const LgSegInfo* __restrict__ info, const uint32_t* __restrict__ bst,
-                                                  const uint32_t* __restrict__ segfmt, const uint64_t* __restrict__ K,
-                                                  uint32_t* __restrict__ lcp) {
-    LgSegInfo si = info[blockIdx.x];
-    uint32_t nbk = 2 * si.nb - 1;
-    uint32_t d = si.seg.depth;
-    const uint32_t f = segfmt[blockIdx.x];
-    for (uint32_t b = threadIdx.x; b < nbk; b += 512) {
-        uint32_t bs = bst[si.bst_base + b], be = bst[si.bst_base + b + 1];
-        if (be > bs && bs > si.seg.start && be <= si.seg.start + si.seg.size)
-            lcp[bs] = d + key_lcp(K[bs - 1], K[bs], f);
+__global__ void __launch_bounds__(512) k_lg_seams(const LsPlan* __restrict__ plan, const LgSegInfo* __restrict__ info,
+                                                  const uint32_t* __restrict__ bst, const uint32_t* __restrict__ segfmt,
+                                                  const uint64_t* __restrict__ K, uint32_t* __restrict__ lcp) {
+    const uint32_t npart = plan->npart;
+    for (uint32_t s = blockIdx.x; s < npart; s += gridDim.x) {
+        LgSegInfo si = info[s];
+        uint32_t nbk = 2 * si.nb - 1;
+        uint32_t d = si.seg.depth;
+        const uint32_t f = segfmt[s];
+        for (uint32_t b = threadIdx.x; b < nbk; b += 512) {
+            uint32_t bs = bst[si.bst_base + b], be = bst[si.bst_base + b + 1];
+            if (be > bs && bs > si.seg.start && be <= si.seg.start + si.seg.size)
+                lcp[bs] = d + key_lcp(K[bs - 1], K[bs], f);
+        }
     }
 }
 
@@ -575,6 +639,7 @@ struct LsBufs {
     Seg* med;
     Seg* large;
     uint32_t* cnt;
+    uint32_t* work;  // dynamic work counters: [0] warp, [1] tiny, [2] med, [3] buckets, [4] direct
     uint32_t* segfmt;
     uint8_t* fixmark;
     SpBufs sp;
@@ -610,22 +675,39 @@ void carve_ls(Arena& ar, uint32_t n, uint32_t p, const sss_params& prm, LsBufs& 
     b.med = ar.take<Seg>(b.cap_med);
     b.large = ar.take<Seg>(b.cap_large);
     b.cnt = ar.take<uint32_t>(4);
+    b.work = ar.take<uint32_t>(8);
     b.segfmt = ar.take<uint32_t>(b.cap_large);
     b.fixmark = ar.take<uint8_t>(n);
     carve_sp(ar, n, b.cap_large, b.sp);
 }
 
-sss_status run_finishers(sss_ctx* ctx, const LsBufs& B, uint32_t nwarp, uint32_t ntiny, uint32_t nmed,
-                         const StrIn& in, uint32_t* perm, uint32_t* lcp) {
-    SSS_TRY(sss_launch(ctx, "ls_finish_warp", k_finish_warp, dim3((nwarp + WF_WARPS - 1) / WF_WARPS),
-                       dim3(32 * WF_WARPS), 0, (const Seg*)B.warp, nwarp, in.chars, in.offs, in.lens, perm, lcp,
-                       ctx->d_err));
-    SSS_TRY(sss_launch(ctx, "ls_finish_tiny", k_finish<TINY_T, TINY_CAP>, dim3(ntiny), dim3(TINY_T),
-                       finish_smem(TINY_CAP), (const Seg*)B.tiny, in.chars, in.offs, in.lens, perm, lcp,
-                       ctx->d_err));
-    SSS_TRY(sss_launch(ctx, "ls_finish_cta", k_finish<MED_T, MED_CAP>, dim3(nmed), dim3(MED_T),
-                       finish_smem(MED_CAP), (const Seg*)B.med, in.chars, in.offs, in.lens, perm, lcp,
-                       ctx->d_err));
+// The three finishers over their lists: host counts, or (d_cnt != NULL) the
+// device counters of the round that just ran (d_cnt[3] warp, [0] tiny, [1] med).
+sss_status run_finishers(sss_ctx* ctx, const LsBufs& B, const uint32_t* d_cnt, uint32_t nwarp, uint32_t ntiny,
+                         uint32_t nmed, const StrIn& in, uint32_t* perm, uint32_t* lcp) {
+    const uint32_t sm = (uint32_t)std::max(1, ctx->sm_count);
+    uint32_t gw, gt, gm;
+    if (d_cnt) {
+        nwarp = B.cap_warp;
+        ntiny = B.cap_tiny;
+        nmed = B.cap_med;
+        gw = sm * 8;
+        gt = sm * 16;
+        gm = sm * 2;
+    } else {
+        gw = std::min((nwarp + WF_WARPS - 1) / WF_WARPS, sm * 16);
+        gt = std::min(ntiny, sm * 32);
+        gm = std::min(nmed, sm * 4);
+    }
+    SSS_TRY(sss_launch(ctx, "ls_finish_warp", k_finish_warp, dim3(gw), dim3(32 * WF_WARPS), 0, (const Seg*)B.warp,
+                       d_cnt ? d_cnt + 3 : (const uint32_t*)nullptr, nwarp, B.work + 0, in.chars, in.offs, in.lens,
+                       perm, lcp, ctx->d_err));
+    SSS_TRY(sss_launch(ctx, "ls_finish_tiny", k_finish<TINY_T, TINY_CAP>, dim3(gt), dim3(TINY_T),
+                       finish_smem(TINY_CAP), (const Seg*)B.tiny, d_cnt ? d_cnt + 0 : (const uint32_t*)nullptr, ntiny,
+                       B.work + 1, in.chars, in.offs, in.lens, perm, lcp, ctx->d_err));
+    SSS_TRY(sss_launch(ctx, "ls_finish_cta", k_finish<MED_T, MED_CAP>, dim3(gm), dim3(MED_T), finish_smem(MED_CAP),
+                       (const Seg*)B.med, d_cnt ? d_cnt + 1 : (const uint32_t*)nullptr, nmed, B.work + 2, in.chars,
+                       in.offs, in.lens, perm, lcp, ctx->d_err));
     return SSS_OK;
 }
 
@@ -665,6 +747,35 @@ sss_status impl_local_sort(sss_ctx* ctx, Arena& ar, const StrIn& in, uint32_t p,
     return impl_sort_segments(ctx, ar, in, init, prm, perm, lcp);
 }
 
+// One round of the multi-CTA path, planned on the device from the segments the
+// previous round pushed: keys, partition of the large segments, bucket sorts,
+// seams, whole-segment sorts, then the finishers of every segment pushed.
+static sss_status launch_round(sss_ctx* ctx, const LsBufs& B, const LsKnobs& kn, const SegLists& L,
+                               const StrIn& in, uint32_t* perm, uint32_t* lcp) {
+    const uint32_t sm = (uint32_t)std::max(1, ctx->sm_count);
+    SSS_TRY(sss_launch(ctx, "ls_lg_plan", k_lg_plan, dim3(1), dim3(1024), 0, (const Seg*)B.large, B.cnt, B.work,
+                       kn.direct_cap, kn.bucket_target, B.sp.cap_segs, B.sp.cap_tiles, B.sp.cap_hist, B.sp.info,
+                       B.sp.plan, ctx->d_err));
+    SSS_TRY(sss_launch(ctx, "ls_lg_tiles", k_lg_tiles, dim3(sm * 4), dim3(256), 0, (const LsPlan*)B.sp.plan,
+                       (const LgSegInfo*)B.sp.info, B.sp.tiles));
+    SSS_TRY(sss_launch(ctx, "ls_lg_ext", k_lg_ext, dim3(sm * 6), dim3(LG_T), 0, (const LsPlan*)B.sp.plan,
+                       (const LgTile*)B.sp.tiles, (const LgSegInfo*)B.sp.info, in.chars, in.offs, in.lens,
+                       (const uint32_t*)perm, B.K, B.segfmt));
+    SSS_TRY(launch_sp(ctx, B.sp, B.K, perm, B.tK, B.tV, "ls_lg_samples", "ls_lg_classify", "ls_lg_offsets",
+                      "ls_lg_scatter"));
+    SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets, dim3(sm * 2), dim3(BK_T), (size_t)BK_CAP * (8 + 8 + 4 + 4),
+                       (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst,
+                       (const uint32_t*)B.segfmt, (const uint64_t*)B.tK, (const uint32_t*)B.tV, in.lens, B.K, perm, lcp,
+                       L, ctx->d_err, B.fixmark, B.work + 3));
+    SSS_TRY(sss_launch(ctx, "ls_lg_seams", k_lg_seams, dim3(sm * 2), dim3(512), 0, (const LsPlan*)B.sp.plan,
+                       (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt,
+                       (const uint64_t*)B.K, lcp));
+    SSS_TRY(sss_launch(ctx, "ls_lg_direct", k_lg_direct, dim3(sm), dim3(DIRECT_T), (size_t)DIRECT_CAP * (8 + 8 + 4 + 4),
+                       (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info, (const uint32_t*)B.segfmt, in.lens, B.K,
+                       perm, lcp, L, ctx->d_err, B.work + 4));
+    return run_finishers(ctx, B, B.cnt, 0, 0, 0, in, perm, lcp);
+}
+
 sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const std::vector<Seg>& init,
                               const sss_params& prm, uint32_t* perm, uint32_t* lcp) {
     const uint32_t n = in.n;
@@ -672,10 +783,9 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
     LsBufs B;
     carve_ls(ar, n, 1, prm, B);
     const LsKnobs kn = ls_knobs(prm);
-    const uint32_t warp_max = kn.warp_cap, med_max = kn.cta_cap, direct_max = kn.direct_cap;
+    const uint32_t warp_max = kn.warp_cap, med_max = kn.cta_cap;
     SSS_TRY(set_ls_attributes(ctx));
     SSS_TRY(sss_launch(ctx, "ls_init", k_init_perm, dim3((n + 255) / 256), dim3(256), 0, perm, lcp, n));
-    bool any_partition = false;
 
     // initial segments (partitions or instances), by size class
     std::vector<Seg> warp, tiny, med, large;
@@ -686,100 +796,61 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
         else if (s.size <= med_max) med.push_back(s);
         else large.push_back(s);
     }
-    // pinned staging: segment info + tiles + counters
-    const size_t nseg_stage = (size_t)B.cap_large + B.cap_med + B.cap_tiny + B.cap_warp;
-    size_t pin_bytes = sizeof(uint32_t) * 16 + sizeof(Seg) * nseg_stage +
-                       sizeof(LgSegInfo) * B.cap_large + sizeof(LgTile) * B.sp.cap_tiles + 1024;
+    if (large.size() > B.cap_large) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: internal capacity exceeded");
+    // pinned staging: counters, then the initial lists
     void* pin;
-    SSS_TRY(sss_pinned(ctx, pin_bytes, &pin));
+    SSS_TRY(sss_pinned(ctx, 64 + sizeof(Seg) * (init.size() + 4), &pin));
     uint32_t* h_cnt = reinterpret_cast<uint32_t*>(pin);
-    Seg* h_seg = reinterpret_cast<Seg*>(reinterpret_cast<char*>(pin) + 64);
-    LgSegInfo* h_info = reinterpret_cast<LgSegInfo*>(h_seg + nseg_stage);
-    LgTile* h_tiles = reinterpret_cast<LgTile*>(h_info + B.cap_large);
+    Seg* hw = reinterpret_cast<Seg*>(reinterpret_cast<char*>(pin) + 64);
+    Seg* ht = hw + warp.size();
+    Seg* hm = ht + tiny.size();
+    Seg* hl = hm + med.size();
+    std::copy(warp.begin(), warp.end(), hw);
+    std::copy(tiny.begin(), tiny.end(), ht);
+    std::copy(med.begin(), med.end(), hm);
+    std::copy(large.begin(), large.end(), hl);
+    h_cnt[0] = h_cnt[1] = h_cnt[3] = 0;
+    h_cnt[2] = (uint32_t)large.size();
+    SSS_TRY(sss_upload(ctx, B.warp, hw, sizeof(Seg) * warp.size()));
+    SSS_TRY(sss_upload(ctx, B.tiny, ht, sizeof(Seg) * tiny.size()));
+    SSS_TRY(sss_upload(ctx, B.med, hm, sizeof(Seg) * med.size()));
+    SSS_TRY(sss_upload(ctx, B.large, hl, sizeof(Seg) * large.size()));
+    SSS_TRY(sss_upload(ctx, B.cnt, h_cnt, sizeof(uint32_t) * 4));
+    SSS_CUDA(cudaMemsetAsync(B.work, 0, sizeof(uint32_t) * 8, ctx->stream));
+    SSS_TRY(run_finishers(ctx, B, nullptr, (uint32_t)warp.size(), (uint32_t)tiny.size(), (uint32_t)med.size(), in,
+                          perm, lcp));
+    if (large.empty()) return SSS_OK;
 
-    if (!warp.empty() || !tiny.empty() || !med.empty()) {
-        Seg* hw = h_seg;
-        Seg* ht = hw + warp.size();
-        Seg* hm = ht + tiny.size();
-        std::copy(warp.begin(), warp.end(), hw);
-        std::copy(tiny.begin(), tiny.end(), ht);
-        std::copy(med.begin(), med.end(), hm);
-        SSS_TRY(sss_upload(ctx, B.warp, hw, sizeof(Seg) * warp.size()));
-        SSS_TRY(sss_upload(ctx, B.tiny, ht, sizeof(Seg) * tiny.size()));
-        SSS_TRY(sss_upload(ctx, B.med, hm, sizeof(Seg) * med.size()));
-        SSS_TRY(run_finishers(ctx, B, (uint32_t)warp.size(), (uint32_t)tiny.size(), (uint32_t)med.size(), in, perm,
-                              lcp));
-        // staging is reused below: wait for the uploads
-        SSS_CUDA(cudaStreamSynchronize(ctx->stream));
-    }
-
+    SSS_CUDA(cudaMemsetAsync(B.fixmark, 0, n, ctx->stream));
     SegLists L{B.tiny, B.med, B.large, B.cnt, B.cap_tiny, B.cap_med, B.cap_large, B.warp, B.cap_warp, warp_max, med_max};
-    uint32_t rounds = 0;
-    while (!large.empty()) {
-        if (++rounds > 100000u) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: round limit exceeded");
-        // segments that need the sampled partition first, whole-segment sorts after
-        std::stable_partition(large.begin(), large.end(),
-                              [direct_max](const Seg& g) { return g.size > direct_max; });
-        uint32_t ns = (uint32_t)large.size();
-        uint32_t npart = 0;
-        while (npart < ns && large[npart].size > direct_max) ++npart;
-        uint32_t ntiles = 0, nbuckets = 0;
-        if (!plan_sp(large, kn.bucket_target, B.sp, h_info, h_tiles, &ntiles, &nbuckets))
-            return sss_fail(ctx, SSS_ERR_CUDA, "local sort: internal capacity exceeded");
-        const uint32_t ptiles = npart < ns ? h_info[npart].tile0 : ntiles;
-        const uint32_t pbuckets = npart < ns ? h_info[npart].bk_base : nbuckets;
-        SSS_TRY(sss_upload(ctx, B.sp.info, h_info, sizeof(LgSegInfo) * ns));
-        SSS_TRY(sss_upload(ctx, B.sp.tiles, h_tiles, sizeof(LgTile) * ntiles));
-        SSS_CUDA(cudaMemsetAsync(B.cnt, 0, sizeof(uint32_t) * 4, ctx->stream));
-        SSS_TRY(sss_launch(ctx, "ls_lg_ext", k_lg_ext, dim3(ntiles), dim3(LG_T), 0, (const LgTile*)B.sp.tiles,
-                           (const LgSegInfo*)B.sp.info, in.chars, in.offs, in.lens, (const uint32_t*)perm, B.K,
-                           B.segfmt));
-        if (npart > 0) {
-            if (!any_partition) SSS_CUDA(cudaMemsetAsync(B.fixmark, 0, n, ctx->stream));
-            any_partition = true;
-            SSS_TRY(launch_sp(ctx, B.sp, npart, ptiles, B.K, perm, B.tK, B.tV, "ls_lg_samples", "ls_lg_classify",
-                              "ls_lg_offsets", "ls_lg_scatter"));
-            SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets, dim3(pbuckets), dim3(BK_T),
-                               (size_t)BK_CAP * (8 + 8 + 4 + 4), (const LgSegInfo*)B.sp.info,
-                               (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt, (const uint64_t*)B.tK,
-                               (const uint32_t*)B.tV, in.lens, B.K, perm, lcp, L, ctx->d_err, npart, B.fixmark));
-            SSS_TRY(sss_launch(ctx, "ls_lg_seams", k_lg_seams, dim3(npart), dim3(512), 0,
-                               (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt,
-                               (const uint64_t*)B.K, lcp));
-        }
-        SSS_TRY(sss_launch(ctx, "ls_lg_direct", k_lg_direct, dim3(ns - npart), dim3(DIRECT_T),
-                           (size_t)DIRECT_CAP * (8 + 8 + 4 + 4), (const LgSegInfo*)B.sp.info, npart,
-                           (const uint32_t*)B.segfmt, in.lens, B.K, perm, lcp, L, ctx->d_err));
-        SSS_CUDA(cudaMemcpyAsync(h_cnt, B.cnt, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost, ctx->stream));
-        SSS_CUDA(cudaMemcpyAsync(h_cnt + 4, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    uint32_t* h_next = reinterpret_cast<uint32_t*>(ctx->h_small);
+    for (uint32_t rounds = 1;; ++rounds) {
+        if (rounds > 100000u) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: round limit exceeded");
+        SSS_TRY(launch_round(ctx, B, kn, L, in, perm, lcp));
+        // segments pushed for the next round, and the sticky error word
+        SSS_CUDA(cudaMemcpyAsync(h_next, B.cnt + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+        SSS_CUDA(cudaMemcpyAsync(h_next + 1, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
         SSS_CUDA(cudaStreamSynchronize(ctx->stream));
-        if (h_cnt[4] & ERRBIT_OVERFLOW) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: device capacity check failed");
-        uint32_t ct = std::min(h_cnt[0], B.cap_tiny), cm = std::min(h_cnt[1], B.cap_med),
-                 cl = std::min(h_cnt[2], B.cap_large), cw = std::min(h_cnt[3], B.cap_warp);
-        SSS_TRY(run_finishers(ctx, B, cw, ct, cm, in, perm, lcp));
-        large.clear();
-        if (cl > 0) {
-            SSS_CUDA(cudaMemcpyAsync(h_seg, B.large, sizeof(Seg) * cl, cudaMemcpyDeviceToHost, ctx->stream));
-            SSS_CUDA(cudaStreamSynchronize(ctx->stream));
-            large.assign(h_seg, h_seg + cl);
-        } else {
-            // the finishers read the lists before the next round resets the counters
-            SSS_CUDA(cudaStreamSynchronize(ctx->stream));
-        }
+        if (h_next[1] & ERRBIT_OVERFLOW) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: device capacity check failed");
+        if (h_next[0] == 0) break;
     }
-    if (any_partition)
-        SSS_TRY(sss_launch(ctx, "ls_fix_seams", k_fix_seams, dim3(std::min((n + 255) / 256, 4096u)), dim3(256), 0,
-                           (const uint8_t*)B.fixmark, n, in.chars, in.offs, in.lens, (const uint32_t*)perm, lcp));
+    SSS_TRY(sss_launch(ctx, "ls_fix_seams", k_fix_seams, dim3(std::min((n + 255) / 256, 4096u)), dim3(256), 0,
+                       (const uint8_t*)B.fixmark, n, in.chars, in.offs, in.lens, (const uint32_t*)perm, lcp));
     return SSS_OK;
 }
 
 sss_status impl_finish_segments(sss_ctx* ctx, const Seg* tiny, uint32_t ntiny, const Seg* med, uint32_t nmed,
                                 const StrIn& in, uint32_t* perm, uint32_t* lcp) {
     SSS_TRY(set_ls_attributes(ctx));
-    SSS_TRY(sss_launch(ctx, "ls_finish_tiny", k_finish<TINY_T, TINY_CAP>, dim3(ntiny), dim3(TINY_T),
-                       finish_smem(TINY_CAP), tiny, in.chars, in.offs, in.lens, perm, lcp, ctx->d_err));
-    SSS_TRY(sss_launch(ctx, "ls_finish_cta", k_finish<MED_T, MED_CAP>, dim3(nmed), dim3(MED_T),
-                       finish_smem(MED_CAP), med, in.chars, in.offs, in.lens, perm, lcp, ctx->d_err));
+    const uint32_t sm = (uint32_t)std::max(1, ctx->sm_count);
+    uint32_t* work = reinterpret_cast<uint32_t*>(ctx->d_err) + 2;  // two spare words of the context
+    SSS_CUDA(cudaMemsetAsync(work, 0, sizeof(uint32_t) * 2, ctx->stream));
+    SSS_TRY(sss_launch(ctx, "ls_finish_tiny", k_finish<TINY_T, TINY_CAP>, dim3(std::min(ntiny, sm * 32)), dim3(TINY_T),
+                       finish_smem(TINY_CAP), tiny, (const uint32_t*)nullptr, ntiny, work, in.chars, in.offs, in.lens,
+                       perm, lcp, ctx->d_err));
+    SSS_TRY(sss_launch(ctx, "ls_finish_cta", k_finish<MED_T, MED_CAP>, dim3(std::min(nmed, sm * 4)), dim3(MED_T),
+                       finish_smem(MED_CAP), med, (const uint32_t*)nullptr, nmed, work + 1, in.chars, in.offs, in.lens,
+                       perm, lcp, ctx->d_err));
     return SSS_OK;
 }
 
