@@ -213,6 +213,7 @@ def main():
     ap.add_argument("--workload", default="all", choices=["all", "pdms", "batch", "serve", "charsample", "suffix"])
     ap.add_argument("--batch-instances", type=int, default=4096)
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner (default knobs)")
+    ap.add_argument("--no-graph", action="store_true", help="batch: host-driven round loop only")
     ap.add_argument("--per-instance-steps", type=int, default=2,
                     help="timed passes of one sss_sort call per instance (0: skip that comparison)")
     ap.add_argument("--serve-requests", type=int, default=20000)
@@ -462,6 +463,21 @@ def bench_batch(args, dev, ctx):
                   "ms_default_knobs": ms_default, "ms_tuned_knobs": ms_tuned,
                   "fastest_on_sample_ms": table[0][0], "slowest_on_sample_ms": table[-1][0]}
 
+    # the round loop as one CUDA graph launch, against the host-driven loop
+    graph = None
+    if not args.no_graph:
+        prm_g = sss.params(flags=prm.flags | sss.SSS_FLAG_GRAPH, cta_cap=prm.cta_cap, direct_cap=prm.direct_cap,
+                           bucket_target=prm.bucket_target, warp_cap=prm.warp_cap)
+        ms_host = timed(prm, max(1, args.steps // 2))
+        ms_graph = timed(prm_g, max(1, args.steps // 2))
+        graph = {"ms_host_loop": ms_host, "ms_graph": ms_graph, "used": ms_graph < ms_host}
+        p_host = perm.clone()
+        run(prm_g)
+        torch.cuda.synchronize()
+        graph["outputs_identical"] = bool(torch.equal(p_host, perm))
+        if ms_graph < ms_host:
+            prm = prm_g
+
     def step():
         run(prm)
 
@@ -493,7 +509,7 @@ def bench_batch(args, dev, ctx):
     algo = D + 20 * n
     return {"workload": f"batch_{m}_instances_2^6..2^16_len8..300_ACGT", "instances": m, "strings": n, "chars": N,
             "D_over_N": D / N, "ms_per_step": ms, "chars_per_s": N / (ms / 1e3), "strings_per_s": n / (ms / 1e3),
-            "gpu_launches_per_step": launches, "tuning": tuning,
+            "gpu_launches_per_step": launches, "tuning": tuning, "graph": graph,
             "per_instance_calls": per,
             "speedup_vs_per_instance": (per["ms_per_step"] / ms) if per else None,
             "outputs_identical": per["outputs_identical"] if per else None,

@@ -63,6 +63,11 @@ typedef enum sss_status {
 #define SSS_FLAG_MERGE_TREE 0x10u /* merge: pairwise LCP-merge tree over whole
                                   buckets instead of second-level sub-buckets
                                   merged inside one CTA each */
+#define SSS_FLAG_GRAPH 0x40u /* local sort: run its round loop as one CUDA graph
+                                  launch (a conditional while node whose body is a
+                                  device-planned round); the graph is kept in the
+                                  context and relaunched while the call's pointers
+                                  and sizes are unchanged */
 #define SSS_FLAG_CHAR_SAMPLING 0x20u /* partition: character-based regular sampling
                                   (Section 3.1.2): about p(v+1) samples at equally
                                   spaced character positions of the runs (truncated

@@ -178,6 +178,9 @@ sss_status sss_destroy(sss_ctx* ctx) {
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->d_small) cudaFree(ctx->d_small);
     if (ctx->h_small) cudaFreeHost(ctx->h_small);
+    if (ctx->ls_exec) cudaGraphExecDestroy(ctx->ls_exec);
+    if (ctx->ls_graph) cudaGraphDestroy(ctx->ls_graph);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->pin_event) cudaEventDestroy(ctx->pin_event);
     delete ctx;
     return SSS_OK;

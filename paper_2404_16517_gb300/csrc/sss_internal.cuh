@@ -82,6 +82,13 @@ struct sss_ctx {
     std::string timing_filter;
     std::vector<PendingTiming> pending;
     std::vector<cudaEvent_t> event_pool;
+    // graph of the local sort's round loop (SSS_FLAG_GRAPH), reused while its key
+    // (every pointer and size baked into it) is unchanged
+    bool capturing = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t ls_graph = nullptr;
+    cudaGraphExec_t ls_exec = nullptr;
+    std::string ls_key;
 };
 
 // Set ctx->last_error and return the status.
@@ -121,7 +128,7 @@ sss_status sss_launch(sss_ctx* ctx, const char* name, void (*kernel)(KArgs...), 
                       size_t smem, Args... args) {
     if (grid.x == 0 || grid.y == 0 || grid.z == 0) return SSS_OK;
     int st = sss_stat_index(ctx, name);
-    bool timed = sss_timing_on(ctx, st);
+    bool timed = !ctx->capturing && sss_timing_on(ctx, st);  // no event nodes inside a captured loop
     cudaEvent_t a = nullptr, b = nullptr;
     if (timed) {
         a = sss_event(ctx);

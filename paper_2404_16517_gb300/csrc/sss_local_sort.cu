@@ -21,6 +21,7 @@
 //  * LCP values fall out at every split (key_lcp); equal strings get lcp = their
 //    length.
 #include <algorithm>
+#include <cstdio>
 #include <vector>
 
 #include "sss_device.cuh"
@@ -776,6 +777,89 @@ static sss_status launch_round(sss_ctx* ctx, const LsBufs& B, const LsKnobs& kn,
     return run_finishers(ctx, B, B.cnt, 0, 0, 0, in, perm, lcp);
 }
 
+// Loop condition of the captured round loop: another round while segments were
+// pushed, the round limit is not reached and no capacity error occurred.
+__global__ void k_ls_cond(const uint32_t* __restrict__ cnt, uint32_t* rounds, uint32_t limit, unsigned* err,
+                          cudaGraphConditionalHandle h) {
+    const uint32_t r = ++*rounds;
+    bool more = cnt[2] > 0;
+    if (more && r >= limit) {
+        atomicOr(err, ERRBIT_OVERFLOW);
+        more = false;
+    }
+    if (*(volatile unsigned*)err & ERRBIT_OVERFLOW) more = false;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// The round loop as one graph launch: a while node whose body is one round plus
+// k_ls_cond.  Built on first use and kept in the context under a key of every
+// pointer and size its kernels take.
+static sss_status run_rounds_graph(sss_ctx* ctx, const LsBufs& B, const LsKnobs& kn, const SegLists& L,
+                                   const StrIn& in, uint32_t* perm, uint32_t* lcp, uint32_t limit) {
+    char keyb[512];
+    std::snprintf(keyb, sizeof(keyb), "%p %p %p %u %p %p %p %p %p %u %u %u %u %d %u", (const void*)in.chars,
+                  (const void*)in.offs, (const void*)in.lens, in.n, (void*)perm, (void*)lcp, (void*)B.K,
+                  (void*)B.large, (void*)B.sp.plan, kn.warp_cap, kn.cta_cap, kn.direct_cap, kn.bucket_target,
+                  ctx->sm_count, limit);
+    uint32_t* rounds = reinterpret_cast<uint32_t*>(ctx->d_err) + 1;  // a spare word of the context
+    if (!ctx->ls_exec || ctx->ls_key != keyb) {
+        if (ctx->ls_exec) cudaGraphExecDestroy(ctx->ls_exec);
+        if (ctx->ls_graph) cudaGraphDestroy(ctx->ls_graph);
+        ctx->ls_exec = nullptr;
+        ctx->ls_graph = nullptr;
+        if (!ctx->cap_stream) SSS_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t g;
+        SSS_CUDA(cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle h;
+        SSS_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        SSS_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaStream_t saved = ctx->stream;
+        ctx->stream = ctx->cap_stream;
+        ctx->capturing = true;
+        sss_status st = SSS_OK;
+        cudaError_t ce = cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0,
+                                                       cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            st = launch_round(ctx, B, kn, L, in, perm, lcp);
+            if (st == SSS_OK)
+                st = sss_launch(ctx, "ls_cond", k_ls_cond, dim3(1), dim3(1), 0, (const uint32_t*)B.cnt, rounds, limit,
+                                ctx->d_err, h);
+            cudaGraph_t out = body;
+            cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &out);
+            if (ce == cudaSuccess) ce = ee;
+        }
+        ctx->capturing = false;
+        ctx->stream = saved;
+        if (st != SSS_OK || ce != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphDestroy(g);
+            return st != SSS_OK ? st : sss_fail(ctx, SSS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        }
+        cudaGraphExec_t ex;
+        ce = cudaGraphInstantiate(&ex, g, 0);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphDestroy(g);
+            return sss_fail(ctx, SSS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        }
+        ctx->ls_graph = g;
+        ctx->ls_exec = ex;
+        ctx->ls_key = keyb;
+    }
+    SSS_CUDA(cudaMemsetAsync(rounds, 0, sizeof(uint32_t), ctx->stream));
+    SSS_CUDA(cudaGraphLaunch(ctx->ls_exec, ctx->stream));
+    int st = sss_stat_index(ctx, "ls_graph");
+    if (st >= 0) ctx->stats[st].launches++;
+    return SSS_OK;
+}
+
 sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const std::vector<Seg>& init,
                               const sss_params& prm, uint32_t* perm, uint32_t* lcp) {
     const uint32_t n = in.n;
@@ -823,6 +907,9 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
 
     SSS_CUDA(cudaMemsetAsync(B.fixmark, 0, n, ctx->stream));
     SegLists L{B.tiny, B.med, B.large, B.cnt, B.cap_tiny, B.cap_med, B.cap_large, B.warp, B.cap_warp, warp_max, med_max};
+    if (prm.flags & SSS_FLAG_GRAPH) {
+        SSS_TRY(run_rounds_graph(ctx, B, kn, L, in, perm, lcp, 100000u));
+    } else {
     uint32_t* h_next = reinterpret_cast<uint32_t*>(ctx->h_small);
     for (uint32_t rounds = 1;; ++rounds) {
         if (rounds > 100000u) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: round limit exceeded");
@@ -833,6 +920,7 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
         SSS_CUDA(cudaStreamSynchronize(ctx->stream));
         if (h_next[1] & ERRBIT_OVERFLOW) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: device capacity check failed");
         if (h_next[0] == 0) break;
+    }
     }
     SSS_TRY(sss_launch(ctx, "ls_fix_seams", k_fix_seams, dim3(std::min((n + 255) / 256, 4096u)), dim3(256), 0,
                        (const uint8_t*)B.fixmark, n, in.chars, in.offs, in.lens, (const uint32_t*)perm, lcp));

@@ -66,3 +66,29 @@ def test_autotuner_picks_a_candidate():
     assert best in autotune.candidates(grid)
     assert len(table) == 4 and table[0][1] == best
     assert all(table[i][0] <= table[i + 1][0] for i in range(3))
+
+
+def test_graph_round_loop_identical_and_reused():
+    """SSS_FLAG_GRAPH runs the round loop as one graph launch: outputs identical
+    to the host-driven loop, on a first call (capture), a repeated call (the
+    kept graph) and a call with other inputs (a new capture)."""
+    import paper_2404_16517_gb300 as sss
+    G = sss.SSS_FLAG_GRAPH
+    for m_inst, cap in ((40, 20000), (25, 9000)):
+        ss, first = datagen.config4(m=m_inst, size_cap=cap)
+        chars, offs, lens = sss.to_device(ss)
+        sizes = np.diff(first).astype(np.int64)
+        ref = sss.sss_sort_batch(chars, offs, lens, first[:-1], sizes, sss.params())
+        for k in ({}, {"bucket_target": 4096, "cta_cap": 300}):
+            for _ in range(2):
+                got = sss.sss_sort_batch(chars, offs, lens, first[:-1], sizes, sss.params(flags=G, **k))
+                sss.context().sync()
+                assert np.array_equal(sss.u32(got[0]), sss.u32(ref[0])), k
+                assert np.array_equal(sss.u32(got[1]), sss.u32(ref[1])), k
+    ss = datagen.config2(n=1 << 15)
+    chars, offs, lens = sss.to_device(ss)
+    want = oracle.sort(ss)
+    perm, lcp, _, _ = sss.sss_sort(chars, offs, lens, 8, sss.params(flags=G))
+    sss.context().sync()
+    assert np.array_equal(sss.u32(perm), want)
+    assert np.array_equal(sss.u32(lcp), oracle.lcp_array(ss, want))
