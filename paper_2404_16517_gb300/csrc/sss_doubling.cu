@@ -69,6 +69,22 @@ __device__ __forceinline__ uint64_t fold_limb(uint64_t h, uint64_t B, uint64_t l
     return t >= P61 ? t - P61 : t;
 }
 
+// Both 32-bit limbs of the word x at once: fold_limb(fold_limb(h, B, x_hi), B,
+// x_lo) = (h*B^2 + x_hi*B + x_lo) mod P, with B2 = B^2 mod P.  The 128-bit sum
+// of the two products and the low limb is reduced once: h*B2 < 2^122 and
+// x_hi*B < 2^93, so the high word stays below 2^59.
+__device__ __forceinline__ uint64_t fold_word(uint64_t h, uint64_t B, uint64_t B2, uint64_t x) {
+    const uint64_t xh = x >> 32, xl = x & 0xFFFFFFFFull;
+    const uint64_t a_lo = h * B2, a_hi = __umul64hi(h, B2);
+    const uint64_t b_lo = xh * B, b_hi = __umul64hi(xh, B);
+    const uint64_t s1 = a_lo + b_lo;
+    const uint64_t s2 = s1 + xl;
+    const uint64_t s_hi = a_hi + b_hi + (s1 < a_lo ? 1u : 0u) + (s2 < s1 ? 1u : 0u);
+    uint64_t s = (s_hi << 3) + (s2 >> 61) + (s2 & P61);
+    s = (s & P61) + (s >> 61);
+    return s >= P61 ? s - P61 : s;
+}
+
 struct PdIn {
     const uint8_t* chars;
     const uint64_t* offs;
@@ -87,12 +103,6 @@ __device__ __forceinline__ uint32_t part_end_of(uint32_t q, uint32_t n, uint32_t
 __device__ __forceinline__ bool is_part_start(uint32_t q, uint32_t n, uint32_t p) {
     uint64_t i = ((uint64_t)q * p + n - 1) / n;  // smallest i with floor(i*n/p) >= q
     return (uint32_t)((i * n) / p) == q;
-}
-
-// position q starts a group of equal L-prefixes in its local run
-__device__ __forceinline__ bool group_start(const PdIn& in, uint32_t q, uint64_t L) {
-    if (!in.run_lcp) return true;
-    return in.run_lcp[q] < L || is_part_start(q, in.n, in.p);
 }
 
 // warp-aggregated append of q to list[] (counter *cnt)
@@ -204,6 +214,7 @@ __global__ void k_pd_hash(PdIn in, const uint32_t* __restrict__ reps, uint32_t n
         }
     }
     uint32_t nw = (le + 7) / 8;
+    const uint64_t B2 = mulmod61(B, B);
     if (w0 < nw) {
         // words w0..nw-1 of the prefix, read as aligned 8-byte loads issued in
         // batches of 8 (only words that hold a character of the prefix are loaded)
@@ -226,8 +237,7 @@ __global__ void k_pd_hash(PdIn in, const uint32_t* __restrict__ reps, uint32_t n
                 prev = buf[i];
                 uint32_t left = le - 8 * (w + i);
                 if (left < 8) x &= ~0ull << (8 * (8 - left));
-                h = fold_limb(h, B, x >> 32);
-                h = fold_limb(h, B, x & 0xFFFFFFFFull);
+                h = fold_word(h, B, B2, x);
             }
             pw += 8;
         }
