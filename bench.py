@@ -481,9 +481,13 @@ def bench_batch(args, dev, ctx):
     def step():
         run(prm)
 
+    # per-kernel launch counts and times from one host-driven pass (kernels
+    # inside a graph launch are not timed one by one)
+    prm_h = sss.params(flags=prm.flags & ~sss.SSS_FLAG_GRAPH, cta_cap=prm.cta_cap, direct_cap=prm.direct_cap,
+                       bucket_target=prm.bucket_target, warp_cap=prm.warp_cap)
     ctx.reset_stats()
     ctx.set_timing(True, "")
-    step()
+    run(prm_h)
     torch.cuda.synchronize()
     stats = ctx.kernel_stats()
     ctx.set_timing(False)

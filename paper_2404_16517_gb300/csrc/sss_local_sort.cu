@@ -542,18 +542,22 @@ __global__ void __launch_bounds__(BK_T) k_lg_buckets(const LsPlan* __restrict__ 
 
 // Large segments of at most DIRECT_CAP strings: one CTA sorts the whole segment
 // by its keys (no sampling, classification or scatter).
-__global__ void __launch_bounds__(DIRECT_T) k_lg_direct(const LsPlan* __restrict__ plan,
-                                                        const LgSegInfo* __restrict__ info,
-                                                        const uint32_t* __restrict__ segfmt,
-                                                        const uint32_t* __restrict__ lens, uint64_t* __restrict__ K,
-                                                        uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
-                                                        SegLists L, unsigned* err, uint32_t* work) {
+// (two instances: segments of at most BK_CAP strings in 512-thread CTAs, two per
+// SM; larger ones up to DIRECT_CAP in 1024-thread CTAs; each skips the other's)
+template <int THREADS, int CAP>
+__global__ void __launch_bounds__(THREADS) k_lg_direct(const LsPlan* __restrict__ plan,
+                                                       const LgSegInfo* __restrict__ info,
+                                                       const uint32_t* __restrict__ segfmt,
+                                                       const uint32_t* __restrict__ lens, uint64_t* __restrict__ K,
+                                                       uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
+                                                       SegLists L, unsigned* err, uint32_t* work, uint32_t min_size) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t ns = plan->ns, npart = plan->npart;
     for (uint32_t sidx = npart + cta_next_unit(work); sidx < ns; sidx = npart + cta_next_unit(work)) {
         const LgSegInfo si = info[sidx];
-        sort_emit<DIRECT_T, DIRECT_CAP>(smem, si.seg.start, si.seg.size, si.seg.depth, segfmt[sidx], K, perm, lens, K,
-                                        perm, lcp, L, err);
+        if (si.seg.size <= min_size || si.seg.size > (uint32_t)CAP) continue;
+        sort_emit<THREADS, CAP>(smem, si.seg.start, si.seg.size, si.seg.depth, segfmt[sidx], K, perm, lens, K, perm,
+                                lcp, L, err);
     }
 }
 
@@ -731,7 +735,9 @@ static sss_status set_ls_attributes(sss_ctx* ctx) {
                                       (int)finish_smem(TINY_CAP)));
         SSS_CUDA(cudaFuncSetAttribute(k_lg_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(BK_CAP * (8 + 8 + 4 + 4))));
-        SSS_CUDA(cudaFuncSetAttribute(k_lg_direct, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SSS_CUDA(cudaFuncSetAttribute(k_lg_direct<BK_T, BK_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(BK_CAP * (8 + 8 + 4 + 4))));
+        SSS_CUDA(cudaFuncSetAttribute(k_lg_direct<DIRECT_T, DIRECT_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(DIRECT_CAP * (8 + 8 + 4 + 4))));
         g_attr_done[ctx->device & 63] = true;
     }
@@ -771,9 +777,13 @@ static sss_status launch_round(sss_ctx* ctx, const LsBufs& B, const LsKnobs& kn,
     SSS_TRY(sss_launch(ctx, "ls_lg_seams", k_lg_seams, dim3(sm * 2), dim3(512), 0, (const LsPlan*)B.sp.plan,
                        (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt,
                        (const uint64_t*)B.K, lcp));
-    SSS_TRY(sss_launch(ctx, "ls_lg_direct", k_lg_direct, dim3(sm), dim3(DIRECT_T), (size_t)DIRECT_CAP * (8 + 8 + 4 + 4),
-                       (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info, (const uint32_t*)B.segfmt, in.lens, B.K,
-                       perm, lcp, L, ctx->d_err, B.work + 4));
+    SSS_TRY(sss_launch(ctx, "ls_lg_direct", k_lg_direct<BK_T, BK_CAP>, dim3(sm * 2), dim3(BK_T),
+                       (size_t)BK_CAP * (8 + 8 + 4 + 4), (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info,
+                       (const uint32_t*)B.segfmt, in.lens, B.K, perm, lcp, L, ctx->d_err, B.work + 4, 0u));
+    SSS_TRY(sss_launch(ctx, "ls_lg_direct", k_lg_direct<DIRECT_T, DIRECT_CAP>, dim3(sm), dim3(DIRECT_T),
+                       (size_t)DIRECT_CAP * (8 + 8 + 4 + 4), (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info,
+                       (const uint32_t*)B.segfmt, in.lens, B.K, perm, lcp, L, ctx->d_err, B.work + 5,
+                       (uint32_t)BK_CAP));
     return run_finishers(ctx, B, B.cnt, 0, 0, 0, in, perm, lcp);
 }
 
