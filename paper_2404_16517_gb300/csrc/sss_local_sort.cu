@@ -35,7 +35,8 @@ constexpr uint32_t DONE = 0xFFFFFFFFu;
 // size classes
 constexpr int WF_WARPS = 8;                     // warp finisher: segments of <= 32 strings, one warp each
 constexpr int TINY_T = 64, TINY_CAP = 64;       // segments of warp_cap+1 .. 64 strings
-constexpr int MED_T = 256, MED_CAP = 2048;      // segments of 65 .. cta_cap (<= 2048) strings
+constexpr int SM_T = 128, SM_CAP = 512;         // segments of 65 .. 512 strings
+constexpr int MED_T = 256, MED_CAP = 2048;      // segments of 513 .. cta_cap (<= 2048) strings
 constexpr int BK_T = 512, BK_CAP = 4096;        // bucket sort CTA
 constexpr int DIRECT_T = 1024, DIRECT_CAP = 8192;  // whole-segment sort CTA (segments <= direct_cap)
 
@@ -43,11 +44,13 @@ struct SegLists {
     Seg* tiny;
     Seg* med;
     Seg* large;
-    uint32_t* cnt;  // [0] tiny, [1] med, [2] large, [3] warp
+    uint32_t* cnt;  // [0] tiny, [1] med, [2] large, [3] warp, [4] small
     uint32_t cap_tiny, cap_med, cap_large;
     Seg* warp;
     uint32_t cap_warp;
-    uint32_t warp_max, med_max;  // size classes: warp <= warp_max < tiny <= TINY_CAP < med <= med_max < large
+    Seg* small;
+    uint32_t cap_small;
+    uint32_t warp_max, med_max;  // classes: warp <= warp_max < tiny <= TINY_CAP < small <= SM_CAP < med <= med_max < large
 };
 
 __device__ __forceinline__ void push_seg(const SegLists& L, uint32_t start, uint32_t size, uint32_t depth,
@@ -59,6 +62,9 @@ __device__ __forceinline__ void push_seg(const SegLists& L, uint32_t start, uint
     } else if (size <= (uint32_t)TINY_CAP) {
         uint32_t i = atomicAdd(&L.cnt[0], 1u);
         if (i < L.cap_tiny) L.tiny[i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
+    } else if (size <= (uint32_t)SM_CAP && size <= L.med_max) {
+        uint32_t i = atomicAdd(&L.cnt[4], 1u);
+        if (i < L.cap_small) L.small[i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
     } else if (size <= L.med_max) {
         uint32_t i = atomicAdd(&L.cnt[1], 1u);
         if (i < L.cap_med) L.med[i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
@@ -542,8 +548,7 @@ __global__ void __launch_bounds__(BK_T) k_lg_buckets(const LsPlan* __restrict__ 
 
 // Large segments of at most DIRECT_CAP strings: one CTA sorts the whole segment
 // by its keys (no sampling, classification or scatter).
-// (two instances: segments of at most BK_CAP strings in 512-thread CTAs, two per
-// SM; larger ones up to DIRECT_CAP in 1024-thread CTAs; each skips the other's)
+// (segments of more than min_size strings; CAP bounds the size)
 template <int THREADS, int CAP>
 __global__ void __launch_bounds__(THREADS) k_lg_direct(const LsPlan* __restrict__ plan,
                                                        const LgSegInfo* __restrict__ info,
@@ -641,6 +646,7 @@ struct LsBufs {
     uint32_t* tV;
     Seg* warp;
     Seg* tiny;
+    Seg* small;
     Seg* med;
     Seg* large;
     uint32_t* cnt;
@@ -648,7 +654,7 @@ struct LsBufs {
     uint32_t* segfmt;
     uint8_t* fixmark;
     SpBufs sp;
-    uint32_t cap_warp, cap_tiny, cap_med, cap_large;
+    uint32_t cap_warp, cap_tiny, cap_small, cap_med, cap_large;
 };
 
 // The size-class knobs of the local sort; 0 (e.g. internal callers passing
@@ -670,16 +676,18 @@ void carve_ls(Arena& ar, uint32_t n, uint32_t p, const sss_params& prm, LsBufs& 
     const LsKnobs kn = ls_knobs(prm);
     b.cap_warp = n / 2 + 2;
     b.cap_tiny = n / (kn.warp_cap + 1) + 2;
-    b.cap_med = n / (TINY_CAP + 1) + 2;
+    b.cap_small = n / (TINY_CAP + 1) + 2;
+    b.cap_med = n / (SM_CAP + 1) + 2;
     b.cap_large = n / (kn.cta_cap + 1) + p + 2;  // every large segment holds > cta_cap strings
     b.K = ar.take<uint64_t>(n);
     b.tK = ar.take<uint64_t>(n);
     b.tV = ar.take<uint32_t>(n);
     b.warp = ar.take<Seg>(b.cap_warp);
     b.tiny = ar.take<Seg>(b.cap_tiny);
+    b.small = ar.take<Seg>(b.cap_small);
     b.med = ar.take<Seg>(b.cap_med);
     b.large = ar.take<Seg>(b.cap_large);
-    b.cnt = ar.take<uint32_t>(4);
+    b.cnt = ar.take<uint32_t>(8);
     b.work = ar.take<uint32_t>(8);
     b.segfmt = ar.take<uint32_t>(b.cap_large);
     b.fixmark = ar.take<uint8_t>(n);
@@ -689,19 +697,22 @@ void carve_ls(Arena& ar, uint32_t n, uint32_t p, const sss_params& prm, LsBufs& 
 // The three finishers over their lists: host counts, or (d_cnt != NULL) the
 // device counters of the round that just ran (d_cnt[3] warp, [0] tiny, [1] med).
 sss_status run_finishers(sss_ctx* ctx, const LsBufs& B, const uint32_t* d_cnt, uint32_t nwarp, uint32_t ntiny,
-                         uint32_t nmed, const StrIn& in, uint32_t* perm, uint32_t* lcp) {
+                         uint32_t nsmall, uint32_t nmed, const StrIn& in, uint32_t* perm, uint32_t* lcp) {
     const uint32_t sm = (uint32_t)std::max(1, ctx->sm_count);
-    uint32_t gw, gt, gm;
+    uint32_t gw, gt, gs, gm;
     if (d_cnt) {
         nwarp = B.cap_warp;
         ntiny = B.cap_tiny;
+        nsmall = B.cap_small;
         nmed = B.cap_med;
         gw = sm * 8;
         gt = sm * 16;
+        gs = sm * 8;
         gm = sm * 2;
     } else {
         gw = std::min((nwarp + WF_WARPS - 1) / WF_WARPS, sm * 16);
         gt = std::min(ntiny, sm * 32);
+        gs = std::min(nsmall, sm * 16);
         gm = std::min(nmed, sm * 4);
     }
     SSS_TRY(sss_launch(ctx, "ls_finish_warp", k_finish_warp, dim3(gw), dim3(32 * WF_WARPS), 0, (const Seg*)B.warp,
@@ -710,6 +721,9 @@ sss_status run_finishers(sss_ctx* ctx, const LsBufs& B, const uint32_t* d_cnt, u
     SSS_TRY(sss_launch(ctx, "ls_finish_tiny", k_finish<TINY_T, TINY_CAP>, dim3(gt), dim3(TINY_T),
                        finish_smem(TINY_CAP), (const Seg*)B.tiny, d_cnt ? d_cnt + 0 : (const uint32_t*)nullptr, ntiny,
                        B.work + 1, in.chars, in.offs, in.lens, perm, lcp, ctx->d_err));
+    SSS_TRY(sss_launch(ctx, "ls_finish_small", k_finish<SM_T, SM_CAP>, dim3(gs), dim3(SM_T), finish_smem(SM_CAP),
+                       (const Seg*)B.small, d_cnt ? d_cnt + 4 : (const uint32_t*)nullptr, nsmall, B.work + 6, in.chars,
+                       in.offs, in.lens, perm, lcp, ctx->d_err));
     SSS_TRY(sss_launch(ctx, "ls_finish_cta", k_finish<MED_T, MED_CAP>, dim3(gm), dim3(MED_T), finish_smem(MED_CAP),
                        (const Seg*)B.med, d_cnt ? d_cnt + 1 : (const uint32_t*)nullptr, nmed, B.work + 2, in.chars,
                        in.offs, in.lens, perm, lcp, ctx->d_err));
@@ -733,9 +747,9 @@ static sss_status set_ls_attributes(sss_ctx* ctx) {
                                       (int)finish_smem(MED_CAP)));
         SSS_CUDA(cudaFuncSetAttribute(k_finish<TINY_T, TINY_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)finish_smem(TINY_CAP)));
+        SSS_CUDA(cudaFuncSetAttribute(k_finish<SM_T, SM_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)finish_smem(SM_CAP)));
         SSS_CUDA(cudaFuncSetAttribute(k_lg_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(BK_CAP * (8 + 8 + 4 + 4))));
-        SSS_CUDA(cudaFuncSetAttribute(k_lg_direct<BK_T, BK_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(BK_CAP * (8 + 8 + 4 + 4))));
         SSS_CUDA(cudaFuncSetAttribute(k_lg_direct<DIRECT_T, DIRECT_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(DIRECT_CAP * (8 + 8 + 4 + 4))));
@@ -777,14 +791,10 @@ static sss_status launch_round(sss_ctx* ctx, const LsBufs& B, const LsKnobs& kn,
     SSS_TRY(sss_launch(ctx, "ls_lg_seams", k_lg_seams, dim3(sm * 2), dim3(512), 0, (const LsPlan*)B.sp.plan,
                        (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt,
                        (const uint64_t*)B.K, lcp));
-    SSS_TRY(sss_launch(ctx, "ls_lg_direct", k_lg_direct<BK_T, BK_CAP>, dim3(sm * 2), dim3(BK_T),
-                       (size_t)BK_CAP * (8 + 8 + 4 + 4), (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info,
-                       (const uint32_t*)B.segfmt, in.lens, B.K, perm, lcp, L, ctx->d_err, B.work + 4, 0u));
     SSS_TRY(sss_launch(ctx, "ls_lg_direct", k_lg_direct<DIRECT_T, DIRECT_CAP>, dim3(sm), dim3(DIRECT_T),
                        (size_t)DIRECT_CAP * (8 + 8 + 4 + 4), (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info,
-                       (const uint32_t*)B.segfmt, in.lens, B.K, perm, lcp, L, ctx->d_err, B.work + 5,
-                       (uint32_t)BK_CAP));
-    return run_finishers(ctx, B, B.cnt, 0, 0, 0, in, perm, lcp);
+                       (const uint32_t*)B.segfmt, in.lens, B.K, perm, lcp, L, ctx->d_err, B.work + 5, 0u));
+    return run_finishers(ctx, B, B.cnt, 0, 0, 0, 0, in, perm, lcp);
 }
 
 // Loop condition of the captured round loop: another round while segments were
@@ -882,11 +892,12 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
     SSS_TRY(sss_launch(ctx, "ls_init", k_init_perm, dim3((n + 255) / 256), dim3(256), 0, perm, lcp, n));
 
     // initial segments (partitions or instances), by size class
-    std::vector<Seg> warp, tiny, med, large;
+    std::vector<Seg> warp, tiny, small, med, large;
     for (const Seg& s : init) {
         if (s.size < 2) continue;
         if (s.size <= warp_max) warp.push_back(s);
         else if (s.size <= (uint32_t)TINY_CAP) tiny.push_back(s);
+        else if (s.size <= (uint32_t)SM_CAP && s.size <= med_max) small.push_back(s);
         else if (s.size <= med_max) med.push_back(s);
         else large.push_back(s);
     }
@@ -897,26 +908,30 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
     uint32_t* h_cnt = reinterpret_cast<uint32_t*>(pin);
     Seg* hw = reinterpret_cast<Seg*>(reinterpret_cast<char*>(pin) + 64);
     Seg* ht = hw + warp.size();
-    Seg* hm = ht + tiny.size();
+    Seg* hs = ht + tiny.size();
+    Seg* hm = hs + small.size();
     Seg* hl = hm + med.size();
     std::copy(warp.begin(), warp.end(), hw);
     std::copy(tiny.begin(), tiny.end(), ht);
+    std::copy(small.begin(), small.end(), hs);
     std::copy(med.begin(), med.end(), hm);
     std::copy(large.begin(), large.end(), hl);
-    h_cnt[0] = h_cnt[1] = h_cnt[3] = 0;
+    for (int k = 0; k < 8; ++k) h_cnt[k] = 0;
     h_cnt[2] = (uint32_t)large.size();
     SSS_TRY(sss_upload(ctx, B.warp, hw, sizeof(Seg) * warp.size()));
     SSS_TRY(sss_upload(ctx, B.tiny, ht, sizeof(Seg) * tiny.size()));
+    SSS_TRY(sss_upload(ctx, B.small, hs, sizeof(Seg) * small.size()));
     SSS_TRY(sss_upload(ctx, B.med, hm, sizeof(Seg) * med.size()));
     SSS_TRY(sss_upload(ctx, B.large, hl, sizeof(Seg) * large.size()));
-    SSS_TRY(sss_upload(ctx, B.cnt, h_cnt, sizeof(uint32_t) * 4));
+    SSS_TRY(sss_upload(ctx, B.cnt, h_cnt, sizeof(uint32_t) * 8));
     SSS_CUDA(cudaMemsetAsync(B.work, 0, sizeof(uint32_t) * 8, ctx->stream));
-    SSS_TRY(run_finishers(ctx, B, nullptr, (uint32_t)warp.size(), (uint32_t)tiny.size(), (uint32_t)med.size(), in,
-                          perm, lcp));
+    SSS_TRY(run_finishers(ctx, B, nullptr, (uint32_t)warp.size(), (uint32_t)tiny.size(), (uint32_t)small.size(),
+                          (uint32_t)med.size(), in, perm, lcp));
     if (large.empty()) return SSS_OK;
 
     SSS_CUDA(cudaMemsetAsync(B.fixmark, 0, n, ctx->stream));
-    SegLists L{B.tiny, B.med, B.large, B.cnt, B.cap_tiny, B.cap_med, B.cap_large, B.warp, B.cap_warp, warp_max, med_max};
+    SegLists L{B.tiny, B.med, B.large, B.cnt, B.cap_tiny, B.cap_med, B.cap_large, B.warp, B.cap_warp, B.small,
+               B.cap_small, warp_max, med_max};
     if (prm.flags & SSS_FLAG_GRAPH) {
         SSS_TRY(run_rounds_graph(ctx, B, kn, L, in, perm, lcp, 100000u));
     } else {

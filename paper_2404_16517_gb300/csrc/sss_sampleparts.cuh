@@ -54,7 +54,7 @@ struct LsPlan {
     uint32_t pad[2];
 };
 
-// Plan a round from the segment list `list` (count cnt[2]); resets the four list
+// Plan a round from the segment list `list` (count cnt[2]); resets the five list
 // counters for the pushes of this round and the eight dynamic work counters.
 // One CTA of 1024 threads.
 __global__ void __launch_bounds__(1024) k_lg_plan(const Seg* __restrict__ list, uint32_t* __restrict__ cnt,
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(1024) k_lg_plan(const Seg* __restrict__ list, 
             pl = LsPlan{0, 0, 0, 0, 0, 0, {0, 0}};
         }
         *plan = pl;
-        cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
+        cnt[0] = cnt[1] = cnt[2] = cnt[3] = cnt[4] = 0;
         for (int k = 0; k < 8; ++k) work[k] = 0;
     }
 }
