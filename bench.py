@@ -376,8 +376,13 @@ def main():
                           "parallelism": f"replicas x{ws}"},
                "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                             "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                            "frac_of_nominal_8tbs": achieved / 8000.0,
                             "algorithmic_bytes_per_launch": algo, "avg_launch_ms": avg_ms},
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+               "paper_context": {"note": "the paper's own PDMS wall times on SuperMUC-NG (48-core nodes), "
+                                         "DNData n/p = 1e5, as chars/s; other hardware, not a target",
+                                 "pdms1_4_nodes_192_cores": 1.62e10, "pdms2_4_nodes_192_cores": 1.51e10,
+                                 "pdms3_1024_nodes_49152_cores": 2.29e12},
                "kernel_ms_per_step": {k: v["total_ms"] for k, v in stats_all.items()}}
         if ws == 1 and args.workload == "all":
             del chars, offs, lens, perm, lcp, dist_t, approx
