@@ -84,6 +84,20 @@ __device__ __forceinline__ uint32_t cta_next_unit(uint32_t* counter) {
     return s_unit;
 }
 
+// The reference member of a group of `cnt` strings starting at `start` with
+// depth `depth`: a fixed pseudo-random one (results do not depend on the
+// choice).  Always taking the first member lets an input whose order follows
+// the strings' lengths or shared prefixes peel off a few strings per round.
+__device__ __forceinline__ uint32_t ref_pick(uint32_t start, uint32_t cnt, uint32_t depth) {
+    uint32_t x = start * 0x9E3779B9u ^ (depth + 0x7F4A7C15u) * 0x85EBCA6Bu ^ cnt * 0xC2B2AE35u;
+    x ^= x >> 16;
+    x *= 0x7FEB352Du;
+    x ^= x >> 15;
+    x *= 0x846CA68Bu;
+    x ^= x >> 16;
+    return cnt > 1 ? x % cnt : 0u;
+}
+
 __global__ void k_init_perm(uint32_t* perm, uint32_t* lcp, uint32_t n) {
     uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q < n) {
@@ -117,7 +131,10 @@ __device__ __forceinline__ void finish_segment(const Seg sg, const uint8_t* __re
         sV[i] = perm[sg.start + i];
         sG[i] = 0;
     }
-    if (tid == 0) sGD[0] = sg.depth;
+    if (tid == 0) {
+        sGD[0] = sg.depth;
+        sGM[0] = m;
+    }
     __syncthreads();
 
     // every iteration splits a group or finishes it, so a segment of m strings
@@ -136,23 +153,24 @@ __device__ __forceinline__ void finish_segment(const Seg sg, const uint8_t* __re
             if (sG[i] != DONE) sC[sA[i]] = i;
         __syncthreads();
 
-        // 2. reference-split key of every member against its group's first member;
-        //    pack (group, key, index)
+        // 2. reference-split key of every member against its group's reference
+        //    (ref_pick among the group's sGM[g] members); pack (group, key, index)
         for (uint32_t j = tid; j < nact; j += THREADS) {
             uint32_t pos = sC[j];
             uint32_t g = sG[pos];
             uint32_t d = sGD[g];
-            uint32_t e = sV[pos], r = sV[g];
+            const uint32_t refpos = g + ref_pick(g, sGM[g], d);
+            uint32_t e = sV[pos], r = sV[refpos];
             const uint8_t* rs = chars + offs[r];
             uint32_t rl = lens[r];
             uint64_t w;
             uint32_t v;
             const uint32_t f = key_fmt(rl, d);
-            if (pos == g) {
+            if (pos == g) sGF[g] = f;
+            if (pos == refpos) {
                 v = rl > d ? rl - d : 0u;
                 v = v < VCAP ? v : VCAP;
                 w = load_word_be(rs, rl, d + v);
-                sGF[g] = f;
             } else {
                 v = lcp_full_w(chars + offs[e], lens[e], rs, rl, d, &w);
             }
@@ -266,7 +284,7 @@ __device__ __forceinline__ void finish_warp_segment(const Seg sg, const uint8_t*
     const uint32_t span = m <= 2u ? 2u : (1u << (32 - __clz((int)(m - 1))));
     uint32_t e = live ? perm[sg.start + lane] : 0u;
     uint32_t len = live ? lens[e] : 0u;
-    uint32_t g = 0, gd = sg.depth;
+    uint32_t g = 0, gd = sg.depth, gc = m;  // group start lane, depth, member count
     bool done = !live;
     uint32_t iter = 0;
     for (;; ++iter) {
@@ -275,15 +293,16 @@ __device__ __forceinline__ void finish_warp_segment(const Seg sg, const uint8_t*
             if (lane == 0) atomicOr(err, ERRBIT_OVERFLOW);
             break;
         }
-        const uint32_t r = __shfl_sync(SSS_FULL, e, g);
-        const uint32_t rl = __shfl_sync(SSS_FULL, len, g);
+        const uint32_t rlane = g + ref_pick(g, gc, gd);
+        const uint32_t r = __shfl_sync(SSS_FULL, e, rlane);
+        const uint32_t rl = __shfl_sync(SSS_FULL, len, rlane);
         const uint32_t f = key_fmt(rl, gd);
         uint64_t hi, lo;
         if (!done) {
             const uint8_t* rs = chars + offs[r];
             uint64_t w;
             uint32_t v;
-            if (lane == g) {
+            if (lane == rlane) {
                 v = rl > gd ? rl - gd : 0u;
                 v = v < VCAP ? v : VCAP;
                 w = load_word_be(rs, rl, gd + v);
@@ -340,11 +359,13 @@ __device__ __forceinline__ void finish_warp_segment(const Seg sg, const uint8_t*
             } else {
                 done = false;
                 g = ng;
+                gc = cnt;
                 gd = gd + key_v(k, f) + fmt_chars(f);
             }
         } else {
             done = true;
             g = lane;
+            gc = 1;
         }
     }
     if (live) perm[sg.start + lane] = e;
@@ -389,7 +410,8 @@ __device__ __forceinline__ void lg_ext_tile(const LgTile tl, const LgSegInfo* __
     __shared__ uint64_t refw[NREF];
     LgSegInfo si = info[tl.s];
     const uint32_t d = si.seg.depth;
-    uint32_t r = perm[si.seg.start];
+    const uint32_t refpos = si.seg.start + ref_pick(si.seg.start, si.seg.size, d);
+    uint32_t r = perm[refpos];
     const uint8_t* rs = chars + offs[r];
     uint32_t rl = lens[r];
     const uint32_t f = key_fmt(rl, d);
@@ -399,7 +421,7 @@ __device__ __forceinline__ void lg_ext_tile(const LgTile tl, const LgSegInfo* __
     for (uint32_t q = tl.begin + threadIdx.x; q < tl.end; q += LG_T) {
         uint64_t w;
         uint32_t v;
-        if (q == si.seg.start) {
+        if (q == refpos) {
             v = rl > d ? rl - d : 0u;
             v = v < VCAP ? v : VCAP;
             w = load_word_be(rs, rl, d + v);

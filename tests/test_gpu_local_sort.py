@@ -135,3 +135,26 @@ def test_checked_mode_flags_bad_input():
     assert ei.value.status == 5
     # the context stays usable
     check_plain(ss)
+
+
+@pytest.mark.parametrize("n,order", [(1500, "up"), (1500, "down"), (6000, "up"), (6000, "down")])
+@pytest.mark.parametrize("knobs", [{}, {"cta_cap": 64, "direct_cap": 64, "bucket_target": 256}])
+def test_nested_prefixes_in_length_order(n, order, knobs):
+    """Strings A, AA, AAA, ... (each a prefix of the next) in length order: with
+    the segment's first member as reference every round would peel off a few
+    strings; a pseudo-random reference keeps the number of rounds logarithmic."""
+    import time
+    import paper_2404_16517_gb300 as m
+    ks = list(range(1, n + 1))
+    if order == "down":
+        ks.reverse()
+    ss = datagen.from_strings([b"A" * k for k in ks])
+    chars, offs, lens = m.to_device(ss)
+    t0 = time.time()
+    perm, lcp, _, _ = m.sss_sort(chars, offs, lens, 1, m.params(**knobs))
+    m.context().sync()
+    assert time.time() - t0 < 30
+    want = np.argsort(np.array(ks), kind="stable").astype(np.uint32)
+    assert np.array_equal(m.u32(perm), want)
+    sk = np.array(ks)[want]
+    assert np.array_equal(m.u32(lcp), np.concatenate([[0], sk[:-1]]).astype(np.uint32))
