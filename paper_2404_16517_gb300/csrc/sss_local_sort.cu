@@ -33,7 +33,8 @@ namespace {
 constexpr uint32_t DONE = 0xFFFFFFFFu;
 
 // size classes
-constexpr int WF_WARPS = 8;                     // warp finisher: segments of <= 32 strings, one warp each
+constexpr int WF_WARPS = 8;                     // group finishers: warps per CTA
+constexpr int QUAD_W = 4;                       // segments of <= 4 strings: 4 lanes each, 8 per warp
 constexpr int TINY_T = 64, TINY_CAP = 64;       // segments of warp_cap+1 .. 64 strings
 constexpr int SM_T = 128, SM_CAP = 512;         // segments of 65 .. 512 strings
 constexpr int MED_T = 256, MED_CAP = 2048;      // segments of 513 .. cta_cap (<= 2048) strings
@@ -44,7 +45,7 @@ struct SegLists {
     Seg* tiny;
     Seg* med;
     Seg* large;
-    uint32_t* cnt;  // [0] tiny, [1] med, [2] large, [3] warp, [4] small
+    uint32_t* cnt;  // [0] tiny, [1] med, [2] large, [3] warp, [4] small, [5] quad
     uint32_t cap_tiny, cap_med, cap_large;
     Seg* warp;
     uint32_t cap_warp;
@@ -57,8 +58,17 @@ __device__ __forceinline__ void push_seg(const SegLists& L, uint32_t start, uint
                                          unsigned* err) {
     Seg s{start, size, depth, 0};
     if (size <= L.warp_max) {
-        uint32_t i = atomicAdd(&L.cnt[3], 1u);
-        if (i < L.cap_warp) L.warp[i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
+        // one array for both short classes: segments of <= QUAD_W strings from
+        // the bottom (count cnt[5]), the others from the top (count cnt[3]); the
+        // two never meet, as the segments of a round are disjoint and hold >= 2
+        // strings each (the finishers check it)
+        if (size <= (uint32_t)QUAD_W) {
+            uint32_t i = atomicAdd(&L.cnt[5], 1u);
+            if (i < L.cap_warp) L.warp[i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
+        } else {
+            uint32_t i = atomicAdd(&L.cnt[3], 1u);
+            if (i < L.cap_warp) L.warp[L.cap_warp - 1u - i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
+        }
     } else if (size <= (uint32_t)TINY_CAP) {
         uint32_t i = atomicAdd(&L.cnt[0], 1u);
         if (i < L.cap_tiny) L.tiny[i] = s; else atomicOr(err, ERRBIT_OVERFLOW);
@@ -259,13 +269,17 @@ __global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs
         finish_segment<THREADS, CAP>(segs[i], chars, offs, lens, perm, lcp, err);
 }
 
-// Warp finisher: one warp completely sorts one segment of <= 32 strings, lane i
-// holding position i.  Same rounds as the CTA finisher (reference-split key of
-// every unfinished member against its group's first member, sort by (group,
-// key, index), split), with the sort a 32-lane bitonic network in registers.
-__device__ __forceinline__ void warp_cas128(uint64_t& hi, uint64_t& lo, uint32_t lane, uint32_t j, bool up) {
+// Group finisher: W consecutive lanes of a warp (W = 32, or QUAD_W for the
+// shortest segments, 32 / W segments per warp) completely sort one segment of
+// <= W strings, lane i of the group holding position i.  Same rounds as the CTA
+// finisher (reference-split key of every unfinished member against its group's
+// reference, sort by (group, key, index), split), with the sort a bitonic
+// network in registers.  Every lane of the warp runs every round (the loop
+// ends when no lane of the warp is left unfinished); a group whose segment is
+// finished, or that has none (`has` false), carries its lanes along unchanged.
+__device__ __forceinline__ void warp_cas128(uint64_t& hi, uint64_t& lo, uint32_t gl, uint32_t j, bool up) {
     uint64_t ohi = __shfl_xor_sync(SSS_FULL, hi, j), olo = __shfl_xor_sync(SSS_FULL, lo, j);
-    bool keep_min = (((lane & j) == 0) == up);
+    bool keep_min = (((gl & j) == 0) == up);
     bool other_less = key128_less(ohi, olo, hi, lo);
     if (keep_min ? other_less : key128_less(hi, lo, ohi, olo)) {
         hi = ohi;
@@ -273,36 +287,42 @@ __device__ __forceinline__ void warp_cas128(uint64_t& hi, uint64_t& lo, uint32_t
     }
 }
 
-__device__ __forceinline__ void finish_warp_segment(const Seg sg, const uint8_t* __restrict__ chars,
-                                                    const uint64_t* __restrict__ offs,
-                                                    const uint32_t* __restrict__ lens, uint32_t* __restrict__ perm,
-                                                    uint32_t* __restrict__ lcp, unsigned* err) {
+template <int W>
+__device__ __forceinline__ void finish_group_segment(const Seg sg, bool has, const uint8_t* __restrict__ chars,
+                                                     const uint64_t* __restrict__ offs,
+                                                     const uint32_t* __restrict__ lens, uint32_t* __restrict__ perm,
+                                                     uint32_t* __restrict__ lcp, unsigned* err) {
+    static_assert(W >= 2 && W <= 32 && (W & (W - 1)) == 0, "group width is a power of two <= 32");
     constexpr uint64_t DONE_BIT = 1ull << 47;  // in the low word, above the 32-bit index
+    constexpr unsigned WMASK = W == 32 ? ~0u : ((1u << W) - 1u);
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t m = sg.size <= 32u ? sg.size : 32u;
-    const bool live = lane < m;
-    const uint32_t span = m <= 2u ? 2u : (1u << (32 - __clz((int)(m - 1))));
-    uint32_t e = live ? perm[sg.start + lane] : 0u;
+    const uint32_t gl = lane & (W - 1);  // lane within the group
+    const uint32_t gb = lane - gl;       // the group's first lane
+    const uint32_t m = has ? (sg.size <= (uint32_t)W ? sg.size : (uint32_t)W) : 0u;
+    const bool live = gl < m;
+    // bitonic span, uniform over the warp: the group width, or for a whole-warp
+    // group the next power of two >= m (lanes past it hold padding and sit out)
+    const uint32_t span = W < 32 ? (uint32_t)W : (m <= 2u ? 2u : (1u << (32 - __clz((int)(m - 1)))));
+    uint32_t e = live ? perm[sg.start + gl] : 0u;
     uint32_t len = live ? lens[e] : 0u;
-    uint32_t g = 0, gd = sg.depth, gc = m;  // group start lane, depth, member count
+    uint32_t g = 0, gd = sg.depth, gc = m;  // group start (within the segment), depth, member count
     bool done = !live;
-    uint32_t iter = 0;
-    for (;; ++iter) {
+    for (uint32_t iter = 0;; ++iter) {
         if (__ballot_sync(SSS_FULL, !done) == 0) break;
-        if (iter > 4u * 32u + 8u) {
-            if (lane == 0) atomicOr(err, ERRBIT_OVERFLOW);
+        if (iter > 4u * W + 8u) {
+            if (!done) atomicOr(err, ERRBIT_OVERFLOW);
             break;
         }
         const uint32_t rlane = g + ref_pick(g, gc, gd);
-        const uint32_t r = __shfl_sync(SSS_FULL, e, rlane);
-        const uint32_t rl = __shfl_sync(SSS_FULL, len, rlane);
+        const uint32_t r = __shfl_sync(SSS_FULL, e, gb + rlane);
+        const uint32_t rl = __shfl_sync(SSS_FULL, len, gb + rlane);
         const uint32_t f = key_fmt(rl, gd);
         uint64_t hi, lo;
         if (!done) {
             const uint8_t* rs = chars + offs[r];
             uint64_t w;
             uint32_t v;
-            if (lane == rlane) {
+            if (gl == rlane) {
                 v = rl > gd ? rl - gd : 0u;
                 v = v < VCAP ? v : VCAP;
                 w = load_word_be(rs, rl, gd + v);
@@ -313,41 +333,39 @@ __device__ __forceinline__ void finish_warp_segment(const Seg sg, const uint8_t*
             hi = ((uint64_t)g << 48) | (k >> 16);
             lo = (k << 48) | (uint64_t)e;
         } else if (live) {
-            hi = (uint64_t)lane << 48;  // a finished string is the only member of group `lane`
+            hi = (uint64_t)gl << 48;  // a finished string is the only member of group `gl`
             lo = DONE_BIT | (uint64_t)e;
         } else {
             hi = ~0ull;
             lo = ~0ull;
         }
-        // bitonic network over the next power of two >= m lanes (warp-uniform);
-        // lanes past it hold padding and sit out
         for (uint32_t kk = 2; kk <= span; kk <<= 1) {
-            const bool up = (lane & kk) == 0 || kk == span;
-            for (uint32_t j = kk >> 1; j > 0; j >>= 1) warp_cas128(hi, lo, lane, j, up);
+            const bool up = (gl & kk) == 0 || kk == span;
+            for (uint32_t j = kk >> 1; j > 0; j >>= 1) warp_cas128(hi, lo, gl, j, up);
         }
-        // lane j now holds the j-th position of the segment; groups kept their ranges
+        // lane j of the group now holds position j; groups kept their ranges
         const uint32_t gg = (uint32_t)(hi >> 48);
         const uint64_t k = (hi << 16) | (lo >> 48);
         const bool fin = !live || (lo & DONE_BIT);
         e = (uint32_t)lo;
         len = live ? lens[e] : 0u;
-        const uint64_t hp = __shfl_up_sync(SSS_FULL, hi, 1), lp = __shfl_up_sync(SSS_FULL, lo, 1);
+        const uint64_t hp = __shfl_up_sync(SSS_FULL, hi, 1, W), lp = __shfl_up_sync(SSS_FULL, lo, 1, W);
         const uint32_t gp = (uint32_t)(hp >> 48);
         const uint64_t kp = (hp << 16) | (lp >> 48);
         bool bnd = true;
-        if (lane > 0 && !fin && gp == gg && !(lp & DONE_BIT)) {
+        if (gl > 0 && !fin && gp == gg && !(lp & DONE_BIT)) {
             bnd = (kp != k);
-            if (bnd) lcp[sg.start + lane] = gd + key_lcp(kp, k, f);
+            if (bnd) lcp[sg.start + gl] = gd + key_lcp(kp, k, f);
         }
         // new group start: inclusive max-scan of boundary positions
-        uint32_t ng = bnd ? lane : 0u;
+        uint32_t ng = bnd ? gl : 0u;
 #pragma unroll
-        for (uint32_t o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(SSS_FULL, ng, o);
-            if (lane >= o) ng = ng > y ? ng : y;
+        for (uint32_t o = 1; o < (uint32_t)W; o <<= 1) {
+            uint32_t y = __shfl_up_sync(SSS_FULL, ng, o, W);
+            if (gl >= o) ng = ng > y ? ng : y;
         }
-        const unsigned bm = __ballot_sync(SSS_FULL, bnd);
-        const unsigned after = lane < 31 ? (bm & (~0u << (lane + 1))) : 0u;
+        const unsigned bm = (__ballot_sync(SSS_FULL, bnd) >> gb) & WMASK;
+        const unsigned after = gl < (uint32_t)W - 1u ? (bm & (~0u << (gl + 1))) : 0u;
         const uint32_t end = after ? (uint32_t)(__ffs(after) - 1) : m;
         const uint32_t cnt = (end > ng ? end : ng + 1) - ng;
         if (!fin) {
@@ -355,7 +373,7 @@ __device__ __forceinline__ void finish_warp_segment(const Seg sg, const uint8_t*
                 done = true;
             } else if (key_ended(k, f)) {
                 done = true;
-                if (lane != ng) lcp[sg.start + lane] = len;
+                if (gl != ng) lcp[sg.start + gl] = len;
             } else {
                 done = false;
                 g = ng;
@@ -364,30 +382,44 @@ __device__ __forceinline__ void finish_warp_segment(const Seg sg, const uint8_t*
             }
         } else {
             done = true;
-            g = lane;
+            g = gl;
             gc = 1;
         }
     }
-    if (live) perm[sg.start + lane] = e;
+    if (live) perm[sg.start + gl] = e;
 }
 
-// segs[0 .. count) (count from the device when d_count is given, clamped to
-// count), one warp per segment
-__global__ void __launch_bounds__(32 * WF_WARPS) k_finish_warp(const Seg* __restrict__ segs,
-                                                               const uint32_t* __restrict__ d_count, uint32_t count,
-                                                               uint32_t* work, const uint8_t* __restrict__ chars,
-                                                               const uint64_t* __restrict__ offs,
-                                                               const uint32_t* __restrict__ lens,
-                                                               uint32_t* __restrict__ perm, uint32_t* __restrict__ lcp,
-                                                               unsigned* err) {
-    const uint32_t nseg = d_count ? min(*d_count, count) : count;
+// Short segments, 32 / W per warp: segment i is segs[i] (top == 0) or
+// segs[top - 1 - i] (a list filled from the top of its array); count from the
+// device when d_count is given, clamped to count.  d_other, when given, is the
+// count of the list that fills the same array from the other end: the two must
+// not overlap.
+template <int W>
+__global__ void __launch_bounds__(32 * WF_WARPS) k_finish_group(const Seg* __restrict__ segs,
+                                                                const uint32_t* __restrict__ d_count,
+                                                                const uint32_t* __restrict__ d_other, uint32_t count,
+                                                                uint32_t top, uint32_t* work,
+                                                                const uint8_t* __restrict__ chars,
+                                                                const uint64_t* __restrict__ offs,
+                                                                const uint32_t* __restrict__ lens,
+                                                                uint32_t* __restrict__ perm,
+                                                                uint32_t* __restrict__ lcp, unsigned* err) {
+    constexpr uint32_t G = 32u / W;
+    uint32_t nseg = d_count ? min(*d_count, count) : count;
+    if (d_count && d_other && (uint64_t)*d_count + *d_other > count) {
+        if (threadIdx.x == 0) atomicOr(err, ERRBIT_OVERFLOW);
+        nseg = 0;
+    }
     const uint32_t lane = threadIdx.x & 31;
     for (;;) {
-        uint32_t i = 0;
-        if (lane == 0) i = atomicAdd(work, 1u);
-        i = __shfl_sync(SSS_FULL, i, 0);
-        if (i >= nseg) break;
-        finish_warp_segment(segs[i], chars, offs, lens, perm, lcp, err);
+        uint32_t i0 = 0;
+        if (lane == 0) i0 = atomicAdd(work, G);
+        i0 = __shfl_sync(SSS_FULL, i0, 0);
+        if (i0 >= nseg) break;
+        const uint32_t i = i0 + lane / W;
+        const bool has = i < nseg;
+        const Seg sg = has ? segs[top ? top - 1u - i : i] : Seg{0, 0, 0, 0};
+        finish_group_segment<W>(sg, has, chars, offs, lens, perm, lcp, err);
     }
 }
 
@@ -716,30 +748,41 @@ void carve_ls(Arena& ar, uint32_t n, uint32_t p, const sss_params& prm, LsBufs& 
     carve_sp(ar, n, b.cap_large, b.sp);
 }
 
-// The three finishers over their lists: host counts, or (d_cnt != NULL) the
-// device counters of the round that just ran (d_cnt[3] warp, [0] tiny, [1] med).
-sss_status run_finishers(sss_ctx* ctx, const LsBufs& B, const uint32_t* d_cnt, uint32_t nwarp, uint32_t ntiny,
-                         uint32_t nsmall, uint32_t nmed, const StrIn& in, uint32_t* perm, uint32_t* lcp) {
+// The finishers over their lists: host counts, or (d_cnt != NULL) the device
+// counters of the round that just ran (d_cnt[5] quad, [3] warp, [0] tiny,
+// [4] small, [1] med).
+sss_status run_finishers(sss_ctx* ctx, const LsBufs& B, const uint32_t* d_cnt, uint32_t nquad, uint32_t nwarp,
+                         uint32_t ntiny, uint32_t nsmall, uint32_t nmed, const StrIn& in, uint32_t* perm,
+                         uint32_t* lcp) {
     const uint32_t sm = (uint32_t)std::max(1, ctx->sm_count);
-    uint32_t gw, gt, gs, gm;
+    uint32_t gq, gw, gt, gs, gm;
     if (d_cnt) {
-        nwarp = B.cap_warp;
+        nquad = nwarp = B.cap_warp;
         ntiny = B.cap_tiny;
         nsmall = B.cap_small;
         nmed = B.cap_med;
+        gq = sm * 8;
         gw = sm * 8;
         gt = sm * 16;
         gs = sm * 8;
         gm = sm * 2;
     } else {
+        if ((uint64_t)nquad + nwarp > B.cap_warp) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: internal capacity exceeded");
+        const uint32_t qpb = WF_WARPS * (32 / QUAD_W);  // quad segments per CTA step
+        gq = std::min((nquad + qpb - 1) / qpb, sm * 8);
         gw = std::min((nwarp + WF_WARPS - 1) / WF_WARPS, sm * 16);
         gt = std::min(ntiny, sm * 32);
         gs = std::min(nsmall, sm * 16);
         gm = std::min(nmed, sm * 4);
     }
-    SSS_TRY(sss_launch(ctx, "ls_finish_warp", k_finish_warp, dim3(gw), dim3(32 * WF_WARPS), 0, (const Seg*)B.warp,
-                       d_cnt ? d_cnt + 3 : (const uint32_t*)nullptr, nwarp, B.work + 0, in.chars, in.offs, in.lens,
-                       perm, lcp, ctx->d_err));
+    SSS_TRY(sss_launch(ctx, "ls_finish_quad", k_finish_group<QUAD_W>, dim3(gq), dim3(32 * WF_WARPS), 0,
+                       (const Seg*)B.warp, d_cnt ? d_cnt + 5 : (const uint32_t*)nullptr,
+                       d_cnt ? d_cnt + 3 : (const uint32_t*)nullptr, nquad, 0u, B.work + 4, in.chars, in.offs,
+                       in.lens, perm, lcp, ctx->d_err));
+    SSS_TRY(sss_launch(ctx, "ls_finish_warp", k_finish_group<32>, dim3(gw), dim3(32 * WF_WARPS), 0,
+                       (const Seg*)B.warp, d_cnt ? d_cnt + 3 : (const uint32_t*)nullptr,
+                       (const uint32_t*)nullptr, nwarp, B.cap_warp, B.work + 0, in.chars, in.offs, in.lens, perm,
+                       lcp, ctx->d_err));
     SSS_TRY(sss_launch(ctx, "ls_finish_tiny", k_finish<TINY_T, TINY_CAP>, dim3(gt), dim3(TINY_T),
                        finish_smem(TINY_CAP), (const Seg*)B.tiny, d_cnt ? d_cnt + 0 : (const uint32_t*)nullptr, ntiny,
                        B.work + 1, in.chars, in.offs, in.lens, perm, lcp, ctx->d_err));
@@ -816,7 +859,7 @@ static sss_status launch_round(sss_ctx* ctx, const LsBufs& B, const LsKnobs& kn,
     SSS_TRY(sss_launch(ctx, "ls_lg_direct", k_lg_direct<DIRECT_T, DIRECT_CAP>, dim3(sm), dim3(DIRECT_T),
                        (size_t)DIRECT_CAP * (8 + 8 + 4 + 4), (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info,
                        (const uint32_t*)B.segfmt, in.lens, B.K, perm, lcp, L, ctx->d_err, B.work + 5, 0u));
-    return run_finishers(ctx, B, B.cnt, 0, 0, 0, 0, in, perm, lcp);
+    return run_finishers(ctx, B, B.cnt, 0, 0, 0, 0, 0, in, perm, lcp);
 }
 
 // Loop condition of the captured round loop: another round while segments were
@@ -914,25 +957,31 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
     SSS_TRY(sss_launch(ctx, "ls_init", k_init_perm, dim3((n + 255) / 256), dim3(256), 0, perm, lcp, n));
 
     // initial segments (partitions or instances), by size class
-    std::vector<Seg> warp, tiny, small, med, large;
+    std::vector<Seg> quad, warp, tiny, small, med, large;
     for (const Seg& s : init) {
         if (s.size < 2) continue;
-        if (s.size <= warp_max) warp.push_back(s);
+        if (s.size <= warp_max && s.size <= (uint32_t)QUAD_W) quad.push_back(s);
+        else if (s.size <= warp_max) warp.push_back(s);
         else if (s.size <= (uint32_t)TINY_CAP) tiny.push_back(s);
         else if (s.size <= (uint32_t)SM_CAP && s.size <= med_max) small.push_back(s);
         else if (s.size <= med_max) med.push_back(s);
         else large.push_back(s);
     }
-    if (large.size() > B.cap_large) return sss_fail(ctx, SSS_ERR_CUDA, "local sort: internal capacity exceeded");
+    if (large.size() > B.cap_large || quad.size() + warp.size() > B.cap_warp)
+        return sss_fail(ctx, SSS_ERR_CUDA, "local sort: internal capacity exceeded");
+    // the warp class fills its array from the top: segment i at cap_warp - 1 - i
+    std::reverse(warp.begin(), warp.end());
     // pinned staging: counters, then the initial lists
     void* pin;
     SSS_TRY(sss_pinned(ctx, 64 + sizeof(Seg) * (init.size() + 4), &pin));
     uint32_t* h_cnt = reinterpret_cast<uint32_t*>(pin);
-    Seg* hw = reinterpret_cast<Seg*>(reinterpret_cast<char*>(pin) + 64);
+    Seg* hq = reinterpret_cast<Seg*>(reinterpret_cast<char*>(pin) + 64);
+    Seg* hw = hq + quad.size();
     Seg* ht = hw + warp.size();
     Seg* hs = ht + tiny.size();
     Seg* hm = hs + small.size();
     Seg* hl = hm + med.size();
+    std::copy(quad.begin(), quad.end(), hq);
     std::copy(warp.begin(), warp.end(), hw);
     std::copy(tiny.begin(), tiny.end(), ht);
     std::copy(small.begin(), small.end(), hs);
@@ -940,15 +989,16 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
     std::copy(large.begin(), large.end(), hl);
     for (int k = 0; k < 8; ++k) h_cnt[k] = 0;
     h_cnt[2] = (uint32_t)large.size();
-    SSS_TRY(sss_upload(ctx, B.warp, hw, sizeof(Seg) * warp.size()));
+    SSS_TRY(sss_upload(ctx, B.warp, hq, sizeof(Seg) * quad.size()));
+    SSS_TRY(sss_upload(ctx, B.warp + (B.cap_warp - warp.size()), hw, sizeof(Seg) * warp.size()));
     SSS_TRY(sss_upload(ctx, B.tiny, ht, sizeof(Seg) * tiny.size()));
     SSS_TRY(sss_upload(ctx, B.small, hs, sizeof(Seg) * small.size()));
     SSS_TRY(sss_upload(ctx, B.med, hm, sizeof(Seg) * med.size()));
     SSS_TRY(sss_upload(ctx, B.large, hl, sizeof(Seg) * large.size()));
     SSS_TRY(sss_upload(ctx, B.cnt, h_cnt, sizeof(uint32_t) * 8));
     SSS_CUDA(cudaMemsetAsync(B.work, 0, sizeof(uint32_t) * 8, ctx->stream));
-    SSS_TRY(run_finishers(ctx, B, nullptr, (uint32_t)warp.size(), (uint32_t)tiny.size(), (uint32_t)small.size(),
-                          (uint32_t)med.size(), in, perm, lcp));
+    SSS_TRY(run_finishers(ctx, B, nullptr, (uint32_t)quad.size(), (uint32_t)warp.size(), (uint32_t)tiny.size(),
+                          (uint32_t)small.size(), (uint32_t)med.size(), in, perm, lcp));
     if (large.empty()) return SSS_OK;
 
     SSS_CUDA(cudaMemsetAsync(B.fixmark, 0, n, ctx->stream));

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(1024) k_lg_plan(const Seg* __restrict__ list, 
             pl = LsPlan{0, 0, 0, 0, 0, 0, {0, 0}};
         }
         *plan = pl;
-        cnt[0] = cnt[1] = cnt[2] = cnt[3] = cnt[4] = 0;
+        cnt[0] = cnt[1] = cnt[2] = cnt[3] = cnt[4] = cnt[5] = 0;
         for (int k = 0; k < 8; ++k) work[k] = 0;
     }
 }
