@@ -98,8 +98,9 @@ __device__ __forceinline__ uint32_t cta_next_unit(uint32_t* counter) {
 // depth `depth`: a fixed pseudo-random one (results do not depend on the
 // choice).  Always taking the first member lets an input whose order follows
 // the strings' lengths or shared prefixes peel off a few strings per round.
-__device__ __forceinline__ uint32_t ref_pick(uint32_t start, uint32_t cnt, uint32_t depth) {
-    uint32_t x = start * 0x9E3779B9u ^ (depth + 0x7F4A7C15u) * 0x85EBCA6Bu ^ cnt * 0xC2B2AE35u;
+// `t` > 0 draws further candidates from the same sequence.
+__device__ __forceinline__ uint32_t ref_pick(uint32_t start, uint32_t cnt, uint32_t depth, uint32_t t = 0) {
+    uint32_t x = start * 0x9E3779B9u ^ (depth + 0x7F4A7C15u) * 0x85EBCA6Bu ^ cnt * 0xC2B2AE35u ^ t * 0x27D4EB2Fu;
     x ^= x >> 16;
     x *= 0x7FEB352Du;
     x ^= x >> 15;
@@ -440,9 +441,35 @@ __device__ __forceinline__ void lg_ext_tile(const LgTile tl, const LgSegInfo* __
                                             uint64_t* __restrict__ K, uint32_t* __restrict__ segfmt) {
     constexpr uint32_t NREF = 68;  // 64 words (512 chars) plus a 4-word block of slack
     __shared__ uint64_t refw[NREF];
+    __shared__ uint32_t s_refpos;
     LgSegInfo si = info[tl.s];
     const uint32_t d = si.seg.depth;
-    const uint32_t refpos = si.seg.start + ref_pick(si.seg.start, si.seg.size, d);
+    // The reference of a large segment: the longest of REF_CAND pseudo-random
+    // members (the earliest candidate on ties).  A member's LCP with the
+    // reference is capped by the reference's length, so a short reference
+    // leaves every longer member that shares its whole remainder in one group,
+    // and an input whose shared prefixes grow with the length (nested copies of
+    // one template) then sheds only a fraction of the segment per round.
+    if (threadIdx.x < 32) {
+        constexpr uint32_t REF_CAND = 8;
+        const uint32_t t = threadIdx.x;
+        uint64_t best = 0;
+        uint32_t pos = si.seg.start;
+        if (t < REF_CAND) {
+            pos = si.seg.start + ref_pick(si.seg.start, si.seg.size, d, t);
+            best = ((uint64_t)lens[perm[pos]] << 32) | (uint64_t)(REF_CAND - t);
+        }
+#pragma unroll
+        for (uint32_t o = 16; o > 0; o >>= 1) {
+            uint64_t ob = __shfl_xor_sync(SSS_FULL, best, o);
+            best = ob > best ? ob : best;
+        }
+        const uint32_t win = REF_CAND - (uint32_t)best;  // the winning candidate's t
+        const uint32_t wpos = __shfl_sync(SSS_FULL, pos, win);
+        if (t == 0) s_refpos = wpos;
+    }
+    __syncthreads();
+    const uint32_t refpos = s_refpos;
     uint32_t r = perm[refpos];
     const uint8_t* rs = chars + offs[r];
     uint32_t rl = lens[r];
