@@ -94,19 +94,25 @@ __device__ __forceinline__ uint32_t cta_next_unit(uint32_t* counter) {
     return s_unit;
 }
 
-// The reference member of a group of `cnt` strings starting at `start` with
-// depth `depth`: a fixed pseudo-random one (results do not depend on the
-// choice).  Always taking the first member lets an input whose order follows
-// the strings' lengths or shared prefixes peel off a few strings per round.
-// `t` > 0 draws further candidates from the same sequence.
-__device__ __forceinline__ uint32_t ref_pick(uint32_t start, uint32_t cnt, uint32_t depth, uint32_t t = 0) {
+// Candidates for the reference member of a group of `cnt` strings starting at
+// `start` with depth `depth`: fixed pseudo-random members, the t-th from
+// ref_pick(.., t) (results do not depend on the choice).  The finishers and
+// the large path take the longest of several candidates: a member's LCP with
+// the reference is capped by the reference's length, so a short reference keeps
+// every longer member that shares its whole remainder in one group.  Always
+// taking the first member would let an input whose order follows the strings'
+// lengths or shared prefixes peel off a few strings per round.
+__device__ __forceinline__ uint32_t ref_mix(uint32_t start, uint32_t cnt, uint32_t depth, uint32_t t) {
     uint32_t x = start * 0x9E3779B9u ^ (depth + 0x7F4A7C15u) * 0x85EBCA6Bu ^ cnt * 0xC2B2AE35u ^ t * 0x27D4EB2Fu;
     x ^= x >> 16;
     x *= 0x7FEB352Du;
     x ^= x >> 15;
     x *= 0x846CA68Bu;
     x ^= x >> 16;
-    return cnt > 1 ? x % cnt : 0u;
+    return x;
+}
+__device__ __forceinline__ uint32_t ref_pick(uint32_t start, uint32_t cnt, uint32_t depth, uint32_t t = 0) {
+    return cnt > 1 ? ref_mix(start, cnt, depth, t) % cnt : 0u;
 }
 
 __global__ void k_init_perm(uint32_t* perm, uint32_t* lcp, uint32_t n) {
@@ -164,13 +170,43 @@ __device__ __forceinline__ void finish_segment(const Seg sg, const uint8_t* __re
             if (sG[i] != DONE) sC[sA[i]] = i;
         __syncthreads();
 
-        // 2. reference-split key of every member against its group's reference
-        //    (ref_pick among the group's sGM[g] members); pack (group, key, index)
+        // 2a. every group's reference: its longest member among up to
+        //     REF_CAND candidates (all members of a smaller group, scanned from
+        //     a pseudo-random one on, else pseudo-random ones; the earliest
+        //     candidate on ties), kept at the group start in the scan buffer,
+        //     which is free until step 5
+        for (uint32_t j = tid; j < nact; j += THREADS) {
+            const uint32_t pos = sC[j];
+            if (sG[pos] != pos) continue;
+            constexpr uint32_t REF_CAND = 8;
+            const uint32_t c = sGM[pos], d = sGD[pos];
+            uint32_t best = pos, blen = 0;
+            if (c <= REF_CAND) {
+                const uint32_t t0 = ref_pick(pos, c, d);
+                for (uint32_t t = 0; t < c; ++t) {
+                    const uint32_t q = pos + (t0 + t < c ? t0 + t : t0 + t - c);
+                    const uint32_t l = lens[sV[q]];
+                    if (t == 0 || l > blen) { blen = l; best = q; }
+                }
+            } else {
+#pragma unroll
+                for (uint32_t t = 0; t < REF_CAND; ++t) {
+                    const uint32_t q = pos + ref_pick(pos, c, d, t);
+                    const uint32_t l = lens[sV[q]];
+                    if (t == 0 || l > blen) { blen = l; best = q; }
+                }
+            }
+            sA[pos] = best;
+        }
+        __syncthreads();
+
+        // 2b. reference-split key of every member against its group's
+        //     reference; pack (group, key, index)
         for (uint32_t j = tid; j < nact; j += THREADS) {
             uint32_t pos = sC[j];
             uint32_t g = sG[pos];
             uint32_t d = sGD[g];
-            const uint32_t refpos = g + ref_pick(g, sGM[g], d);
+            const uint32_t refpos = sA[g];
             uint32_t e = sV[pos], r = sV[refpos];
             const uint8_t* rs = chars + offs[r];
             uint32_t rl = lens[r];
@@ -314,7 +350,18 @@ __device__ __forceinline__ void finish_group_segment(const Seg sg, bool has, con
             if (!done) atomicOr(err, ERRBIT_OVERFLOW);
             break;
         }
-        const uint32_t rlane = g + ref_pick(g, gc, gd);
+        // the reference of the lane's group: its longest member, ties broken by
+        // a pseudo-random rank (segmented max-scan over the group's lanes; the
+        // group's last lane holds the maximum)
+        uint64_t best = live ? ((uint64_t)len << 32) | (ref_mix(g, gc, gd, gl + 1u) & 0xFFFFFF00u) | gl : 0ull;
+        const uint32_t gs = live ? g : gl;
+#pragma unroll
+        for (uint32_t o = 1; o < (uint32_t)W; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(SSS_FULL, best, o, W);
+            if (gl >= gs + o) best = y > best ? y : best;
+        }
+        best = __shfl_sync(SSS_FULL, best, gb + (live ? g + gc - 1u : gl));
+        const uint32_t rlane = (uint32_t)best & 0xFFu;
         const uint32_t r = __shfl_sync(SSS_FULL, e, gb + rlane);
         const uint32_t rl = __shfl_sync(SSS_FULL, len, gb + rlane);
         const uint32_t f = key_fmt(rl, gd);
