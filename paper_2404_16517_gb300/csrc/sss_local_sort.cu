@@ -84,6 +84,45 @@ __device__ __forceinline__ void push_seg(const SegLists& L, uint32_t start, uint
     }
 }
 
+// push_seg for a whole warp: every lane calls it (converged) and the lanes
+// with `want` push their segment.  Lanes pushing to the same list share one
+// atomic on its counter: a round can emit millions of short segments, and one
+// atomic per segment on the few list counters serialises in L2.
+__device__ __forceinline__ void push_seg_warp(const SegLists& L, bool want, uint32_t start, uint32_t size,
+                                              uint32_t depth, unsigned* err) {
+    if (__ballot_sync(SSS_FULL, want) == 0) return;
+    // list of the segment: 0 quad, 1 warp, 2 tiny, 3 small, 4 med, 5 large; 6 none
+    uint32_t cls = 6u;
+    if (want) {
+        if (size <= L.warp_max) cls = size <= (uint32_t)QUAD_W ? 0u : 1u;
+        else if (size <= (uint32_t)TINY_CAP) cls = 2u;
+        else if (size <= (uint32_t)SM_CAP && size <= L.med_max) cls = 3u;
+        else if (size <= L.med_max) cls = 4u;
+        else cls = 5u;
+    }
+    const unsigned peers = __match_any_sync(SSS_FULL, cls);
+    if (!want) return;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t leader = (uint32_t)__ffs(peers) - 1u;
+    const uint32_t rank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    const uint32_t cidx = (0x214035u >> (4u * cls)) & 0xFu;  // counter of the list: 5 3 0 4 1 2
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&L.cnt[cidx], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const uint32_t i = base + rank;
+    const Seg sg{start, size, depth, 0};
+    bool ok;
+    switch (cls) {
+        case 0: ok = i < L.cap_warp; if (ok) L.warp[i] = sg; break;
+        case 1: ok = i < L.cap_warp; if (ok) L.warp[L.cap_warp - 1u - i] = sg; break;
+        case 2: ok = i < L.cap_tiny; if (ok) L.tiny[i] = sg; break;
+        case 3: ok = i < L.cap_small; if (ok) L.small[i] = sg; break;
+        case 4: ok = i < L.cap_med; if (ok) L.med[i] = sg; break;
+        default: ok = i < L.cap_large; if (ok) L.large[i] = sg; break;
+    }
+    if (!ok) atomicOr(err, ERRBIT_OVERFLOW);
+}
+
 // Dynamic work distribution: the next unit for the whole CTA (units vary a lot
 // in cost, so a static block-to-unit map leaves a long tail).
 __device__ __forceinline__ uint32_t cta_next_unit(uint32_t* counter) {
@@ -596,16 +635,24 @@ __device__ void sort_emit(unsigned char* smem, uint32_t bs, uint32_t m, uint32_t
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < m; i += THREADS) atomicAdd(&sN[sA[i]], 1u);
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < m; i += THREADS) {
-        uint32_t g = sA[i];
-        uint32_t c = sN[g];
-        if (c < 2) continue;
-        uint64_t k = sHi[i];
-        if (key_ended(k, f)) {
-            if (i != g) lcp[bs + i] = lens[(uint32_t)sLo[i]];
-        } else if (i == g) {
-            push_seg(L, bs + g, c, d + key_v(k, f) + fmt_chars(f), err);
+    for (uint32_t i0 = 0; i0 < m; i0 += THREADS) {  // uniform trip count: push_seg_warp needs whole warps
+        const uint32_t i = i0 + threadIdx.x;
+        bool want = false;
+        uint32_t c = 0, dn = 0;
+        if (i < m) {
+            const uint32_t g = sA[i];
+            c = sN[g];
+            if (c >= 2) {
+                const uint64_t k = sHi[i];
+                if (key_ended(k, f)) {
+                    if (i != g) lcp[bs + i] = lens[(uint32_t)sLo[i]];
+                } else if (i == g) {
+                    want = true;
+                    dn = d + key_v(k, f) + fmt_chars(f);
+                }
+            }
         }
+        push_seg_warp(L, want, bs + i, c, dn, err);
     }
 }
 
@@ -660,7 +707,7 @@ __device__ __forceinline__ void lg_bucket(uint32_t g, uint32_t ns, const LgSegIn
     sort_emit<BK_T, BK_CAP>(smem, bs, m, d, f, tK, tV, lens, K, perm, lcp, L, err);
 }
 
-__global__ void __launch_bounds__(BK_T) k_lg_buckets(const LsPlan* __restrict__ plan,
+__global__ void __launch_bounds__(BK_T, 2) k_lg_buckets(const LsPlan* __restrict__ plan,
                                                      const LgSegInfo* __restrict__ info,
                                                      const uint32_t* __restrict__ bst,
                                                      const uint32_t* __restrict__ segfmt,
