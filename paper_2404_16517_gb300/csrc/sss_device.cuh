@@ -551,21 +551,39 @@ __device__ void block_merge_sort128(uint64_t* sHi, uint64_t* sLo, uint32_t count
             else hi = mid;
         }
         uint32_t a = lo, b = diag - lo;
+        // the heads of both lists stay in registers; each output step loads
+        // only the new head of the list it took from (address chosen without a
+        // branch, so the warp does not diverge)
+        uint64_t ah = ~0ull, al = ~0ull, bh = ~0ull, bl = ~0ull;
+        if (a < L) {
+            const uint32_t aj = swz<ITEMS>(A0 + a);
+            ah = sHi[aj];
+            al = sLo[aj];
+        }
+        if (b < L) {
+            const uint32_t bj = swz<ITEMS>(B0 + b);
+            bh = sHi[bj];
+            bl = sLo[bj];
+        }
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
-            uint32_t aj = swz<ITEMS>(A0 + a), bj = swz<ITEMS>(B0 + b);
-            bool takeA;
-            if (a >= L) takeA = false;
-            else if (b >= L) takeA = true;
-            else takeA = !key128_less(sHi[bj], sLo[bj], sHi[aj], sLo[aj]);
-            if (takeA) {
-                h[i] = sHi[aj];
-                l[i] = sLo[aj];
-                ++a;
-            } else {
-                h[i] = sHi[bj];
-                l[i] = sLo[bj];
-                ++b;
+            const bool takeA = a < L && (b >= L || !key128_less(bh, bl, ah, al));
+            h[i] = takeA ? ah : bh;
+            l[i] = takeA ? al : bl;
+            a += takeA ? 1u : 0u;
+            b += takeA ? 0u : 1u;
+            if (i + 1 < ITEMS) {
+                const uint32_t nx = takeA ? a : b;
+                uint64_t nh = ~0ull, nl = ~0ull;
+                if (nx < L) {
+                    const uint32_t nj = swz<ITEMS>((takeA ? A0 : B0) + nx);
+                    nh = sHi[nj];
+                    nl = sLo[nj];
+                }
+                ah = takeA ? nh : ah;
+                al = takeA ? nl : al;
+                bh = takeA ? bh : nh;
+                bl = takeA ? bl : nl;
             }
         }
     }
@@ -592,4 +610,19 @@ __device__ void block_merge_sort128(uint64_t* sHi, uint64_t* sLo, uint32_t count
         sLo[j] = l[i];
     }
     __syncthreads();
+}
+
+// block_merge_sort128 with half the items per thread when `count` fits in half
+// the slots: every thread then holds real keys, instead of half of them idling
+// through every merge round (one more, shorter round).  `count` is uniform over
+// the CTA; both variants are compiled in.
+template <int THREADS, int ITEMS>
+__device__ void block_merge_sort128_fit(uint64_t* sHi, uint64_t* sLo, uint32_t count) {
+    if constexpr (ITEMS >= 4) {
+        if (count <= (uint32_t)(THREADS * ITEMS / 2)) {
+            block_merge_sort128<THREADS, ITEMS / 2>(sHi, sLo, count);
+            return;
+        }
+    }
+    block_merge_sort128<THREADS, ITEMS>(sHi, sLo, count);
 }

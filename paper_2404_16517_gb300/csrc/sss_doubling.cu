@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(DD_T) k_pd_buckets(const uint32_t* __restrict_
             sV[i] = tV[bs + i];
         }
         __syncthreads();
-        block_merge_sort128<DD_T, DD_CAP / DD_T>(sK, sV, m);
+        block_merge_sort128_fit<DD_T, DD_CAP / DD_T>(sK, sV, m);
         for (uint32_t i = threadIdx.x; i < m; i += DD_T) {
             uint64_t k = sK[i];
             bool d = (i > 0 && sK[i - 1] == k) || (i + 1 < m && sK[i + 1] == k);
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(DD_T) k_pd_buckets(const uint32_t* __restrict_
             sV[i] = tV[c0 + i];
         }
         __syncthreads();
-        block_merge_sort128<DD_T, DD_CAP / DD_T>(sK, sV, cm);
+        block_merge_sort128_fit<DD_T, DD_CAP / DD_T>(sK, sV, cm);
         for (uint32_t i = threadIdx.x; i < cm; i += DD_T) {
             tK[c0 + i] = sK[i];
             tV[c0 + i] = (uint32_t)sV[i];

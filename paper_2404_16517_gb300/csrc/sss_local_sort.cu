@@ -267,7 +267,7 @@ __device__ __forceinline__ void finish_segment(const Seg sg, const uint8_t* __re
         __syncthreads();
 
         // 3. sort (group, key, index)
-        block_merge_sort128<THREADS, ITEMS>(sHi, sLo, nact);
+        block_merge_sort128_fit<THREADS, ITEMS>(sHi, sLo, nact);
 
         // 5. write back, find new group boundaries, LCP at new boundaries
         for (uint32_t j = tid; j < nact; j += THREADS) {
@@ -615,7 +615,7 @@ __device__ void sort_emit(unsigned char* smem, uint32_t bs, uint32_t m, uint32_t
         sLo[i] = srcV[bs + i];
     }
     __syncthreads();
-    block_merge_sort128<THREADS, ITEMS>(sHi, sLo, m);
+    block_merge_sort128_fit<THREADS, ITEMS>(sHi, sLo, m);
     for (uint32_t i = threadIdx.x; i < CAP; i += THREADS) {
         uint32_t v = 0;
         if (i < m) {

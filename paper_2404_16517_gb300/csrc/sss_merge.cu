@@ -918,7 +918,7 @@ __global__ void __launch_bounds__(D2_T) k_d2_cta(Strs S, Recs R, const uint64_t*
         sLo[u] = (k << 32) | u;
     }
     __syncthreads();
-    block_merge_sort128<D2_T, D2_CAP / D2_T>(sHi, sLo, m);
+    block_merge_sort128_fit<D2_T, D2_CAP / D2_T>(sHi, sLo, m);
     for (uint32_t t = threadIdx.x; t < m; t += D2_T) {
         uint32_t u = (uint32_t)sLo[t];
         out_perm[base + t] = R.idx[base + u];
