@@ -46,6 +46,13 @@ struct WordStream {
         cur = rem ? bswap64(__ldg(p)) : 0;
         ++p;
     }
+    // the characters at the current position that came with the first load:
+    // returns them left-aligned, *nb = how many (>= 1 when rem > 0)
+    __device__ __forceinline__ uint64_t head(uint32_t* nb) const {
+        const uint32_t av = 8u - sh / 8u;
+        *nb = av < rem ? av : rem;
+        return cur << sh;
+    }
     // the next 4 words (32 characters), with the 4 aligned loads issued together
     __device__ __forceinline__ void next4(uint64_t* w) {
         uint64_t nx[4];
@@ -150,6 +157,11 @@ struct WordStream16 {
 // at d + v (zero past its end).
 constexpr uint32_t VCAP = (1u << 30) - 1;
 
+// the first nb (0..8) bytes of a big-endian word
+__device__ __forceinline__ uint64_t top_bytes_mask(uint32_t nb) {
+    return nb >= 8u ? ~0ull : (nb ? ~0ull << (8u * (8u - nb)) : 0ull);
+}
+
 __device__ __forceinline__ uint32_t lcp_full_w(const uint8_t* __restrict__ a, uint32_t la,
                                                const uint8_t* __restrict__ b, uint32_t lb, uint32_t d,
                                                uint64_t* w) {
@@ -161,7 +173,16 @@ __device__ __forceinline__ uint32_t lcp_full_w(const uint8_t* __restrict__ a, ui
         A.init(a, la, d);
         B.init(b, lb, d);
         r = cap;
-        for (uint32_t k = 0; k < cap && k < VCAP; k += 32) {
+        // most pairs differ within the characters of the first loads: only
+        // then stream on
+        uint32_t na, nb;
+        const uint64_t ha = A.head(&na), hb = B.head(&nb);
+        const uint64_t x0 = (ha ^ hb) & top_bytes_mask(na < nb ? na : nb);
+        if (x0) {
+            const uint32_t c = (uint32_t)__clzll((long long)x0) >> 3;
+            r = c < cap ? c : cap;
+        }
+        for (uint32_t k = 0; !x0 && k < cap && k < VCAP; k += 32) {
             uint64_t xa[4], xb[4];
             A.next4(xa);
             B.next4(xb);

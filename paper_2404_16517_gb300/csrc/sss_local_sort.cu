@@ -38,7 +38,8 @@ constexpr int QUAD_W = 4;                       // segments of <= 4 strings: 4 l
 constexpr int TINY_T = 64, TINY_CAP = 64;       // segments of warp_cap+1 .. 64 strings
 constexpr int SM_T = 128, SM_CAP = 512;         // segments of 65 .. 512 strings
 constexpr int MED_T = 256, MED_CAP = 2048;      // segments of 513 .. cta_cap (<= 2048) strings
-constexpr int BK_T = 512, BK_CAP = 4096;        // bucket sort CTA
+constexpr int BK_T = 512, BK_CAP = 4096;        // bucket sort CTA (bucket targets above BKS_CAP / 2)
+constexpr int BKS_T = 256, BKS_CAP = 2048;      // bucket sort CTA for targets <= BKS_CAP / 2 (4 CTAs per SM)
 constexpr int DIRECT_T = 1024, DIRECT_CAP = 8192;  // whole-segment sort CTA (segments <= direct_cap)
 
 struct SegLists {
@@ -658,6 +659,7 @@ __device__ void sort_emit(unsigned char* smem, uint32_t bs, uint32_t m, uint32_t
 
 // One CTA per (segment, bucket).  Range buckets are sorted in shared memory;
 // groups of equal keys become new segments at depth d + v + C.
+template <int THREADS, int CAP>
 __device__ __forceinline__ void lg_bucket(uint32_t g, uint32_t ns, const LgSegInfo* __restrict__ info,
                                           const uint32_t* __restrict__ bst, const uint32_t* __restrict__ segfmt,
                                           const uint64_t* __restrict__ tK, const uint32_t* __restrict__ tV,
@@ -680,8 +682,8 @@ __device__ __forceinline__ void lg_bucket(uint32_t g, uint32_t ns, const LgSegIn
     uint32_t d = si.seg.depth;
     const uint32_t f = segfmt[sidx];
     bool eq = (b & 1u) != 0;
-    if (eq || m > (uint32_t)BK_CAP) {
-        for (uint32_t q = bs + threadIdx.x; q < be; q += BK_T) {
+    if (eq || m > (uint32_t)CAP) {
+        for (uint32_t q = bs + threadIdx.x; q < be; q += THREADS) {
             K[q] = tK[q];
             perm[q] = tV[q];
         }
@@ -700,14 +702,15 @@ __device__ __forceinline__ void lg_bucket(uint32_t g, uint32_t ns, const LgSegIn
         }
         if (eq && m >= 2 && key_ended(tK[bs], f)) {
             // a run of equal strings: lcp = length inside the run
-            for (uint32_t q = bs + 1 + threadIdx.x; q < be; q += BK_T) lcp[q] = lens[tV[q]];
+            for (uint32_t q = bs + 1 + threadIdx.x; q < be; q += THREADS) lcp[q] = lens[tV[q]];
         }
         return;
     }
-    sort_emit<BK_T, BK_CAP>(smem, bs, m, d, f, tK, tV, lens, K, perm, lcp, L, err);
+    sort_emit<THREADS, CAP>(smem, bs, m, d, f, tK, tV, lens, K, perm, lcp, L, err);
 }
 
-__global__ void __launch_bounds__(BK_T, 2) k_lg_buckets(const LsPlan* __restrict__ plan,
+template <int THREADS, int CAP>
+__global__ void __launch_bounds__(THREADS, 65536 / (64 * THREADS)) k_lg_buckets(const LsPlan* __restrict__ plan,
                                                      const LgSegInfo* __restrict__ info,
                                                      const uint32_t* __restrict__ bst,
                                                      const uint32_t* __restrict__ segfmt,
@@ -718,7 +721,7 @@ __global__ void __launch_bounds__(BK_T, 2) k_lg_buckets(const LsPlan* __restrict
                                                      uint32_t* work) {
     const uint32_t nb = plan->pbuckets, npart = plan->npart;
     for (uint32_t g = cta_next_unit(work); g < nb; g = cta_next_unit(work))
-        lg_bucket(g, npart, info, bst, segfmt, tK, tV, lens, K, perm, lcp, L, err, fixmark);
+        lg_bucket<THREADS, CAP>(g, npart, info, bst, segfmt, tK, tV, lens, K, perm, lcp, L, err, fixmark);
 }
 
 // Large segments of at most DIRECT_CAP strings: one CTA sorts the whole segment
@@ -935,8 +938,10 @@ static sss_status set_ls_attributes(sss_ctx* ctx) {
                                       (int)finish_smem(TINY_CAP)));
         SSS_CUDA(cudaFuncSetAttribute(k_finish<SM_T, SM_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)finish_smem(SM_CAP)));
-        SSS_CUDA(cudaFuncSetAttribute(k_lg_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SSS_CUDA(cudaFuncSetAttribute(k_lg_buckets<BK_T, BK_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(BK_CAP * (8 + 8 + 4 + 4))));
+        SSS_CUDA(cudaFuncSetAttribute(k_lg_buckets<BKS_T, BKS_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(BKS_CAP * (8 + 8 + 4 + 4))));
         SSS_CUDA(cudaFuncSetAttribute(k_lg_direct<DIRECT_T, DIRECT_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(DIRECT_CAP * (8 + 8 + 4 + 4))));
         g_attr_done[ctx->device & 63] = true;
@@ -970,10 +975,17 @@ static sss_status launch_round(sss_ctx* ctx, const LsBufs& B, const LsKnobs& kn,
                        (const uint32_t*)perm, B.K, B.segfmt));
     SSS_TRY(launch_sp(ctx, B.sp, B.K, perm, B.tK, B.tV, "ls_lg_samples", "ls_lg_classify", "ls_lg_offsets",
                       "ls_lg_scatter"));
-    SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets, dim3(sm * 2), dim3(BK_T), (size_t)BK_CAP * (8 + 8 + 4 + 4),
-                       (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst,
-                       (const uint32_t*)B.segfmt, (const uint64_t*)B.tK, (const uint32_t*)B.tV, in.lens, B.K, perm, lcp,
-                       L, ctx->d_err, B.fixmark, B.work + 3));
+    if (kn.bucket_target <= (uint32_t)BKS_CAP / 2) {
+        SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets<BKS_T, BKS_CAP>, dim3(sm * 4), dim3(BKS_T),
+                           (size_t)BKS_CAP * (8 + 8 + 4 + 4), (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info,
+                           (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt, (const uint64_t*)B.tK,
+                           (const uint32_t*)B.tV, in.lens, B.K, perm, lcp, L, ctx->d_err, B.fixmark, B.work + 3));
+    } else {
+        SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets<BK_T, BK_CAP>, dim3(sm * 2), dim3(BK_T),
+                           (size_t)BK_CAP * (8 + 8 + 4 + 4), (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info,
+                           (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt, (const uint64_t*)B.tK,
+                           (const uint32_t*)B.tV, in.lens, B.K, perm, lcp, L, ctx->d_err, B.fixmark, B.work + 3));
+    }
     SSS_TRY(sss_launch(ctx, "ls_lg_seams", k_lg_seams, dim3(sm * 2), dim3(512), 0, (const LsPlan*)B.sp.plan,
                        (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt,
                        (const uint64_t*)B.K, lcp));
