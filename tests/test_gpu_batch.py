@@ -78,3 +78,31 @@ def test_device_instance_generator_identical():
     assert np.array_equal(first, first2)
     assert np.array_equal(c.cpu().numpy()[:ss.chars.size], ss.chars)
     assert np.array_equal(l.cpu().numpy().view(np.uint32), ss.lens)
+
+
+def test_batch_of_short_instances_fills_both_short_classes():
+    # instances of 2..33 strings over {a, b} with many duplicates: the 2..4
+    # string instances go to the 4-lane class, 5..32 to the warp class (both
+    # filling one shared array, from its two ends), 33 to the 64-thread CTA
+    m = sss()
+    rng = np.random.default_rng(17)
+    strs, sizes = [], []
+    for k in range(3000):
+        c = 2 + k % 32
+        sizes.append(c)
+        for _ in range(c):
+            ln = int(rng.integers(0, 12))
+            strs.append(bytes(rng.choice(np.frombuffer(b"ab", dtype=np.uint8), ln).tolist()))
+    ss = datagen.from_strings(strs)
+    sizes = np.array(sizes, dtype=np.int64)
+    first = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    chars, offs, lens = m.to_device(ss)
+    perm, lcp, _ = m.sss_sort_batch(chars, offs, lens, first[:-1], sizes)
+    m.context().sync()
+    P, L = m.u32(perm), m.u32(lcp)
+    for k in range(len(sizes)):
+        a, b = int(first[k]), int(first[k + 1])
+        sub = view(ss, a, b)
+        want = oracle.sort(sub)
+        assert np.array_equal(P[a:b], want), f"instance {k}"
+        assert np.array_equal(L[a:b], oracle.lcp_array(sub, want)), f"instance {k} lcp"
