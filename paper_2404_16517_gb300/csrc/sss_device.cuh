@@ -633,6 +633,139 @@ __device__ void block_merge_sort128(uint64_t* sHi, uint64_t* sLo, uint32_t count
     __syncthreads();
 }
 
+// Merge nr sorted runs of 128-bit keys held in shared memory (run k = slots
+// [rb[k], rb[k+1]), rb[0] = 0, rb[nr] = count; plain order in and out) into one
+// ascending list: ceil(log2 nr) rounds that merge adjacent pairs of runs, where a
+// full sort takes log2(THREADS) rounds plus the per-thread sorts.  Every thread
+// produces the ITEMS consecutive outputs from tid*ITEMS on, crossing into the
+// next pair of runs where its range does; layout and merge steps as in
+// block_merge_sort128.  rb (nr + 1 shared words) is overwritten; nr <= 2*THREADS.
+template <int THREADS, int ITEMS>
+__device__ void block_merge_runs128(uint64_t* sHi, uint64_t* sLo, uint32_t count, uint32_t* rb, uint32_t nr) {
+    const uint32_t tid = threadIdx.x;
+    uint64_t h[ITEMS], l[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t j = tid + i * THREADS;
+        h[i] = j < count ? sHi[j] : ~0ull;
+        l[i] = j < count ? sLo[j] : ~0ull;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t j = swz<ITEMS>(tid + i * THREADS);
+        sHi[j] = h[i];
+        sLo[j] = l[i];
+    }
+    while (nr > 1) {
+        __syncthreads();
+        const uint32_t npair = (nr + 1) / 2;
+        const uint32_t j0 = tid * ITEMS;
+        if (j0 < count) {
+            // the pair of runs holding output j0: the last q with rb[2q] <= j0
+            uint32_t q = 0, qe = npair;
+            while (qe - q > 1) {
+                const uint32_t mid = (q + qe) >> 1;
+                if (rb[2 * mid] <= j0) q = mid;
+                else qe = mid;
+            }
+            uint32_t A0 = rb[2 * q], B0 = 2 * q + 1 <= nr ? rb[2 * q + 1] : count;
+            uint32_t E = 2 * q + 2 <= nr ? rb[2 * q + 2] : count;
+            uint32_t LA = B0 - A0, LB = E - B0;
+            const uint32_t diag = j0 - A0;
+            uint32_t lo = diag > LB ? diag - LB : 0, hi = diag < LA ? diag : LA;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                const uint32_t bj = swz<ITEMS>(B0 + diag - 1 - mid), aj = swz<ITEMS>(A0 + mid);
+                if (!key128_less(sHi[bj], sLo[bj], sHi[aj], sLo[aj])) lo = mid + 1;
+                else hi = mid;
+            }
+            uint32_t a = lo, b = diag - lo;
+            uint64_t ah = ~0ull, al = ~0ull, bh = ~0ull, bl = ~0ull;
+            if (a < LA) {
+                ah = sHi[swz<ITEMS>(A0 + a)];
+                al = sLo[swz<ITEMS>(A0 + a)];
+            }
+            if (b < LB) {
+                bh = sHi[swz<ITEMS>(B0 + b)];
+                bl = sLo[swz<ITEMS>(B0 + b)];
+            }
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                if (j0 + i >= count) {
+                    h[i] = ~0ull;
+                    l[i] = ~0ull;
+                    continue;
+                }
+                while (a >= LA && b >= LB) {  // this pair is done: on to the next
+                    ++q;
+                    A0 = E;
+                    B0 = 2 * q + 1 <= nr ? rb[2 * q + 1] : count;
+                    E = 2 * q + 2 <= nr ? rb[2 * q + 2] : count;
+                    LA = B0 - A0;
+                    LB = E - B0;
+                    a = b = 0;
+                    if (LA) {
+                        ah = sHi[swz<ITEMS>(A0)];
+                        al = sLo[swz<ITEMS>(A0)];
+                    }
+                    if (LB) {
+                        bh = sHi[swz<ITEMS>(B0)];
+                        bl = sLo[swz<ITEMS>(B0)];
+                    }
+                }
+                const bool takeA = a < LA && (b >= LB || !key128_less(bh, bl, ah, al));
+                h[i] = takeA ? ah : bh;
+                l[i] = takeA ? al : bl;
+                a += takeA ? 1u : 0u;
+                b += takeA ? 0u : 1u;
+                const uint32_t nx = takeA ? a : b;
+                if (nx < (takeA ? LA : LB)) {
+                    const uint32_t nj = swz<ITEMS>((takeA ? A0 : B0) + nx);
+                    const uint64_t nh = sHi[nj], nl = sLo[nj];
+                    ah = takeA ? nh : ah;
+                    al = takeA ? nl : al;
+                    bh = takeA ? bh : nh;
+                    bl = takeA ? bl : nl;
+                }
+            }
+        }
+        // the merged pairs are the next round's runs
+        uint32_t nb = 0;
+        if (tid < npair) nb = rb[2 * tid];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t j = tid * ITEMS + i;
+            if (j < count) {
+                sHi[swz<ITEMS>(j)] = h[i];
+                sLo[swz<ITEMS>(j)] = l[i];
+            }
+        }
+        if (tid < npair) rb[tid] = nb;
+        if (tid == 0) rb[npair] = count;
+        nr = npair;
+    }
+    // swizzled -> plain
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t j = tid + i * THREADS;
+        h[i] = sHi[swz<ITEMS>(j)];
+        l[i] = sLo[swz<ITEMS>(j)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t j = tid + i * THREADS;
+        if (j < count) {
+            sHi[j] = h[i];
+            sLo[j] = l[i];
+        }
+    }
+    __syncthreads();
+}
+
 // block_merge_sort128 with half the items per thread when `count` fits in half
 // the slots: every thread then holds real keys, instead of half of them idling
 // through every merge round (one more, shorter round).  `count` is uniform over

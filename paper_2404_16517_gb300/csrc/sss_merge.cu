@@ -675,6 +675,8 @@ __global__ void k_d_out(const Recs R, const uint32_t* __restrict__ Rfin, const u
 constexpr uint32_t D2_CAP = 2048;  // strings merged by one CTA (<= the stage-A CTA finisher)
 constexpr uint32_t D2_OVS = 16;    // samples per sub-bucket
 constexpr int D2_T = 512;
+constexpr uint32_t D2_MAXP = 256;  // slices a CTA merges as runs (more: a full sort)
+static_assert(D2_MAXP <= 2 * D2_T, "block_merge_runs128 takes at most 2*THREADS runs");
 
 struct BucketInfo {
     uint32_t sbase;  // first sorted-sample index of the bucket
@@ -911,6 +913,11 @@ __global__ void __launch_bounds__(D2_T) k_d2_cta(Strs S, Recs R, const uint64_t*
     const uint32_t base = (uint32_t)soff[(uint64_t)b * p];
     const uint32_t m = (uint32_t)soff[(uint64_t)(b + 1) * p] - base;
     if (m == 0 || m > D2_CAP) return;
+    // slice i (one sorted run of the merge) is [rb[i], rb[i+1])
+    __shared__ uint32_t s_rb[D2_MAXP + 1];
+    const bool runs = p <= D2_MAXP;
+    if (runs)
+        for (uint32_t i = threadIdx.x; i <= p; i += D2_T) s_rb[i] = (uint32_t)soff[(uint64_t)b * p + i] - base;
     for (uint32_t u = threadIdx.x; u < m; u += D2_T) {
         uint32_t r = rr[base + u];
         uint64_t k = rk[base + u];
@@ -918,7 +925,12 @@ __global__ void __launch_bounds__(D2_T) k_d2_cta(Strs S, Recs R, const uint64_t*
         sLo[u] = (k << 32) | u;
     }
     __syncthreads();
-    block_merge_sort128_fit<D2_T, D2_CAP / D2_T>(sHi, sLo, m);
+    // every slice is ascending in these keys (r never grows along a sorted slice
+    // of strings above the reference, and at equal r the next characters do
+    // not fall), so a merge of the p slices sorts the sub-bucket
+    if (!runs) block_merge_sort128_fit<D2_T, D2_CAP / D2_T>(sHi, sLo, m);
+    else if (m <= D2_CAP / 2) block_merge_runs128<D2_T, D2_CAP / D2_T / 2>(sHi, sLo, m, s_rb, p);
+    else block_merge_runs128<D2_T, D2_CAP / D2_T>(sHi, sLo, m, s_rb, p);
     for (uint32_t t = threadIdx.x; t < m; t += D2_T) {
         uint32_t u = (uint32_t)sLo[t];
         out_perm[base + t] = R.idx[base + u];
