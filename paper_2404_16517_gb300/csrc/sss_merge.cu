@@ -876,18 +876,32 @@ __global__ void k_d2_decode(Strs S, Recs R, const BucketInfo* __restrict__ bi, u
     uint64_t key = load_word_be(S.chars + S.offs[e0], R.tl[s0], r);
     rr[s0] = r;
     rk[s0] = key;
-    for (uint32_t u = s0 + 1; u < s1; ++u) {
-        uint32_t h = R.h[u];
-        uint64_t hw = R.head[u];  // characters [h, h+8) of string u
-        if (h <= r) {
-            r = h;
-            key = hw;
-        } else if (h - r < 8) {
-            uint32_t d = h - r;
-            key = (key & (~0ull << (64 - 8 * d))) | (hw >> (8 * d));
+    // the walk is serial, so the records are read 8 at a time ahead of it
+    const uint32_t* __restrict__ rh = R.h;
+    const uint64_t* __restrict__ rhead = R.head;
+    for (uint32_t u0 = s0 + 1; u0 < s1; u0 += 8) {
+        uint32_t hb[8];
+        uint64_t wb[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            hb[i] = u0 + i < s1 ? rh[u0 + i] : 0u;
+            wb[i] = u0 + i < s1 ? rhead[u0 + i] : 0ull;  // characters [h, h+8) of the string
         }
-        rr[u] = r;
-        rk[u] = key;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (u0 + i >= s1) break;
+            const uint32_t h = hb[i];
+            const uint64_t hw = wb[i];
+            if (h <= r) {
+                r = h;
+                key = hw;
+            } else if (h - r < 8) {
+                uint32_t d = h - r;
+                key = (key & (~0ull << (64 - 8 * d))) | (hw >> (8 * d));
+            }
+            rr[u0 + i] = r;
+            rk[u0 + i] = key;
+        }
     }
 }
 
