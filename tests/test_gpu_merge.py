@@ -49,7 +49,8 @@ def test_partition_matches_oracle(seed, n, p):
 
 @pytest.mark.parametrize("tree", [False, True])
 @pytest.mark.parametrize("seed,n,p,trunc", [(0, 800, 4, False), (1, 5000, 16, True), (2, 3000, 5, True),
-                                            (3, 30000, 16, False), (4, 7, 3, True), (5, 60000, 2, True)])
+                                            (3, 30000, 16, False), (4, 7, 3, True), (5, 60000, 2, True),
+                                            (6, 40000, 256, True), (7, 30000, 255, False), (8, 20000, 100, True)])
 def test_lcp_merge_matches_oracle(seed, n, p, trunc, tree):
     m = sss()
     ss = rand_set(seed, n)
