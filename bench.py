@@ -282,6 +282,7 @@ def main():
     dom = max(stats_all.items(), key=lambda kv: kv[1]["total_ms"])[0]
     D = int(dist_t.to(torch.int64).sum().item())
     Dapprox = int(approx.to(torch.int64).sum().item())
+    sum_lcp = int(lcp.to(torch.int64).sum().item())
 
     # timed region: events on the context stream, the dominant kernel timed too
     ctx.reset_stats()
@@ -383,7 +384,9 @@ def main():
                                          "DNData n/p = 1e5, as chars/s; other hardware, not a target",
                                  "pdms1_4_nodes_192_cores": 1.62e10, "pdms2_4_nodes_192_cores": 1.51e10,
                                  "pdms3_1024_nodes_49152_cores": 2.29e12},
-               "kernel_ms_per_step": {k: v["total_ms"] for k, v in stats_all.items()}}
+               "kernel_ms_per_step": {k: v["total_ms"] for k, v in stats_all.items()},
+               "stages": stage_rooflines({k: v["total_ms"] for k, v in stats_all.items()}, n, D, Dapprox, sum_lcp,
+                                         hbm)}
         if ws == 1 and args.workload == "all":
             del chars, offs, lens, perm, lcp, dist_t, approx
             out["batch"] = bench_batch(args, dev, ctx)
@@ -716,6 +719,32 @@ def algorithmic_bytes(kernel: str, n: int, N: int, D: int, Dapprox: int, launche
         "d_search": 32 * n / lps,
     }
     return float(models.get(kernel, 24 * n / lps))
+
+
+STAGE_OF = (("ls_", "A"), ("dist", "A"), ("pd_", "B"), ("c_", "C"), ("d2_", "D"), ("d_", "D"))
+
+
+def stage_rooflines(kernel_ms: dict, n: int, D: int, Dapprox: int, sum_lcp: int, peak_gbs: float) -> dict:
+    """Stage-level algorithmic-byte efficiency of one step: each
+    stage's kernel time (CUDA events, per step) against the bytes its step must
+    move at least.  A: D + 20n (distinguishing prefixes, views, perm and lcp)
+    plus 12n for dist; B: sum(approx) + 16n (prefix characters read once, one
+    key per string, approx); C: negligible (samples and p^2 searches); D: the
+    LCP-compressed records, about sum(approx) - sum(lcp) characters + 8n,
+    written by the scatter and read twice by the merge, plus 8n of output."""
+    ms = {"A": 0.0, "B": 0.0, "C": 0.0, "D": 0.0, "other": 0.0}
+    for k, v in kernel_ms.items():
+        st = next((s for pre, s in STAGE_OF if k.startswith(pre)), "other")
+        ms[st] += v
+    rec = max(0, Dapprox - sum_lcp) + 8 * n
+    algo = {"A": D + 32 * n, "B": Dapprox + 16 * n, "C": None, "D": 3 * rec + 8 * n, "other": None}
+    out = {}
+    for st, t in ms.items():
+        a = algo[st]
+        gbs = a / (t / 1e3) / 1e9 if (a is not None and t > 0) else None
+        out[st] = {"ms": t, "algorithmic_bytes": a, "achieved_gbs": gbs,
+                   "frac": gbs / peak_gbs if gbs is not None else None}
+    return out
 
 
 def known_traffic(kernel: str):
