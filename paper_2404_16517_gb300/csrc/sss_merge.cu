@@ -731,21 +731,35 @@ __global__ void k_d2_subspl(const BucketInfo* __restrict__ bi, uint32_t p, uint3
 }
 
 // sb[m*p+i] = number of strings of piece (bucket of m, i) that are <= subspl[m]
-// (one warp per search, warp-wide comparisons)
+// (one warp per search, warp-wide comparisons).  A bucket's sub-splitters are
+// sorted, so their bounds in a piece are too: phase 0 searches the whole piece
+// for every D2_BSTRIDE-th sub-splitter of the bucket (the anchors), phase 1
+// searches for the others only between the bounds of the anchors around them.
+constexpr uint32_t D2_BSTRIDE = 16;
+
 __global__ void k_d2_bounds(const uint32_t* __restrict__ run_perm, Strs S, const BucketInfo* __restrict__ bi,
                             uint32_t p, uint32_t nss, const uint32_t* __restrict__ pstart,
                             const uint32_t* __restrict__ psz, const uint32_t* __restrict__ subspl,
-                            uint32_t* __restrict__ sb) {
+                            uint32_t* __restrict__ sb, uint32_t phase) {
     uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (g >= nss * p) return;
     uint32_t m = g / p, i = g % p;
     uint32_t j = last_le(&bi[0].ss0, p, m, sizeof(BucketInfo) / 4, 0);
     while (j + 1 < p && bi[j + 1].ss0 <= m) ++j;
+    const uint32_t k = m - bi[j].ss0, nk = bi[j].nsb - 1;  // index among the bucket's nk sub-splitters
+    const bool anchor = (k + 1) % D2_BSTRIDE == 0;
+    if (anchor != (phase == 0)) return;
+    uint32_t a = 0, b = psz[j * p + i], la = 0, lb = 0;
+    if (!anchor) {
+        const uint32_t blk = (k + 1) / D2_BSTRIDE;
+        if (blk > 0) a = sb[(bi[j].ss0 + blk * D2_BSTRIDE - 1) * p + i];
+        const uint32_t kb = (blk + 1) * D2_BSTRIDE - 1;
+        if (kb < nk) b = sb[(bi[j].ss0 + kb) * p + i];
+    }
     uint32_t f = subspl[m];
     const uint8_t* fs = S.chars + S.offs[f];
     uint32_t fl = tlen(S, f);
     uint32_t q0 = pstart[j * p + i];
-    uint32_t a = 0, b = psz[j * p + i], la = 0, lb = 0;
     while (a < b) {
         uint32_t mid = (a + b) >> 1;
         uint32_t e = run_perm[q0 + mid];
@@ -1486,9 +1500,10 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
         SSS_TRY(sss_launch(ctx, "d2_subspl", k_d2_subspl, dim3((NSS + 255) / 256), dim3(256), 0,
                            (const BucketInfo*)b.binfo, p, NSS, (const uint32_t*)b.smp2, (const uint32_t*)b.s2perm,
                            b.subspl));
-        SSS_TRY(sss_launch(ctx, "d2_bounds", k_d2_bounds, dim3((NSS * p * 32 + 127) / 128), dim3(128), 0, run_perm, S,
-                           (const BucketInfo*)b.binfo, p, NSS, (const uint32_t*)b.pstart, (const uint32_t*)b.psz,
-                           (const uint32_t*)b.subspl, b.sb));
+        for (uint32_t phase = 0; phase < 2; ++phase)
+            SSS_TRY(sss_launch(ctx, "d2_bounds", k_d2_bounds, dim3((NSS * p * 32 + 127) / 128), dim3(128), 0,
+                               run_perm, S, (const BucketInfo*)b.binfo, p, NSS, (const uint32_t*)b.pstart,
+                               (const uint32_t*)b.psz, (const uint32_t*)b.subspl, b.sb, phase));
     }
     SSS_TRY(sss_launch(ctx, "d2_slices", k_d2_slices, dim3((nslices + 255) / 256), dim3(256), 0,
                        (const BucketInfo*)b.binfo, p, NSB, (const uint32_t*)b.sb, (const uint32_t*)b.psz, b.ssz));
