@@ -294,7 +294,7 @@ sss_status sss_dist_prefix_noalloc(const uint8_t* chars, uint64_t n_chars, const
 /* ------------------------------------------------------------------------ */
 /* Instrumentation: per-kernel launch counts and (when timing is enabled) device
  * time measured with CUDA events on the context's stream around each launch. */
-#define SSS_MAX_KERNELS 64
+#define SSS_MAX_KERNELS 128
 
 typedef struct sss_kernel_stat {
     const char* name;   /* static string */

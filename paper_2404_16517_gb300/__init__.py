@@ -30,7 +30,7 @@ SSS_FLAG_MERGE_TREE = 0x10
 SSS_FLAG_CHAR_SAMPLING = 0x20
 SSS_FLAG_GRAPH = 0x40
 SSS_KMAX_AUTO = 0xFFFFFFFF
-SSS_MAX_KERNELS = 64
+SSS_MAX_KERNELS = 128
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "device wait timed out",
           5: "input validation failed on the device", 6: "not implemented", 7: "workspace too small"}
