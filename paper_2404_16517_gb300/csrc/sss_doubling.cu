@@ -187,15 +187,51 @@ __global__ void __launch_bounds__(256) k_pd_lists(PdIn in, const uint32_t* __res
     }
 }
 
+// Fold words wa..wb-1 of the prefix of s (le characters: a last partial word is
+// zero-padded) into h, read as aligned 8-byte loads issued in batches of 8
+// (only words that hold a character of the prefix are loaded).
+__device__ __forceinline__ uint64_t fold_words(uint64_t h, const uint8_t* s, uint32_t wa, uint32_t wb, uint32_t le,
+                                               uint64_t B, uint64_t B2) {
+    if (wa >= wb) return h;
+    uintptr_t a0 = (uintptr_t)(s + 8 * wa);
+    const uint64_t* pw = reinterpret_cast<const uint64_t*>(a0 & ~uintptr_t(7));
+    const uint32_t sh = (uint32_t)(a0 & 7) * 8;
+    const uint32_t lim = le < 8 * wb ? le : 8 * wb;
+    const uint8_t* end = s + lim;
+    uint64_t prev = bswap64(__ldg(pw));
+    for (uint32_t w = wa; w < wb; w += 8) {
+        uint64_t buf[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint64_t* pi = pw + 1 + i;
+            buf[i] = reinterpret_cast<const uint8_t*>(pi) < end ? bswap64(__ldg(pi)) : 0ull;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (w + i >= wb) break;
+            uint64_t x = sh ? ((prev << sh) | (buf[i] >> (64 - sh))) : prev;
+            prev = buf[i];
+            uint32_t left = le - 8 * (w + i);
+            if (left < 8) x &= ~0ull << (8 * (8 - left));
+            h = fold_word(h, B, B2, x);
+        }
+        pw += 8;
+    }
+    return h;
+}
+
 // B1: keys of the reps.  Horner resumes from the L/2-prefix state of the
 // previous round: the rep's own state, or (for a position that starts a group
-// only from this round on) the state of its previous group start, which shares
-// that prefix.  States are double-buffered by round parity.
+// only from this round on) the state of its previous group start q', which
+// shares that prefix.  Such a position also shares its first minlcp[q]
+// characters with q': the whole words among them are read from q''s string,
+// which every member of the group reads (so from L2), and only the rest from
+// its own.  States are double-buffered by round parity.
 __global__ void k_pd_hash(PdIn in, const uint32_t* __restrict__ reps, uint32_t nreps, const uint32_t* __restrict__ lpos,
                           const uint64_t* __restrict__ hst_in, const uint32_t* __restrict__ hlen_in,
                           uint64_t* __restrict__ hst_out, uint32_t* __restrict__ hlen_out,
-                          const uint32_t* __restrict__ prevstart, uint64_t* __restrict__ K,
-                          uint32_t* __restrict__ V, uint64_t L, uint64_t B) {
+                          const uint32_t* __restrict__ prevstart, const uint32_t* __restrict__ minlcp,
+                          uint64_t* __restrict__ K, uint32_t* __restrict__ V, uint64_t L, uint64_t B) {
     uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nreps) return;
     uint32_t q = reps[j];
@@ -204,7 +240,8 @@ __global__ void k_pd_hash(PdIn in, const uint32_t* __restrict__ reps, uint32_t n
     uint32_t le = L < len ? (uint32_t)L : len;
     const uint8_t* str = in.chars + in.offs[s];
     uint64_t h = 0;
-    uint32_t w0 = 0;
+    uint32_t w0 = 0, wsh = 0;
+    const uint8_t* sstr = str;
     if (L >= 16) {
         uint32_t src = q;
         if (hlen_in[q] != (uint32_t)(L / 2) && prevstart) src = prevstart[q];
@@ -212,36 +249,17 @@ __global__ void k_pd_hash(PdIn in, const uint32_t* __restrict__ reps, uint32_t n
             h = hst_in[src];
             w0 = (uint32_t)(L / 16);
         }
-    }
-    uint32_t nw = (le + 7) / 8;
-    const uint64_t B2 = mulmod61(B, B);
-    if (w0 < nw) {
-        // words w0..nw-1 of the prefix, read as aligned 8-byte loads issued in
-        // batches of 8 (only words that hold a character of the prefix are loaded)
-        uintptr_t a0 = (uintptr_t)(str + 8 * w0);
-        const uint64_t* pw = reinterpret_cast<const uint64_t*>(a0 & ~uintptr_t(7));
-        const uint32_t sh = (uint32_t)(a0 & 7) * 8;
-        const uint8_t* end = str + le;
-        uint64_t prev = bswap64(__ldg(pw));
-        for (uint32_t w = w0; w < nw; w += 8) {
-            uint64_t buf[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const uint64_t* pi = pw + 1 + i;
-                buf[i] = reinterpret_cast<const uint8_t*>(pi) < end ? bswap64(__ldg(pi)) : 0ull;
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                if (w + i >= nw) break;
-                uint64_t x = sh ? ((prev << sh) | (buf[i] >> (64 - sh))) : prev;
-                prev = buf[i];
-                uint32_t left = le - 8 * (w + i);
-                if (left < 8) x &= ~0ull << (8 * (8 - left));
-                h = fold_word(h, B, B2, x);
-            }
-            pw += 8;
+        if (src != q && minlcp) {
+            const uint32_t ml = minlcp[q];
+            wsh = (ml < le ? ml : le) / 8;
+            sstr = in.chars + in.offs[ord_of(in, src)];
         }
     }
+    wsh = wsh > w0 ? wsh : w0;
+    uint32_t nw = (le + 7) / 8;
+    const uint64_t B2 = mulmod61(B, B);
+    h = fold_words(h, sstr, w0, wsh, 8 * wsh, B, B2);  // whole words shared with the group start
+    h = fold_words(h, str, wsh, nw, le, B, B2);
     hst_out[q] = h;
     hlen_out[q] = le;
     K[j] = smix64(h ^ ((uint64_t)le * GAMMA));
@@ -249,52 +267,89 @@ __global__ void k_pd_hash(PdIn in, const uint32_t* __restrict__ reps, uint32_t n
 }
 
 // prevstart[q] = last position q' <= q that starts a group in round k-1
-// (kstar(q') <= k-1): inclusive max-scan of flagged positions in tiles of 4096,
-// then the carry from earlier tiles.
+// (kstar(q') <= k-1), and minlcp[q] = min of run_lcp over (q', q], the number
+// of characters q shares with q' (all ones when q' = q).  One scan over the
+// pairs (last start + 1, min since it) with the operator
+//     (s1, m1) then (s2, m2) = s2 ? (s2, m2) : (s1, min(m1, m2)):
+// tiles of 4096 positions (4 per thread, warp shuffles, warp totals in shared
+// memory), then the carry of earlier tiles.
+struct PsPair {
+    uint32_t s;  // last group start + 1 (0: none yet)
+    uint32_t m;  // min run_lcp since it
+};
+__device__ __forceinline__ PsPair ps_then(PsPair a, PsPair b) {
+    return b.s ? b : PsPair{a.s, a.m < b.m ? a.m : b.m};
+}
+
 __global__ void __launch_bounds__(1024) k_pd_ps_tiles(PdIn in, uint32_t kprev, uint32_t kmin,
-                                                      uint32_t* __restrict__ out, uint32_t* __restrict__ tmax) {
+                                                      uint32_t* __restrict__ out_s, uint32_t* __restrict__ out_m,
+                                                      PsPair* __restrict__ tagg) {
     constexpr int ITEMS = 4;
-    __shared__ uint32_t sh_warp[32];
-    uint32_t base = blockIdx.x * 4096 + threadIdx.x * ITEMS;
-    uint32_t loc[ITEMS];
-    uint32_t m = 0;
+    __shared__ PsPair sh_w[32];
+    const uint32_t base = blockIdx.x * 4096 + threadIdx.x * ITEMS;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    PsPair loc[ITEMS];
+    PsPair t{0u, ~0u};
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        uint32_t q = base + i;
-        if (q < in.n && kstar_of(in, q, kmin) <= kprev) m = q + 1;  // +1: 0 means none
-        loc[i] = m;
+        const uint32_t q = base + i;
+        if (q < in.n) {
+            const bool start = kstar_of(in, q, kmin) <= kprev;
+            t = start ? PsPair{q + 1, ~0u} : ps_then(t, PsPair{0u, in.run_lcp[q]});
+        }
+        loc[i] = t;
     }
-    uint32_t incl = BlockScan<1024>::inclusive_max(m, sh_warp);
-    uint32_t prev = __shfl_up_sync(SSS_FULL, incl, 1);
-    __shared__ uint32_t sh_last[32];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 31) sh_last[w] = incl;
+    // inclusive scan of the thread totals within the warp
+    PsPair x = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        PsPair y{__shfl_up_sync(SSS_FULL, x.s, o), __shfl_up_sync(SSS_FULL, x.m, o)};
+        if (lane >= o) x = ps_then(y, x);
+    }
+    PsPair ex{__shfl_up_sync(SSS_FULL, x.s, 1), __shfl_up_sync(SSS_FULL, x.m, 1)};
+    if (lane == 0) ex = PsPair{0u, ~0u};
+    if (lane == 31) sh_w[w] = x;
     __syncthreads();
-    if (lane == 0) prev = w > 0 ? sh_last[w - 1] : 0;
+    if (w == 0) {
+        PsPair v = sh_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            PsPair y{__shfl_up_sync(SSS_FULL, v.s, o), __shfl_up_sync(SSS_FULL, v.m, o)};
+            if (lane >= o) v = ps_then(y, v);
+        }
+        sh_w[lane] = v;  // inclusive over warps
+    }
+    __syncthreads();
+    const PsPair pre = w > 0 ? ps_then(sh_w[w - 1], ex) : ex;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        uint32_t q = base + i;
-        if (q < in.n) out[q] = loc[i] > prev ? loc[i] : prev;
+        const uint32_t q = base + i;
+        if (q < in.n) {
+            const PsPair r = ps_then(pre, loc[i]);
+            out_s[q] = r.s;
+            out_m[q] = r.m;
+        }
     }
-    if (threadIdx.x == 1023) tmax[blockIdx.x] = incl;
+    if (threadIdx.x == 0) tagg[blockIdx.x] = sh_w[31];
 }
 
-__global__ void k_pd_ps_carry(uint32_t* __restrict__ tmax, uint32_t nt) {
+__global__ void k_pd_ps_carry(PsPair* __restrict__ tagg, uint32_t nt) {
     if (threadIdx.x != 0) return;
-    uint32_t run = 0;
+    PsPair run{0u, ~0u};
     for (uint32_t t = 0; t < nt; ++t) {
-        uint32_t v = tmax[t];
-        tmax[t] = run;  // exclusive: max over earlier tiles
-        run = v > run ? v : run;
+        const PsPair v = tagg[t];
+        tagg[t] = run;  // exclusive: the earlier tiles
+        run = ps_then(run, v);
     }
 }
 
-__global__ void k_pd_ps_apply(uint32_t n, uint32_t* __restrict__ out, const uint32_t* __restrict__ tmax) {
-    uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_pd_ps_apply(uint32_t n, uint32_t* __restrict__ out_s, uint32_t* __restrict__ out_m,
+                              const PsPair* __restrict__ tagg) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
-    uint32_t v = out[q], c = tmax[q / 4096];
-    v = v > c ? v : c;
-    out[q] = v ? v - 1 : q;  // no earlier start (cannot happen): itself
+    const PsPair r = ps_then(tagg[q / 4096], PsPair{out_s[q], out_m[q]});
+    out_s[q] = r.s ? r.s - 1 : q;  // no earlier start (cannot happen): itself
+    out_m[q] = r.s ? r.m : 0u;
 }
 
 // B2: bucket the keys by their top bits
@@ -553,7 +608,8 @@ struct PdBufs {
     uint32_t* hlen2;
     uint64_t* hst2;
     uint32_t* prevstart;
-    uint32_t* tmax;
+    uint32_t* minlcp;
+    PsPair* tagg;
     uint32_t* list_ks;
     uint32_t* list_kl;
     uint32_t* reps[2];
@@ -579,7 +635,8 @@ void carve_pd(Arena& ar, uint32_t n, PdBufs& b) {
     b.hlen2 = ar.take<uint32_t>(n);
     b.hst2 = ar.take<uint64_t>(n);
     b.prevstart = ar.take<uint32_t>(n);
-    b.tmax = ar.take<uint32_t>(n / 4096 + 2);
+    b.minlcp = ar.take<uint32_t>(n);
+    b.tagg = ar.take<PsPair>(n / 4096 + 2);
     b.list_ks = ar.take<uint32_t>(n);
     b.list_kl = ar.take<uint32_t>(n);
     b.reps[0] = ar.take<uint32_t>(n);
@@ -678,10 +735,10 @@ sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& sin, const uin
             if (run_lcp && k >= 4 && k > kmin && nnew > n / 16) {
                 uint32_t nt = (n + 4095) / 4096;
                 SSS_TRY(sss_launch(ctx, "pd_prevstart", k_pd_ps_tiles, dim3(nt), dim3(1024), 0, in, k - 1, kmin,
-                                   B.prevstart, B.tmax));
-                SSS_TRY(sss_launch(ctx, "pd_prevstart_carry", k_pd_ps_carry, dim3(1), dim3(32), 0, B.tmax, nt));
+                                   B.prevstart, B.minlcp, B.tagg));
+                SSS_TRY(sss_launch(ctx, "pd_prevstart_carry", k_pd_ps_carry, dim3(1), dim3(32), 0, B.tagg, nt));
                 SSS_TRY(sss_launch(ctx, "pd_prevstart_apply", k_pd_ps_apply, dim3((n + 255) / 256), dim3(256), 0, n,
-                                   B.prevstart, (const uint32_t*)B.tmax));
+                                   B.prevstart, B.minlcp, (const PsPair*)B.tagg));
                 ps = B.prevstart;
             }
             const bool odd = ((k - kmin) & 1u) != 0;
@@ -691,7 +748,8 @@ sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& sin, const uin
             uint32_t* hl_out = odd ? B.hlen : B.hlen2;
             SSS_TRY(sss_launch(ctx, "pd_hash", k_pd_hash, dim3((nreps + 255) / 256), dim3(256), 0, in, reps, nreps,
                                (const uint32_t*)B.lpos, (const uint64_t*)hs_in, (const uint32_t*)hl_in, hs_out,
-                               hl_out, ps, B.K, B.V, L, Bh));
+                               hl_out, ps, ps ? (const uint32_t*)B.minlcp : (const uint32_t*)nullptr, B.K, B.V, L,
+                               Bh));
             if (use_ht) {
                 uint32_t T = 1024;
                 while (T < 2ull * nreps) T <<= 1;
