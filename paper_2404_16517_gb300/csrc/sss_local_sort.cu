@@ -37,7 +37,7 @@ constexpr int WF_WARPS = 8;                     // group finishers: warps per CT
 constexpr int QUAD_W = 4;                       // segments of <= 4 strings: 4 lanes each, 8 per warp
 constexpr int TINY_T = 64, TINY_CAP = 64;       // segments of warp_cap+1 .. 64 strings
 constexpr int SM_T = 128, SM_CAP = 512;         // segments of 65 .. 512 strings
-constexpr int MED_T = 256, MED_CAP = 2048;      // segments of 513 .. cta_cap (<= 2048) strings
+constexpr int MED_T = 512, MED_CAP = 2048;      // segments of 513 .. cta_cap (<= 2048) strings, 2 CTAs per SM
 constexpr int BK_T = 512, BK_CAP = 4096;        // bucket sort CTA (bucket targets above BKS_CAP / 2)
 constexpr int BKS_T = 256, BKS_CAP = 2048;      // bucket sort CTA for targets <= BKS_CAP / 2 (4 CTAs per SM)
 constexpr int DIRECT_T = 1024, DIRECT_CAP = 8192;  // whole-segment sort CTA (segments <= direct_cap)
@@ -337,6 +337,18 @@ __device__ __forceinline__ void finish_segment(const Seg sg, const uint8_t* __re
 // clamped to count), one CTA at a time.
 template <int THREADS, int CAP>
 __global__ void __launch_bounds__(THREADS) k_finish(const Seg* __restrict__ segs, const uint32_t* __restrict__ d_count,
+                                                    uint32_t count, uint32_t* work, const uint8_t* __restrict__ chars,
+                                                    const uint64_t* __restrict__ offs,
+                                                    const uint32_t* __restrict__ lens, uint32_t* __restrict__ perm,
+                                                    uint32_t* __restrict__ lcp, unsigned* err) {
+    const uint32_t nseg = d_count ? min(*d_count, count) : count;
+    for (uint32_t i = cta_next_unit(work); i < nseg; i = cta_next_unit(work))
+        finish_segment<THREADS, CAP>(segs[i], chars, offs, lens, perm, lcp, err);
+}
+
+// k_finish held to two CTAs per SM (the 512-thread class: 63 registers)
+template <int THREADS, int CAP>
+__global__ void __launch_bounds__(THREADS, 2) k_finish2(const Seg* __restrict__ segs, const uint32_t* __restrict__ d_count,
                                                     uint32_t count, uint32_t* work, const uint8_t* __restrict__ chars,
                                                     const uint64_t* __restrict__ offs,
                                                     const uint32_t* __restrict__ lens, uint32_t* __restrict__ perm,
@@ -913,7 +925,7 @@ sss_status run_finishers(sss_ctx* ctx, const LsBufs& B, const uint32_t* d_cnt, u
     SSS_TRY(sss_launch(ctx, "ls_finish_small", k_finish<SM_T, SM_CAP>, dim3(gs), dim3(SM_T), finish_smem(SM_CAP),
                        (const Seg*)B.small, d_cnt ? d_cnt + 4 : (const uint32_t*)nullptr, nsmall, B.work + 6, in.chars,
                        in.offs, in.lens, perm, lcp, ctx->d_err));
-    SSS_TRY(sss_launch(ctx, "ls_finish_cta", k_finish<MED_T, MED_CAP>, dim3(gm), dim3(MED_T), finish_smem(MED_CAP),
+    SSS_TRY(sss_launch(ctx, "ls_finish_cta", k_finish2<MED_T, MED_CAP>, dim3(gm), dim3(MED_T), finish_smem(MED_CAP),
                        (const Seg*)B.med, d_cnt ? d_cnt + 1 : (const uint32_t*)nullptr, nmed, B.work + 2, in.chars,
                        in.offs, in.lens, perm, lcp, ctx->d_err));
     return SSS_OK;
@@ -932,7 +944,7 @@ static bool g_attr_done[64];
 
 static sss_status set_ls_attributes(sss_ctx* ctx) {
     if (!g_attr_done[ctx->device & 63]) {
-        SSS_CUDA(cudaFuncSetAttribute(k_finish<MED_T, MED_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SSS_CUDA(cudaFuncSetAttribute(k_finish2<MED_T, MED_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)finish_smem(MED_CAP)));
         SSS_CUDA(cudaFuncSetAttribute(k_finish<TINY_T, TINY_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)finish_smem(TINY_CAP)));
@@ -1166,7 +1178,7 @@ sss_status impl_finish_segments(sss_ctx* ctx, const Seg* tiny, uint32_t ntiny, c
     SSS_TRY(sss_launch(ctx, "ls_finish_tiny", k_finish<TINY_T, TINY_CAP>, dim3(std::min(ntiny, sm * 32)), dim3(TINY_T),
                        finish_smem(TINY_CAP), tiny, (const uint32_t*)nullptr, ntiny, work, in.chars, in.offs, in.lens,
                        perm, lcp, ctx->d_err));
-    SSS_TRY(sss_launch(ctx, "ls_finish_cta", k_finish<MED_T, MED_CAP>, dim3(std::min(nmed, sm * 4)), dim3(MED_T),
+    SSS_TRY(sss_launch(ctx, "ls_finish_cta", k_finish2<MED_T, MED_CAP>, dim3(std::min(nmed, sm * 4)), dim3(MED_T),
                        finish_smem(MED_CAP), med, (const uint32_t*)nullptr, nmed, work + 1, in.chars, in.offs, in.lens,
                        perm, lcp, ctx->d_err));
     return SSS_OK;
