@@ -708,7 +708,7 @@ def bench_suffix(args, dev, ctx):
 
 
 def algorithmic_bytes(kernel: str, n: int, N: int, D: int, Dapprox: int, launches_per_step: float) -> float:
-    """Minimum bytes a launch of `kernel` must move on this workload (DESIGN.md)."""
+    """Minimum bytes a launch of `kernel` must move on this workload."""
     lps = max(launches_per_step, 1.0)
     models = {
         # local sort: every string's distinguishing prefix plus its view and outputs
@@ -725,7 +725,7 @@ STAGE_OF = (("ls_", "A"), ("dist", "A"), ("pd_", "B"), ("c_", "C"), ("d2_", "D")
 
 
 def stage_rooflines(kernel_ms: dict, n: int, D: int, Dapprox: int, sum_lcp: int, peak_gbs: float) -> dict:
-    """Stage-level algorithmic-byte efficiency of one step (DESIGN.md): each
+    """Stage-level algorithmic-byte efficiency of one step: each
     stage's kernel time (CUDA events, per step) against the bytes its step must
     move at least.  A: D + 20n (distinguishing prefixes, views, perm and lcp)
     plus 12n for dist; B: sum(approx) + 16n (prefix characters read once, one

@@ -5,10 +5,11 @@
  * paper's order) with no blocking, fusion or reordering.  Citations name the
  * paper's section / lemma / appendix the function follows.
  *
- * Parity: the 64-bit prefix-hash values (oracle_prefix_key) are "parity
- * unpinned" -- the paper only asks for a random hash function; this file fixes
- * one by its definition (Karp-Rabin polynomial over P = 2^61-1 with a SplitMix64
- * finaliser).  Everything else is pinned by the tests.
+ * The paper only asks for a random hash function; this file fixes one by its
+ * definition (Karp-Rabin polynomial over P = 2^61-1 with a SplitMix64
+ * finaliser).  Its values are pinned by inverting the finaliser and checking
+ * the polynomial, its closed forms and its linearity; everything else is pinned
+ * by the tests as well.
  */
 #include "oracle.h"
 

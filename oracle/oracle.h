@@ -10,11 +10,11 @@
  * "String Properties and Input Format").  Where a truncation array is given,
  * string i is compared as its first trunc[i] characters (trunc[i] <= lens[i]).
  *
- * Parity status (see the design doc for the pins): sort, LCP array, dist, doubling,
- * sampling, splitters, bucket bounds and merge are pinned by tests; the 64-bit
- * prefix-hash values themselves (oracle_prefix_key) are "parity unpinned": the
- * paper fixes no hash function, so only its structure and its SplitMix64 part
- * are pinned.
+ * Parity status: sort, LCP array, dist, doubling, sampling, splitters, bucket
+ * bounds and merge are pinned by tests, and so are the 64-bit prefix-hash
+ * values (oracle_prefix_key): the paper fixes no hash function, and the one
+ * defined here is checked through the inverse of its finaliser against the
+ * Karp-Rabin polynomial it states.
  */
 #ifndef SSS_ORACLE_H
 #define SSS_ORACLE_H

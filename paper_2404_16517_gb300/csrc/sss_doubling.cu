@@ -823,6 +823,7 @@ constexpr size_t NA_OFF_TAB = NA_OFF_KEY + sizeof(uint64_t) * NA_MAXN;
 constexpr size_t NA_OFF_MARK = NA_OFF_TAB + sizeof(uint64_t) * NA_TSLOTS;
 constexpr size_t NA_BYTES = NA_OFF_MARK + NA_TSLOTS;
 constexpr int NA_T = 1024;
+static_assert((NA_TSLOTS & (NA_TSLOTS - 1)) == 0, "the fixed hash table must have a power-of-two slot count");
 
 // The scratch shared by every call on a device (contents persist between calls).
 static __device__ __align__(256) unsigned char g_pd_noalloc_scratch[NA_BYTES];
@@ -830,7 +831,8 @@ static __device__ __align__(256) unsigned char g_pd_noalloc_scratch[NA_BYTES];
 __global__ void __launch_bounds__(NA_T) k_pd_noalloc(const uint8_t* __restrict__ chars,
                                                      const uint64_t* __restrict__ offs,
                                                      const uint32_t* __restrict__ lens, uint32_t n, uint32_t kmin,
-                                                     uint32_t kmax, uint64_t B, uint32_t* __restrict__ out_approx,
+                                                     uint32_t kmax, uint64_t B, uint32_t tslots,
+                                                     uint32_t* __restrict__ out_approx,
                                                      unsigned char* __restrict__ scratch) {
     uint32_t* apos = reinterpret_cast<uint32_t*>(scratch + NA_OFF_APOS);
     uint32_t* hlen = reinterpret_cast<uint32_t*>(scratch + NA_OFF_HLEN);
@@ -839,7 +841,9 @@ __global__ void __launch_bounds__(NA_T) k_pd_noalloc(const uint8_t* __restrict__
     unsigned long long* tab = reinterpret_cast<unsigned long long*>(scratch + NA_OFF_TAB);
     uint8_t* mark = scratch + NA_OFF_MARK;
     __shared__ uint32_t sh_zero, sh_active;
-    const uint32_t tmask = NA_TSLOTS - 1;
+    // the table in use: tslots = the power of two >= 2n (<= NA_TSLOTS), so the
+    // per-round clear touches only the slots this call can fill
+    const uint32_t tmask = tslots - 1;
     // every call starts from a clean state: the array keeps the previous call's contents
     for (uint32_t i = threadIdx.x; i < n; i += NA_T) {
         apos[i] = ACTIVE;
@@ -848,7 +852,7 @@ __global__ void __launch_bounds__(NA_T) k_pd_noalloc(const uint8_t* __restrict__
     __syncthreads();
     for (uint32_t k = kmin; k <= kmax; ++k) {
         const uint64_t L = 1ull << k;
-        for (uint32_t t = threadIdx.x; t < NA_TSLOTS; t += NA_T) {
+        for (uint32_t t = threadIdx.x; t < tslots; t += NA_T) {
             tab[t] = 0ull;
             mark[t] = 0;
         }
@@ -954,7 +958,9 @@ extern "C" sss_status sss_dist_prefix_noalloc(const uint8_t* chars, uint64_t n_c
                    ? SSS_OK
                    : SSS_ERR_CUDA;
     }
+    uint32_t tslots = 64;
+    while (tslots < 2 * n) tslots *= 2;  // n <= NA_MAXN, so tslots <= NA_TSLOTS
     k_pd_noalloc<<<1, NA_T, 0, static_cast<cudaStream_t>(cuda_stream)>>>(chars, offsets, lengths, n, kmin, kmax, Bh,
-                                                                         out_approx, scratch);
+                                                                         tslots, out_approx, scratch);
     return cudaGetLastError() == cudaSuccess ? SSS_OK : SSS_ERR_CUDA;
 }

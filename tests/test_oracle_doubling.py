@@ -10,7 +10,7 @@
       approx = len                                     otherwise,
   with dist taken from an all-pairs brute force or from Python's own sort.
 * The invariant dist <= approx <= min(2*dist, len) (kmin = 0, kmax large).
-The 64-bit key values themselves are parity unpinned (no published hash).
+The 64-bit key values themselves are pinned in test_oracle_hash.py.
 """
 import os
 import random

@@ -1,7 +1,10 @@
 """The allocation-free doubling entry point (for callers that cannot allocate
 device memory: it keeps its state in a fixed device array inside libsss.so)
-gives the same approximate distinguishing prefixes as sss_dist_prefix, on two
-calls in a row (the second call must not see leftovers of the first).
+gives the same approximate distinguishing prefixes as sss_dist_prefix and as
+the oracle, on two calls in a row (the second call must not see leftovers of
+the first), for several round ranges: the default one, a finite kmax that
+leaves strings unretired, a kmin >= 4 whose first round has no hash state to
+resume from, and kmin > kmax (no rounds at all).
 
 Collected last on purpose: if it fails, every other test has already run."""
 import ctypes as C
@@ -11,6 +14,7 @@ import numpy as np
 import pytest
 
 import datagen
+import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -24,27 +28,46 @@ def _sets():
             datagen.config2(n=4194304, count=65536)]
 
 
+KRANGES = [(0, None), (0, 3), (5, None), (4, 2)]
+
+
+def _call(m, chars, offs, lens, n, prm, out):
+    return m.lib().sss_dist_prefix_noalloc(C.c_void_p(chars.data_ptr()), chars.numel(), C.c_void_p(offs.data_ptr()),
+                                           C.c_void_p(lens.data_ptr()), n, C.byref(prm), C.c_void_p(out.data_ptr()),
+                                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+@pytest.mark.parametrize("kr", KRANGES, ids=lambda k: f"k{k[0]}-{'auto' if k[1] is None else k[1]}")
 @pytest.mark.parametrize("idx", [0, 1, 2])
-def test_noalloc_matches_sss_dist_prefix_twice(idx):
+def test_noalloc_matches_sss_dist_prefix_and_oracle_twice(idx, kr):
     import paper_2404_16517_gb300 as m
     ss = _sets()[idx]
     chars, offs, lens = m.to_device(ss)
     n = ss.n
-    prm = m.params(kmin=0, kmax=m.SSS_KMAX_AUTO, hash_seed=7)
+    kmin, kmax = kr
+    prm = m.params(kmin=kmin, kmax=m.SSS_KMAX_AUTO if kmax is None else kmax, hash_seed=7)
     want = m.sss_dist_prefix(chars, offs, lens, None, None, 1, prm)  # the allocating entry point
     m.context().sync()
-    want = want.cpu().numpy()
-    lib = m.lib()
-    stream = torch.cuda.current_stream().cuda_stream
+    want = want.cpu().numpy().view(np.uint32)
+    okmax = oracle.default_kmax(ss) if kmax is None else kmax
+    want_oracle = oracle.doubling(ss, kmin, okmax, 7)
+    assert np.array_equal(want, want_oracle), "sss_dist_prefix differs from the oracle"
     for call in range(2):
         out = torch.full((n,), -1, dtype=torch.int32, device="cuda")
-        st = lib.sss_dist_prefix_noalloc(C.c_void_p(chars.data_ptr()), chars.numel(), C.c_void_p(offs.data_ptr()),
-                                         C.c_void_p(lens.data_ptr()), n, C.byref(prm), C.c_void_p(out.data_ptr()),
-                                         C.c_void_p(stream))
+        st = _call(m, chars, offs, lens, n, prm, out)
         assert st == 0, f"call {call}: status {st}"
         torch.cuda.synchronize()
-        got = out.cpu().numpy()
-        assert np.array_equal(got, want), f"call {call}: differs at {np.flatnonzero(got != want)[:5]}"
+        got = out.cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, want_oracle), f"call {call}: differs at {np.flatnonzero(got != want_oracle)[:5]}"
+
+
+def test_noalloc_binding_wrapper_matches_oracle():
+    import paper_2404_16517_gb300 as m
+    ss = _sets()[1]
+    chars, offs, lens = m.to_device(ss)
+    got = m.sss_dist_prefix_noalloc(chars, offs, lens, m.params(hash_seed=3))
+    torch.cuda.synchronize()
+    assert np.array_equal(m.u32(got), oracle.doubling(ss, 0, oracle.default_kmax(ss), 3))
 
 
 def test_noalloc_rejects_too_many_strings():
@@ -58,3 +81,5 @@ def test_noalloc_rejects_too_many_strings():
                                          C.c_void_p(lens.data_ptr()), n, None, C.c_void_p(out.data_ptr()),
                                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == 1  # SSS_ERR_INVALID_ARG: beyond the fixed capacity, nothing enqueued
+    with pytest.raises(ValueError):
+        m.sss_dist_prefix_noalloc(chars, offs, lens)
