@@ -32,7 +32,8 @@ sys.path.insert(0, ROOT)
 METRIC = "sorted chars/s and strings/s on 1 GB300 (% of HBM roofline); p50/p99 request latency"
 WORKLOAD = "pdms_4194304x500_AZ_T64_shared242_p16"
 N_FULL, LEN, P = 4194304, 500, 16
-CPU_SAMPLE = 1 << 19  # strings timed on the oracle
+CPU_SAMPLE = 1 << 17  # strings of the CPU-baseline sample (both oracle modes)
+REF_SAMPLE = 1 << 19  # strings per step of the reference arm (all host cores)
 
 
 def peaks():
@@ -135,66 +136,109 @@ def dist_env():
 
 
 # ---------------------------------------------------------------------------
-def run_reference(args, ws, rank):
-    """The oracle (plain C, single thread) on a bounded sample of the workload."""
-    if rank != 0:
-        return 0
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the report."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_sample(n: int):
+    """The first n strings of the full-pipeline workload, from the same
+    generator the GPU run uses (device generator when a GPU is present)."""
     import numpy as np
 
     import datagen
-    import oracle
-
-    n = args.cpu_sample
     try:
         import torch
         import datagen.cuda as dgc
         if torch.cuda.is_available():
             c, o, l = dgc.config2(N_FULL, 0, n)
-            ss = datagen.StringSet(c.cpu().numpy(), o.cpu().numpy().view(np.uint64), l.cpu().numpy().view(np.uint32))
-        else:
-            raise RuntimeError
+            return datagen.StringSet(c.cpu().numpy(), o.cpu().numpy().view(np.uint64),
+                                     l.cpu().numpy().view(np.uint32))
     except Exception:
-        ss = datagen.config2(N_FULL, 0, n)
+        pass
+    return datagen.config2(N_FULL, 0, n)
+
+
+def _time_runs(fn, runs: int, warm: int = 1):
+    """The paper's timing rule: `warm` untimed runs, then the mean of `runs` runs."""
+    for _ in range(warm):
+        fn()
+    ts = []
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        fn()
+        ts.append(time.perf_counter() - t0)
+    return statistics.mean(ts), ts
+
+
+def cpu_baseline(n: int, runs: int = 5):
+    """The oracle pipeline (p = 16, v = 2, k = 0..9) on the host cores, two
+    modes on the same sample: one thread (the definition) and every core
+    (partitions, key ranges and buckets shared out among threads; the reported
+    baseline).  Each is one warm-up run, then the mean of `runs` runs."""
+    import oracle
+    ss = _oracle_sample(n)
+    cores = os.cpu_count() or 1
+    t1, _ = _time_runs(lambda: oracle.pdms(ss, P, 2, 0, 9, 0), runs)
+    tn, _ = _time_runs(lambda: oracle.pdms_parallel(ss, P, 2, 0, 9, 0, nthreads=cores), runs)
+    chars = n * LEN
+    return {"value": chars / tn, "unit": "chars/s", "cores": cores, "kind": "oracle",
+            "strings_per_s": n / tn, "cpu_model": cpu_model(),
+            "sample": f"first {n} of the {N_FULL} strings (same generator), p={P}, v=2, k=0..9; "
+                      f"one warm-up then the mean of {runs} runs per mode",
+            "single_thread": {"value": chars / t1, "unit": "chars/s", "cores": 1, "s_per_run": t1},
+            "all_cores": {"value": chars / tn, "unit": "chars/s", "cores": cores, "s_per_run": tn}}
+
+
+def run_reference(args, ws, rank):
+    """The oracle pipeline on every host core, on a bounded sample of the
+    workload (rank 0 only; other ranks exit without work)."""
+    if rank != 0:
+        return 0
+    import oracle
+
+    n = args.cpu_sample
+    ss = _oracle_sample(n)
+    cores = os.cpu_count() or 1
     times = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.pdms(ss, P, 2, 0, 9, 0)
+        oracle.pdms_parallel(ss, P, 2, 0, 9, 0, nthreads=cores)
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(dt)
         if s == 0 and args.steps + args.warmup > 1 and dt * (args.steps + args.warmup) > 240:
             # keep the whole reference run within a few minutes
             args.steps = max(1, int(240 // dt) - args.warmup)
-    t = statistics.median(times)
+    t = statistics.mean(times)
     chars = n * LEN
     value = chars / t
+    sample = (f"first {n} of the {N_FULL} strings (same generator), p={P}; one oracle PDMS pass per step on "
+              f"{cores} host threads; mean of the timed steps")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "chars/s", "n_gpus": ws,
            "steps": len(times), "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
            "strings_per_s": n / t,
            "config": {"workload": WORKLOAD, "sample_strings": n, "partitions": P},
-           "cpu_baseline": {"value": value, "unit": "chars/s", "cores": 1, "kind": "oracle",
-                            "sample": f"first {n} of the {N_FULL} strings (same generator), p={P}, one "
-                                      f"single-threaded oracle PDMS pass per step"},
+           "cpu_baseline": {"value": value, "unit": "chars/s", "cores": cores, "kind": "oracle", "sample": sample,
+                            "cpu_model": cpu_model()},
            "e2e": {"value": value, "unit": "chars/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
-
-
-def cpu_baseline(n: int):
-    import numpy as np
-
-    import datagen
-    import datagen.cuda as dgc
-    import oracle
-    c, o, l = dgc.config2(N_FULL, 0, n)
-    ss = datagen.StringSet(c.cpu().numpy(), o.cpu().numpy().view(np.uint64), l.cpu().numpy().view(np.uint32))
-    t0 = time.perf_counter()
-    oracle.pdms(ss, P, 2, 0, 9, 0)
-    dt = time.perf_counter() - t0
-    return {"value": n * LEN / dt, "unit": "chars/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {n} of the {N_FULL} strings (same generator), p={P}, single-threaded oracle PDMS, "
-                      f"{dt:.1f} s"}
 
 
 def main():
@@ -205,12 +249,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_FULL)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE)
+    ap.add_argument("--cpu-sample", type=int, default=None,
+                    help=f"oracle sample in strings (default {CPU_SAMPLE}; {REF_SAMPLE} for --impl reference)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--breakdown", action="store_true", help="per-kernel times to stderr")
     ap.add_argument("--merge-ms", type=int, default=0, help="merge segment spacing (0 = library default)")
     ap.add_argument("--p", type=int, default=P, help="partitions (profiling of smaller cases)")
-    ap.add_argument("--workload", default="all", choices=["all", "pdms", "batch", "serve", "charsample", "suffix"])
+    ap.add_argument("--workload", default="all",
+                    choices=["all", "pdms", "batch", "serve", "charsample", "suffix", "config1", "config3"])
     ap.add_argument("--batch-instances", type=int, default=4096)
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner (default knobs)")
     ap.add_argument("--no-graph", action="store_true", help="batch: host-driven round loop only")
@@ -225,6 +271,8 @@ def main():
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, local = dist_env()
+    if args.cpu_sample is None:
+        args.cpu_sample = REF_SAMPLE if args.impl == "reference" else CPU_SAMPLE
     if args.impl == "reference":
         return run_reference(args, ws, rank)
 
@@ -245,9 +293,10 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    if args.workload in ("batch", "serve", "charsample", "suffix"):
+    if args.workload in ("batch", "serve", "charsample", "suffix", "config1", "config3"):
         ctx = sss.context(local)
-        res = {"batch": bench_batch, "charsample": bench_charsample, "suffix": bench_suffix}.get(args.workload, None)
+        res = {"batch": bench_batch, "charsample": bench_charsample, "suffix": bench_suffix,
+               "config1": bench_config1, "config3": bench_config3}.get(args.workload, None)
         res = res(args, dev, ctx) if res else bench_serve(args, dev)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "n_gpus": ws, **res}), flush=True)
@@ -394,6 +443,10 @@ def main():
             out["char_sampling"] = bench_charsample(args, dev, ctx)
             torch.cuda.empty_cache()
             out["suffix_sort"] = bench_suffix(args, dev, ctx)
+            torch.cuda.empty_cache()
+            out["config1_plain"] = bench_config1(args, dev, ctx)
+            torch.cuda.empty_cache()
+            out["config3_suffixes"] = bench_config3(args, dev, ctx)
             torch.cuda.empty_cache()
             out["serving"] = bench_serve(args, dev)
             out["p50_ms"] = out["serving"].get("p50_ms")
@@ -705,6 +758,92 @@ def bench_suffix(args, dev, ctx):
     return {"workload": "suffix_array_markov_order2_2^22_sigma64", "text_bytes": n, "ms_per_step": ms,
             "suffixes_per_s": n / (ms / 1e3), "mean_lcp": float(l64.float().mean().item()),
             "max_lcp": int(l64.max().item()), "steps": args.steps}
+
+
+def bench_sort_config(args, dev, ctx, workload: str, chars, offs, lens, p: int, note: str, steps: int = 20):
+    """Time sss_sort on one more string set (a sub-line of the JSON): L2
+    flushed (a 256 MB write) before every step, each step timed by its own CUDA
+    events on the context stream, the dominant kernel's roofline and the
+    stage-level efficiencies as for the headline."""
+    import torch
+
+    import paper_2404_16517_gb300 as sss
+    n = lens.numel()
+    N = int(lens.to(torch.int64).sum().item())
+    prm = sss.params()
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp = torch.empty(n, dtype=torch.int32, device=dev)
+    dist_t = torch.empty(n, dtype=torch.int32, device=dev)
+    approx = torch.empty(n, dtype=torch.int32, device=dev) if p > 1 else None
+
+    def step():
+        sss.sss_sort(chars, offs, lens, p, prm, perm, lcp, out_dist=dist_t, out_approx=approx, ctx=ctx)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    ctx.set_timing(True, "")
+    step()
+    torch.cuda.synchronize()
+    stats_all = ctx.kernel_stats()
+    ctx.set_timing(False)
+    dom = max(stats_all.items(), key=lambda kv: kv[1]["total_ms"])[0]
+    D = int(dist_t.to(torch.int64).sum().item())
+    Dapprox = int(approx.to(torch.int64).sum().item()) if approx is not None else D
+    sum_lcp = int(lcp.to(torch.int64).sum().item())
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    ctx.reset_stats()
+    ctx.set_timing(True, dom)
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(st)
+        step()
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
+    stats = ctx.kernel_stats()
+    ctx.set_timing(False)
+    ms_step = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    hbm, peak_kind = peaks()
+    dstat = stats.get(dom, {"launches": 0, "total_ms": 0.0, "timed": 0})
+    avg_ms = dstat["total_ms"] / max(1, dstat["timed"])
+    algo = algorithmic_bytes(dom, n, N, D, Dapprox, dstat["launches"] / max(1, steps))
+    achieved = algo / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+    launches = sum(v["launches"] for v in stats.values()) / steps
+    return {"workload": workload, "strings": n, "chars": N, "partitions": p, "steps": steps,
+            "ms_per_step": ms_step, "chars_per_s": N / (ms_step / 1e3), "strings_per_s": n / (ms_step / 1e3),
+            "D_over_N": D / max(1, N), "approx_over_N": Dapprox / max(1, N), "gpu_launches_per_step": launches,
+            "l2": note,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo,
+                         "avg_launch_ms": avg_ms},
+            "kernel_ms_per_step": {k: v["total_ms"] for k, v in stats_all.items()},
+            "stages": stage_rooflines({k: v["total_ms"] for k, v in stats_all.items()}, n, D, Dapprox, sum_lcp,
+                                      hbm)}
+
+
+def bench_config1(args, dev, ctx):
+    """65,536 strings x 100 chars (4 templates sharing 42 chars), p = 1: plain
+    local sort with LCP array and exact dist."""
+    import datagen.cuda as dgc
+    chars, offs, lens = dgc.config1()
+    return bench_sort_config(args, dev, ctx, "plain_65536x100_AZ_T4_shared42_p1", chars, offs, lens, 1,
+                             "inputs (6.6 MB) fit in L2: L2 flushed by a 256 MB write before every step", steps=50)
+
+
+def bench_config3(args, dev, ctx):
+    """2,097,152 suffixes (length <= 256) at distinct random offsets of a
+    2^22-byte order-2 Markov text over 64 symbols, p = 64: the full pipeline."""
+    import datagen
+    import paper_2404_16517_gb300 as sss
+    ss = datagen.config3()
+    chars, offs, lens = sss.to_device(ss, dev)
+    return bench_sort_config(args, dev, ctx, "suffixes_2097152_of_markov2_2^22_sigma64_max256_p64", chars, offs,
+                             lens, 64, "the 4 MiB text and the 25 MB of views fit in L2: L2 flushed by a 256 MB "
+                                       "write before every step", steps=20)
 
 
 def algorithmic_bytes(kernel: str, n: int, N: int, D: int, Dapprox: int, launches_per_step: float) -> float:

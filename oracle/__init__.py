@@ -21,19 +21,20 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_PAR = os.path.join(_HERE, "oracle_par.c")
 _HDR = os.path.join(_HERE, "oracle.h")
 _SO = os.path.join(_HERE, "liboracle.so")
 UINT32_MAX = 0xFFFFFFFF
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so with gcc (plain C, -O2)."""
+    """Compile oracle.c and oracle_par.c into liboracle.so with gcc (plain C, -O2)."""
     stale = (not os.path.exists(_SO) or
-             os.path.getmtime(_SO) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+             os.path.getmtime(_SO) < max(os.path.getmtime(f) for f in (_SRC, _SRC_PAR, _HDR)))
     if force or stale:
         fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
         os.close(fd)
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-pthread", "-shared", "-fPIC", "-o", tmp, _SRC, _SRC_PAR])
         os.replace(tmp, _SO)
     return _SO
 
@@ -68,6 +69,9 @@ def lib():
             "oracle_bounds": (None, [P8, P64, P32, P32, P32, u32, u32, P32, P32]),
             "oracle_merge": (None, [P8, P64, P32, P32, P32, u32, u32, P32, P32, P32]),
             "oracle_check_sorted": (u32, [P8, P64, P32, P32, P32, u32]),
+            "oracle_bounds_row": (None, [P8, P64, P32, P32, P32, u32, u32, P32, u32, P32]),
+            "oracle_merge_bucket": (u32, [P8, P64, P32, P32, P32, u32, u32, P32, u32, P32]),
+            "oracle_pdms_parallel": (C.c_int, [P8, P64, P32, u32, u32, u32, u32, u32, u64, u32, P32, P32, P32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -235,6 +239,25 @@ def pdms(ss, p: int, v: int = 2, kmin: int = 0, kmax: int | None = None, seed: i
     perm, lcp = merge(ss, run_perm, p, bnd, approx)
     return dict(run_perm=run_perm, run_lcp=run_lcp, approx=approx, samples=smp,
                 sorted_samples=sorted_smp, splitters=spl, bounds=bnd, perm=perm, lcp=lcp)
+
+
+def pdms_parallel(ss, p: int, v: int = 2, kmin: int = 0, kmax: int | None = None, seed: int = 0,
+                  nthreads: int | None = None):
+    """The same pipeline as pdms() (string-based sampling) on nthreads host
+    threads (default: every core); returns (perm, lcp, approx), equal to pdms()'s."""
+    if kmax is None:
+        kmax = default_kmax(ss)
+    if nthreads is None:
+        nthreads = os.cpu_count() or 1
+    c, o, l = _views(ss)
+    perm = np.empty(ss.n, np.uint32)
+    lcp = np.empty(ss.n, np.uint32)
+    approx = np.empty(ss.n, np.uint32)
+    rc = lib().oracle_pdms_parallel(_p(c), _p(o), _p(l), ss.n, p, v, kmin, kmax, seed, nthreads, _p(perm), _p(lcp),
+                                    _p(approx))
+    if rc != 0:
+        raise RuntimeError("oracle_pdms_parallel: a thread could not be started")
+    return perm, lcp, approx
 
 
 def default_kmax(ss) -> int:

@@ -353,56 +353,67 @@ void oracle_splitters(const uint8_t* chars, const uint64_t* offs, const uint32_t
 /* Buckets (Section 3, step 1): B_i^j = { s in S_i : f_j < s <= f_{j+1} } with
  * f_0 = -inf and f_p = +inf; bounds[i][j] counts the strings of run i that are
  * <= f_j (string order only, so equal strings share a bucket). */
+void oracle_bounds_row(const uint8_t* chars, const uint64_t* offs, const uint32_t* lens,
+                       const uint32_t* trunc, const uint32_t* run_perm, uint32_t n, uint32_t p,
+                       const uint32_t* splitters, uint32_t i, uint32_t* bounds) {
+    uint32_t lo = oracle_part_lo(n, p, i), hi = oracle_part_lo(n, p, i + 1);
+    uint32_t* b = bounds + (size_t)i * (p + 1);
+    b[0] = 0;
+    b[p] = hi - lo;
+    for (uint32_t j = 1; j < p; ++j) {
+        uint32_t f = splitters[j - 1];
+        uint32_t c = 0;
+        if (f != UINT32_MAX) {
+            for (uint32_t q = lo; q < hi; ++q)
+                if (oracle_cmp_str(chars, offs, lens, trunc, run_perm[q], f) <= 0) ++c;
+        }
+        b[j] = c;
+    }
+}
+
 void oracle_bounds(const uint8_t* chars, const uint64_t* offs, const uint32_t* lens,
                    const uint32_t* trunc, const uint32_t* run_perm, uint32_t n, uint32_t p,
                    const uint32_t* splitters, uint32_t* bounds) {
-    for (uint32_t i = 0; i < p; ++i) {
-        uint32_t lo = oracle_part_lo(n, p, i), hi = oracle_part_lo(n, p, i + 1);
-        uint32_t* b = bounds + (size_t)i * (p + 1);
-        b[0] = 0;
-        b[p] = hi - lo;
-        for (uint32_t j = 1; j < p; ++j) {
-            uint32_t f = splitters[j - 1];
-            uint32_t c = 0;
-            if (f != UINT32_MAX) {
-                for (uint32_t q = lo; q < hi; ++q)
-                    if (oracle_cmp_str(chars, offs, lens, trunc, run_perm[q], f) <= 0) ++c;
-            }
-            b[j] = c;
-        }
-    }
+    for (uint32_t i = 0; i < p; ++i) oracle_bounds_row(chars, offs, lens, trunc, run_perm, n, p, splitters, i, bounds);
 }
 
 /* Merging (Section 3, step 3): each bucket receives one sorted piece from every
  * run; the pieces are merged (here by repeatedly taking the smallest head, the
  * lower run winning ties) and the buckets are concatenated in order. */
-void oracle_merge(const uint8_t* chars, const uint64_t* offs, const uint32_t* lens,
-                  const uint32_t* trunc, const uint32_t* run_perm, uint32_t n, uint32_t p,
-                  const uint32_t* bounds, uint32_t* out_perm, uint32_t* out_lcp) {
+uint32_t oracle_merge_bucket(const uint8_t* chars, const uint64_t* offs, const uint32_t* lens,
+                             const uint32_t* trunc, const uint32_t* run_perm, uint32_t n, uint32_t p,
+                             const uint32_t* bounds, uint32_t j, uint32_t* out) {
     uint32_t* head = (uint32_t*)malloc((size_t)p * sizeof(uint32_t));
     uint32_t* end = (uint32_t*)malloc((size_t)p * sizeof(uint32_t));
     uint32_t o = 0;
-    for (uint32_t j = 0; j < p; ++j) {
-        for (uint32_t i = 0; i < p; ++i) {
-            uint32_t lo = oracle_part_lo(n, p, i);
-            head[i] = lo + bounds[(size_t)i * (p + 1) + j];
-            end[i] = lo + bounds[(size_t)i * (p + 1) + j + 1];
-        }
-        for (;;) {
-            int best = -1;
-            for (uint32_t i = 0; i < p; ++i) {
-                if (head[i] >= end[i]) continue;
-                if (best < 0 ||
-                    oracle_cmp_str(chars, offs, lens, trunc, run_perm[head[i]], run_perm[head[best]]) < 0)
-                    best = (int)i;
-            }
-            if (best < 0) break;
-            out_perm[o++] = run_perm[head[best]++];
-        }
+    for (uint32_t i = 0; i < p; ++i) {
+        uint32_t lo = oracle_part_lo(n, p, i);
+        head[i] = lo + bounds[(size_t)i * (p + 1) + j];
+        end[i] = lo + bounds[(size_t)i * (p + 1) + j + 1];
     }
-    oracle_lcp_array(chars, offs, lens, NULL, out_perm, o, out_lcp);
+    for (;;) {
+        int best = -1;
+        for (uint32_t i = 0; i < p; ++i) {
+            if (head[i] >= end[i]) continue;
+            if (best < 0 ||
+                oracle_cmp_str(chars, offs, lens, trunc, run_perm[head[i]], run_perm[head[best]]) < 0)
+                best = (int)i;
+        }
+        if (best < 0) break;
+        out[o++] = run_perm[head[best]++];
+    }
     free(head);
     free(end);
+    return o;
+}
+
+void oracle_merge(const uint8_t* chars, const uint64_t* offs, const uint32_t* lens,
+                  const uint32_t* trunc, const uint32_t* run_perm, uint32_t n, uint32_t p,
+                  const uint32_t* bounds, uint32_t* out_perm, uint32_t* out_lcp) {
+    uint32_t o = 0;
+    for (uint32_t j = 0; j < p; ++j)
+        o += oracle_merge_bucket(chars, offs, lens, trunc, run_perm, n, p, bounds, j, out_perm + o);
+    oracle_lcp_array(chars, offs, lens, NULL, out_perm, o, out_lcp);
 }
 
 uint32_t oracle_check_sorted(const uint8_t* chars, const uint64_t* offs, const uint32_t* lens,

@@ -105,6 +105,25 @@ void oracle_bounds(const uint8_t* chars, const uint64_t* offs, const uint32_t* l
                    const uint32_t* trunc, const uint32_t* run_perm, uint32_t n, uint32_t p,
                    const uint32_t* splitters, uint32_t* bounds);
 
+/* One row of oracle_bounds: the counts of run i (bounds + i*(p+1)). */
+void oracle_bounds_row(const uint8_t* chars, const uint64_t* offs, const uint32_t* lens,
+                       const uint32_t* trunc, const uint32_t* run_perm, uint32_t n, uint32_t p,
+                       const uint32_t* splitters, uint32_t i, uint32_t* bounds);
+
+/* One bucket of oracle_merge: bucket j's merged indices into out (returns how many). */
+uint32_t oracle_merge_bucket(const uint8_t* chars, const uint64_t* offs, const uint32_t* lens,
+                             const uint32_t* trunc, const uint32_t* run_perm, uint32_t n, uint32_t p,
+                             const uint32_t* bounds, uint32_t j, uint32_t* out);
+
+/* The whole pipeline (local sorts, doubling, string-based sampling with v,
+ * splitters, bounds, merge of the approx-truncated strings) on nthreads host
+ * threads: partitions, key ranges and buckets are shared out among them.  Every
+ * step calls the single-threaded functions above on its share, so the outputs
+ * equal theirs.  Returns 0, or -1 if a thread could not be started. */
+int oracle_pdms_parallel(const uint8_t* chars, const uint64_t* offs, const uint32_t* lens, uint32_t n,
+                         uint32_t p, uint32_t v, uint32_t kmin, uint32_t kmax, uint64_t seed, uint32_t nthreads,
+                         uint32_t* out_perm, uint32_t* out_lcp, uint32_t* out_approx);
+
 /* Merge: bucket j = concatenation over runs i of run_i[bounds[i][j], bounds[i][j+1]);
  * each bucket is merged by repeatedly taking the smallest head (ties: lower run);
  * buckets are emitted in order.  out_lcp is the full-string LCP array. */
