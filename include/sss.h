@@ -45,7 +45,8 @@ typedef enum sss_status {
     SSS_ERR_INVALID_ARG = 1,   /* bad pointer/size/parameter; nothing was enqueued */
     SSS_ERR_OOM = 2,           /* device or pinned host allocation failed */
     SSS_ERR_CUDA = 3,          /* a CUDA runtime call failed (see sss_last_error) */
-    SSS_ERR_TIMEOUT = 4,       /* a bounded device-side wait ran out */
+    SSS_ERR_TIMEOUT = 4,       /* reserved: a bounded device-side wait ran out (no call
+                                  of this version waits on the device) */
     SSS_ERR_DEVICE_CHECK = 5,  /* SSS_CHECKED validation found bad input */
     SSS_ERR_UNIMPLEMENTED = 6, /* the requested mode is not built */
     SSS_ERR_WORKSPACE = 7      /* caller-supplied workspace is too small */
@@ -130,14 +131,20 @@ const char* sss_last_error(sss_ctx* ctx);
 /* ------------------------------------------------------------------------ */
 /* Stage A -- local string sort with LCP output (Section 3, "Initialization":
  * each PE sorts its local array; the LCP array is a by-product of sorting).
- * MSD radix sort over 8-byte big-endian character words with an equal-prefix
- * skip, finished inside one CTA for segments of up to cta_cap strings.
+ * MSD string sort by reference-split keys: every member of a segment (strings
+ * sharing `depth` characters) is keyed by its LCP with the segment's reference
+ * member, the side of the reference it falls on and its next 4-6 characters;
+ * large segments are split by sampled key splitters into range and equality
+ * buckets sorted in shared memory, segments of up to cta_cap strings are
+ * finished inside one CTA (or one warp / 4-lane group when tiny), and equal
+ * keys form the next round's segments.
  *
  * out_run_perm : uint32_t[n]; positions [lo_i, hi_i) hold partition i's input
  *                indices in sorted order (equal strings by index).
  * out_run_lcp  : uint32_t[n]; out_run_lcp[q] = lcp(run[q-1], run[q]) within a
  *                partition, 0 at every partition start.
- * Synchronises the stream once per radix round of segments larger than cta_cap. */
+ * Synchronises the stream once per round of segments larger than cta_cap
+ * (never with SSS_FLAG_GRAPH, whose round loop runs on the device). */
 sss_status sss_local_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars,
                           const uint64_t* offsets, const uint32_t* lengths, uint32_t n,
                           uint32_t p, const sss_params* params,
@@ -152,8 +159,10 @@ sss_status sss_dist(sss_ctx* ctx, const uint32_t* lengths, uint32_t n,
 /* Stage B -- prefix doubling (Section 4): for k = kmin..kmax the prefixes of
  * length L = 2^k of the still-active strings are hashed to 64-bit keys; keys
  * that occur once (or strings with length <= L) retire with
- * approx = min(L, len); duplicate detection sorts the keys (appendix,
- * "Duplicate Detection with Atomic Hypercube Quicksort").  Survivors of round
+ * approx = min(L, len); duplicates are found by counting the full 64-bit keys
+ * in an exact open-addressing hash table (a single-shot filter without false
+ * positives), or with SSS_FLAG_DEDUPE_SORT by sorting them (the appendix's
+ * route, "Duplicate Detection with Atomic Hypercube Quicksort").  Survivors of round
  * kmax get approx = len.  approx >= dist always.
  * run_perm/run_lcp (nullable together): the local sorted runs of p partitions
  * (as from sss_local_sort); when given, strings whose L-prefix equals a local

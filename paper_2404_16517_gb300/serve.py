@@ -333,9 +333,6 @@ class DeviceEngine:
 
     def run(self, slot, b: Batch):
         torch = self.torch
-        import datagen.cuda as dgc
-
-        from . import sss_sort_batch
         st, ctx = slot["stream"], slot["ctx"]
         lay, _ = batch_layout(b.n_table, [r.n for r in b.reqs])
         offs = self._view(b.keep_off + lay["offs"], b.n_table, torch.int64)
@@ -344,6 +341,23 @@ class DeviceEngine:
         lcp = self._view(b.keep_off + lay["lcp"], b.n_table, torch.int32)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         m = len(b.reqs)
+        try:
+            self._run_on_stream(st, ctx, b, lay, offs, lens, perm, lcp, ev, m)
+        finally:
+            # whatever happened, the arena ranges of this batch go back to the
+            # allocator only once no kernel of it can still touch them
+            st.synchronize()
+            ctx.set_workspace(None)
+        b.gen_ms = ev[0].elapsed_time(ev[1])
+        b.sort_ms = ev[1].elapsed_time(ev[2])
+        for r, f in zip(b.reqs, b.first):
+            r.perm, r.lcp = perm[f:f + r.n], lcp[f:f + r.n]
+
+    def _run_on_stream(self, st, ctx, b: Batch, lay, offs, lens, perm, lcp, ev, m: int):
+        torch = self.torch
+        import datagen.cuda as dgc
+
+        from . import sss_sort_batch
         with torch.cuda.stream(st):
             ev[0].record(st)
             gen_off = b.temp_off + _align(64 * m)
@@ -371,13 +385,7 @@ class DeviceEngine:
             ctx.set_workspace(self.arena[ws_off: ws_off + self._ws(b)])
             sss_sort_batch(self.arena, offs[:b.n_table], lens[:b.n_table], b.first, [r.n for r in b.reqs], self.prm,
                            out_perm=perm[:b.n_table], out_lcp=lcp[:b.n_table], ctx=ctx)
-            ctx.set_workspace(None)
             ev[2].record(st)
-            st.synchronize()
-        b.gen_ms = ev[0].elapsed_time(ev[1])
-        b.sort_ms = ev[1].elapsed_time(ev[2])
-        for r, f in zip(b.reqs, b.first):
-            r.perm, r.lcp = perm[f:f + r.n], lcp[f:f + r.n]
 
     def _ws(self, b: Batch) -> int:
         from . import batch_workspace_bytes
