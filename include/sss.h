@@ -222,6 +222,32 @@ sss_status sss_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars,
                     const sss_params* params, uint32_t* out_perm, uint32_t* out_lcp,
                     uint32_t* out_dist, uint32_t* out_approx);
 
+/* The whole path (as sss_sort, without dist/approx outputs) for a string set in
+ * HOST memory, with the upload overlapped with stage A.  No counterpart in the
+ * paper, whose input starts in the PEs' memory: here the offsets and lengths are
+ * uploaded first, then the characters in one chunk per partition on a second
+ * stream, and partition i's local sort (Section 3, "Initialization") starts as
+ * soon as the chunk holding its strings has arrived, while later chunks are
+ * still in flight.  Stages B to D follow as in sss_sort.
+ * h_chars, h_offsets, h_lengths : HOST arrays (n_chars, n, n entries); pinned
+ *                 (cudaHostAlloc) memory gives full copy speed
+ * d_chars, d_offsets, d_lengths : caller-owned DEVICE buffers of the same sizes,
+ *                 filled by the call (only the characters up to the end of the
+ *                 last string are copied)
+ * out_perm, out_lcp : DEVICE uint32_t[n], as for sss_sort
+ * h_out_perm, h_out_lcp : HOST uint32_t[n] or NULL: copies of the outputs,
+ *                 valid once the context stream has been synchronised
+ * Partitions are sorted in groups of halving size (p/2, p/4, ..., 1, 1), each
+ * as soon as its characters are in, with the local sort's round loop as one
+ * graph launch (SSS_FLAG_GRAPH is implied).  Synchronises the stream to read the
+ * partitions' character extents and, as sss_sort does, the total length.
+ * SSS_FLAG_CHECKED is not supported here (SSS_ERR_UNIMPLEMENTED): validate
+ * with sss_sort. */
+sss_status sss_sort_host(sss_ctx* ctx, const uint8_t* h_chars, uint64_t n_chars, const uint64_t* h_offsets,
+                         const uint32_t* h_lengths, uint32_t n, uint32_t p, const sss_params* params,
+                         uint8_t* d_chars, uint64_t* d_offsets, uint32_t* d_lengths, uint32_t* out_perm,
+                         uint32_t* out_lcp, uint32_t* h_out_perm, uint32_t* h_out_lcp);
+
 /* Batched sorting: m independent instances, instance k being the strings
  * [first, first + n) of one shared string table of n_table strings.  All
  * instances are sorted together (stage A over all of them at once: the

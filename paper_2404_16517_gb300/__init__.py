@@ -95,6 +95,7 @@ def lib():
             "sss_partition": (st, [vp, vp, u64, vp, vp, vp, vp, u32, u32, P, vp, vp]),
             "sss_lcp_merge": (st, [vp, vp, u64, vp, vp, vp, vp, vp, u32, u32, P, vp, vp]),
             "sss_sort": (st, [vp, vp, u64, vp, vp, u32, u32, P, vp, vp, vp, vp]),
+            "sss_sort_host": (st, [vp, vp, u64, vp, vp, u32, u32, P, vp, vp, vp, vp, vp, vp, vp]),
             "sss_dist_prefix_noalloc": (st, [vp, u64, vp, vp, u32, P, vp, vp]),
             "sss_sort_batch": (st, [vp, vp, u64, vp, vp, u32, C.POINTER(sss_instance), u32, P, vp, vp, vp]),
             "sss_set_timing": (st, [vp, C.c_int, C.c_char_p]),
@@ -114,7 +115,7 @@ def exported_symbols() -> list[str]:
     return ["sss_params_default", "sss_create", "sss_destroy", "sss_set_stream", "sss_set_workspace",
             "sss_workspace_bytes", "sss_sync", "sss_status_string", "sss_last_error", "sss_local_sort",
             "sss_dist", "sss_dist_prefix", "sss_partition", "sss_lcp_merge", "sss_sort", "sss_set_timing",
-            "sss_kernel_stats", "sss_reset_stats", "sss_dist_prefix_noalloc", "sss_sort_batch",
+            "sss_kernel_stats", "sss_reset_stats", "sss_dist_prefix_noalloc", "sss_sort_batch", "sss_sort_host",
             "sss_batch_workspace_bytes", "sss_suffix_workspace_bytes", "sss_suffix_sort"]
 
 
@@ -309,6 +310,33 @@ def sss_sort(chars, offs, lens, p: int = 1, prm: sss_params | None = None, out_p
     ctx._check(lib().sss_sort(ctx.h, _ptr(chars), chars.numel(), _ptr(offs), _ptr(lens), n, p, C.byref(prm),
                               _ptr(op), _ptr(ol), _ptr(d), _ptr(a)), ctx.h)
     return op, ol, d, a
+
+
+def sss_sort_host(h_chars, h_offs, h_lens, p: int, d_chars, d_offs, d_lens, prm: sss_params | None = None,
+                  out_perm=None, out_lcp=None, h_out_perm=None, h_out_lcp=None, ctx: Context | None = None):
+    """The whole path for a string set in host memory (CPU tensors, pinned for
+    full copy speed), the upload overlapped with the local sorts.  d_chars/d_offs/
+    d_lens are device buffers of the same sizes that the call fills; h_out_perm/
+    h_out_lcp (CPU int32 tensors or None) receive copies of the outputs once the
+    stream is synchronised.  Returns the device (perm, lcp)."""
+    for t, dt, name in ((h_chars, torch.uint8, "h_chars"), (h_offs, torch.int64, "h_offs"),
+                        (h_lens, torch.int32, "h_lens")):
+        if t.is_cuda or t.dtype != dt or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CPU tensor of dtype {dt}")
+    _check_strings(d_chars, d_offs, d_lens)
+    n = h_lens.numel()
+    if h_offs.numel() != n or d_lens.numel() < n or d_offs.numel() < n or d_chars.numel() < h_chars.numel():
+        raise ValueError("device buffers must be at least as large as the host arrays")
+    for t in (h_out_perm, h_out_lcp):
+        if t is not None and (t.is_cuda or t.dtype != torch.int32 or t.numel() < n or not t.is_contiguous()):
+            raise ValueError("host outputs must be contiguous CPU int32 tensors of length >= n")
+    ctx = ctx or context(d_chars.device.index)
+    op, ol = _out(out_perm, n, d_chars.device), _out(out_lcp, n, d_chars.device)
+    prm = prm or params()
+    ctx._check(lib().sss_sort_host(ctx.h, _ptr(h_chars), h_chars.numel(), _ptr(h_offs), _ptr(h_lens), n, p,
+                                   C.byref(prm), _ptr(d_chars), _ptr(d_offs), _ptr(d_lens), _ptr(op), _ptr(ol),
+                                   _ptr(h_out_perm), _ptr(h_out_lcp)), ctx.h)
+    return op, ol
 
 
 NOALLOC_MAX_STRINGS = 65536

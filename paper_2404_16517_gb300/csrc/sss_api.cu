@@ -181,6 +181,8 @@ sss_status sss_destroy(sss_ctx* ctx) {
     if (ctx->ls_exec) cudaGraphExecDestroy(ctx->ls_exec);
     if (ctx->ls_graph) cudaGraphDestroy(ctx->ls_graph);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    for (cudaEvent_t e : ctx->chunk_events) cudaEventDestroy(e);
     if (ctx->pin_event) cudaEventDestroy(ctx->pin_event);
     delete ctx;
     return SSS_OK;
@@ -405,6 +407,48 @@ sss_status sss_lcp_merge(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, c
                       out_lcp);
 }
 
+}  // extern "C"
+
+// Stages B to D and dist after stage A: the path of sss_sort for p > 1 on a
+// workspace laid out as run_perm, run_lcp, approx, then the stage scratch.
+// `stage_a` fills run_perm/run_lcp (on the context stream).
+template <typename StageA>
+static sss_status run_pipeline(sss_ctx* ctx, const StrIn& in, uint32_t p, const sss_params& prm, uint32_t* out_perm,
+                               uint32_t* out_lcp, uint32_t* out_dist, uint32_t* out_approx, StageA stage_a) {
+    const uint32_t n = in.n;
+    uint64_t total_len = 0;
+    SSS_TRY(impl_sum_tlen(ctx, in, nullptr, &total_len));
+    size_t need = need_pipeline(n, total_len, p, prm);
+    char* ws;
+    SSS_TRY(sss_workspace(ctx, need, &ws));
+    Arena ar{ws, need, 0};
+    uint32_t* run_perm = ar.take<uint32_t>(n);
+    uint32_t* run_lcp = ar.take<uint32_t>(n);
+    uint32_t* approx = ar.take<uint32_t>(n);
+    size_t stage_off = (ar.off + 255) & ~size_t(255);
+    char* stage = ws + stage_off;
+    size_t stage_bytes = need - stage_off;
+    {
+        Arena sa{stage, stage_bytes, 0};
+        SSS_TRY(stage_a(sa, run_perm, run_lcp));
+    }
+    const uint32_t* trunc = nullptr;
+    if (!(prm.flags & SSS_FLAG_MS)) {
+        Arena sa{stage, stage_bytes, 0};
+        SSS_TRY(impl_dist_prefix(ctx, sa, in, run_perm, run_lcp, p, prm, approx));
+        trunc = approx;
+    }
+    SSS_TRY(impl_merge(ctx, stage, stage_bytes, in, trunc, run_perm, run_lcp, p, prm.v, prm.merge_ms, prm.flags,
+                       total_len, out_perm, out_lcp));
+    if (out_dist) SSS_TRY(impl_dist(ctx, in.lens, n, out_perm, out_lcp, out_dist));
+    if (out_approx)
+        SSS_CUDA(cudaMemcpyAsync(out_approx, trunc ? trunc : in.lens, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+    return SSS_OK;
+}
+
+extern "C" {
+
 sss_status sss_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const uint64_t* offsets,
                     const uint32_t* lengths, uint32_t n, uint32_t p, const sss_params* params, uint32_t* out_perm,
                     uint32_t* out_lcp, uint32_t* out_dist, uint32_t* out_approx) {
@@ -425,34 +469,105 @@ sss_status sss_sort(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, const 
             SSS_CUDA(cudaMemcpyAsync(out_approx, lengths, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
         return SSS_OK;
     }
-    uint64_t total_len = 0;
-    SSS_TRY(impl_sum_tlen(ctx, in, nullptr, &total_len));
-    size_t need = need_pipeline(n, total_len, p, prm);
-    char* ws;
-    SSS_TRY(sss_workspace(ctx, need, &ws));
-    Arena ar{ws, need, 0};
-    uint32_t* run_perm = ar.take<uint32_t>(n);
-    uint32_t* run_lcp = ar.take<uint32_t>(n);
-    uint32_t* approx = ar.take<uint32_t>(n);
-    size_t stage_off = (ar.off + 255) & ~size_t(255);
-    char* stage = ws + stage_off;
-    size_t stage_bytes = need - stage_off;
-    {
-        Arena sa{stage, stage_bytes, 0};
-        SSS_TRY(impl_local_sort(ctx, sa, in, p, prm, run_perm, run_lcp));
+    return run_pipeline(ctx, in, p, prm, out_perm, out_lcp, out_dist, out_approx,
+                        [&](Arena& sa, uint32_t* run_perm, uint32_t* run_lcp) {
+                            return impl_local_sort(ctx, sa, in, p, prm, run_perm, run_lcp);
+                        });
+}
+
+sss_status sss_sort_host(sss_ctx* ctx, const uint8_t* h_chars, uint64_t n_chars, const uint64_t* h_offsets,
+                         const uint32_t* h_lengths, uint32_t n, uint32_t p, const sss_params* params,
+                         uint8_t* d_chars, uint64_t* d_offsets, uint32_t* d_lengths, uint32_t* out_perm,
+                         uint32_t* out_lcp, uint32_t* h_out_perm, uint32_t* h_out_lcp) {
+    SSS_TRY(check_common(ctx, h_chars, h_offsets, h_lengths, n, p));
+    if (n > 0 && (!out_perm || !out_lcp || !d_chars || !d_offsets || !d_lengths))
+        return sss_fail(ctx, SSS_ERR_INVALID_ARG, "device buffers and outputs must be non-NULL");
+    if (n == 0) return SSS_OK;
+    cudaSetDevice(ctx->device);
+    sss_params prm = resolve_params(params);
+    if (prm.flags & SSS_FLAG_CHECKED)
+        return sss_fail(ctx, SSS_ERR_UNIMPLEMENTED, "sss_sort_host: SSS_FLAG_CHECKED needs sss_sort");
+    if (!ctx->copy_stream) SSS_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    while (ctx->chunk_events.size() < (size_t)p + 1) {
+        cudaEvent_t e;
+        SSS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->chunk_events.push_back(e);
     }
-    const uint32_t* trunc = nullptr;
-    if (!(prm.flags & SSS_FLAG_MS)) {
-        Arena sa{stage, stage_bytes, 0};
-        SSS_TRY(impl_dist_prefix(ctx, sa, in, run_perm, run_lcp, p, prm, approx));
-        trunc = approx;
+    // views first (12 bytes per string), then every partition's character extent
+    SSS_CUDA(cudaMemcpyAsync(d_offsets, h_offsets, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+    SSS_CUDA(cudaMemcpyAsync(d_lengths, h_lengths, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+    StrIn in{d_chars, n_chars, d_offsets, d_lengths, n};
+    unsigned long long* d_ext = ctx->d_small;  // 2p words: the 4 KiB scratch holds them for p <= 256
+    std::vector<unsigned long long> ext(2 * (size_t)p);
+    if ((size_t)p * 16 <= 4096) {
+        SSS_TRY(impl_part_extents(ctx, in, p, d_ext));
+        SSS_CUDA(cudaMemcpyAsync(ext.data(), d_ext, 16 * (size_t)p, cudaMemcpyDeviceToHost, ctx->stream));
+        SSS_CUDA(cudaStreamSynchronize(ctx->stream));
+    } else {
+        for (uint32_t i = 0; i < p; ++i) ext[2 * i + 1] = n_chars;  // too many partitions: one chunk
     }
-    SSS_TRY(impl_merge(ctx, stage, stage_bytes, in, trunc, run_perm, run_lcp, p, prm.v, prm.merge_ms, prm.flags,
-                       total_len, out_perm, out_lcp));
-    if (out_dist) SSS_TRY(impl_dist(ctx, lengths, n, out_perm, out_lcp, out_dist));
-    if (out_approx)
-        SSS_CUDA(cudaMemcpyAsync(out_approx, trunc ? trunc : lengths, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice,
-                                 ctx->stream));
+    // Characters on the copy stream, one chunk per partition: chunk i ends where
+    // the strings of partitions 0..i end, so partition i may start once chunk i
+    // is in (the copies wait for earlier work of the stream on these buffers).
+    cudaEvent_t start = ctx->chunk_events[p];
+    SSS_CUDA(cudaEventRecord(start, ctx->stream));
+    SSS_CUDA(cudaStreamWaitEvent(ctx->copy_stream, start, 0));
+    uint64_t done = 0;
+    auto copy_chunks = [&](uint32_t i0, uint32_t i1) -> sss_status {
+        for (uint32_t i = i0; i < i1; ++i) {
+            // an empty partition leaves its extent at (max, 0): nothing to add
+            uint64_t end = std::min<uint64_t>(std::max<uint64_t>(done, ext[2 * i + 1]), n_chars);
+            if (end > done) {
+                SSS_CUDA(cudaMemcpyAsync(d_chars + done, h_chars + done, end - done, cudaMemcpyHostToDevice,
+                                         ctx->copy_stream));
+                done = end;
+            }
+            SSS_CUDA(cudaEventRecord(ctx->chunk_events[i], ctx->copy_stream));
+        }
+        return SSS_OK;
+    };
+    // Partitions are sorted in groups of halving size (p/2, p/4, ..., 1, 1), each
+    // once the chunk of its last partition is in: a local sort has a fixed cost per
+    // round, so early groups are large, and only the last, small group's sort is
+    // left after the upload ends.  A group's chunks are enqueued just before its
+    // sort, behind the previous group's: the small uploads of a sort's segment
+    // lists then wait on the copy engine only for chunks that group needs.  The
+    // round loops run as the captured graph (SSS_FLAG_GRAPH): no group waits for
+    // the host between rounds, and one graph serves every group.
+    sss_params prm_a = prm;
+    prm_a.flags |= SSS_FLAG_GRAPH;
+    auto group_end = [&](uint32_t i0) { return i0 + (p - i0 > 1 ? (p - i0) / 2 : 1u); };
+    auto stage_a = [&](Arena& sa, uint32_t* run_perm, uint32_t* run_lcp) -> sss_status {
+        uint32_t i0 = 0;
+        SSS_TRY(copy_chunks(0, group_end(0)));
+        while (i0 < p) {
+            const uint32_t i1 = group_end(i0);
+            SSS_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->chunk_events[i1 - 1], 0));
+            std::vector<Seg> segs;
+            for (uint32_t i = i0; i < i1; ++i) {
+                const uint32_t lo = part_lo(n, p, i), hi = part_lo(n, p, i + 1);
+                segs.push_back(Seg{lo, hi - lo, 0, 0});
+            }
+            Arena a{sa.base, sa.cap, 0};
+            SSS_TRY(impl_sort_segments_range(ctx, a, in, segs, prm_a, run_perm, run_lcp, part_lo(n, p, i0),
+                                             part_lo(n, p, i1)));
+            if (i1 < p) SSS_TRY(copy_chunks(i1, group_end(i1)));
+            i0 = i1;
+        }
+        return SSS_OK;
+    };
+    if (p == 1) {
+        char* ws;
+        SSS_TRY(sss_workspace(ctx, need_local_sort(n, 1, prm), &ws));
+        Arena ar{ws, 0, 0};
+        SSS_TRY(stage_a(ar, out_perm, out_lcp));
+    } else {
+        SSS_TRY(run_pipeline(ctx, in, p, prm, out_perm, out_lcp, nullptr, nullptr, stage_a));
+    }
+    if (h_out_perm)
+        SSS_CUDA(cudaMemcpyAsync(h_out_perm, out_perm, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (h_out_lcp)
+        SSS_CUDA(cudaMemcpyAsync(h_out_lcp, out_lcp, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
     return SSS_OK;
 }
 

@@ -89,6 +89,10 @@ struct sss_ctx {
     cudaGraph_t ls_graph = nullptr;
     cudaGraphExec_t ls_exec = nullptr;
     std::string ls_key;
+    // sss_sort_host: the stream that uploads characters while stage A runs, and
+    // one event per uploaded chunk
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> chunk_events;
 };
 
 // Set ctx->last_error and return the status.
@@ -166,6 +170,13 @@ size_t need_local_sort(uint32_t n, uint32_t p, const sss_params& prm);
 // Sort every given segment of positions (each starting at depth 0) independently.
 sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const std::vector<Seg>& init,
                               const sss_params& prm, uint32_t* perm, uint32_t* lcp);
+// The same for segments inside positions [q0, q1): only that range of perm and
+// lcp is initialised and written (other positions keep their contents).
+sss_status impl_sort_segments_range(sss_ctx* ctx, Arena& ar, const StrIn& in, const std::vector<Seg>& init,
+                                    const sss_params& prm, uint32_t* perm, uint32_t* lcp, uint32_t q0, uint32_t q1);
+// Character extent [lo, hi) of every partition's strings: out[2i] = smallest
+// offset, out[2i+1] = largest offset + length (~0, 0 for an empty partition).
+sss_status impl_part_extents(sss_ctx* ctx, const StrIn& in, uint32_t p, unsigned long long* out);
 sss_status impl_suffix_views(sss_ctx* ctx, uint32_t n, uint32_t max_len, uint64_t* offs, uint32_t* lens);
 sss_status impl_batch_finish(sss_ctx* ctx, const Seg* d_inst, uint32_t m, const uint32_t* lens, uint32_t* perm,
                              const uint32_t* lcp, uint32_t* dist);

@@ -155,10 +155,11 @@ __device__ __forceinline__ uint32_t ref_pick(uint32_t start, uint32_t cnt, uint3
     return cnt > 1 ? ref_mix(start, cnt, depth, t) % cnt : 0u;
 }
 
-__global__ void k_init_perm(uint32_t* perm, uint32_t* lcp, uint32_t n) {
+// identity order and LCP 0 over positions q0 .. q0 + n (perm and lcp point at q0)
+__global__ void k_init_perm(uint32_t* perm, uint32_t* lcp, uint32_t n, uint32_t q0) {
     uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q < n) {
-        perm[q] = q;
+        perm[q] = q0 + q;
         lcp[q] = 0;
     }
 }
@@ -1092,14 +1093,21 @@ static sss_status run_rounds_graph(sss_ctx* ctx, const LsBufs& B, const LsKnobs&
 
 sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const std::vector<Seg>& init,
                               const sss_params& prm, uint32_t* perm, uint32_t* lcp) {
+    return impl_sort_segments_range(ctx, ar, in, init, prm, perm, lcp, 0, in.n);
+}
+
+sss_status impl_sort_segments_range(sss_ctx* ctx, Arena& ar, const StrIn& in, const std::vector<Seg>& init,
+                                    const sss_params& prm, uint32_t* perm, uint32_t* lcp, uint32_t q0, uint32_t q1) {
     const uint32_t n = in.n;
-    if (n == 0) return SSS_OK;
+    if (n == 0 || q1 <= q0) return SSS_OK;
+    const uint32_t nr = q1 - q0;
     LsBufs B;
     carve_ls(ar, n, 1, prm, B);
     const LsKnobs kn = ls_knobs(prm);
     const uint32_t warp_max = kn.warp_cap, med_max = kn.cta_cap;
     SSS_TRY(set_ls_attributes(ctx));
-    SSS_TRY(sss_launch(ctx, "ls_init", k_init_perm, dim3((n + 255) / 256), dim3(256), 0, perm, lcp, n));
+    SSS_TRY(sss_launch(ctx, "ls_init", k_init_perm, dim3((nr + 255) / 256), dim3(256), 0, perm + q0, lcp + q0, nr,
+                       q0));
 
     // initial segments (partitions or instances), by size class
     std::vector<Seg> quad, warp, tiny, small, med, large;
@@ -1146,7 +1154,7 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
                           (uint32_t)small.size(), (uint32_t)med.size(), in, perm, lcp));
     if (large.empty()) return SSS_OK;
 
-    SSS_CUDA(cudaMemsetAsync(B.fixmark, 0, n, ctx->stream));
+    SSS_CUDA(cudaMemsetAsync(B.fixmark + q0, 0, nr, ctx->stream));
     SegLists L{B.tiny, B.med, B.large, B.cnt, B.cap_tiny, B.cap_med, B.cap_large, B.warp, B.cap_warp, B.small,
                B.cap_small, warp_max, med_max};
     if (prm.flags & SSS_FLAG_GRAPH) {
@@ -1164,8 +1172,10 @@ sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const st
         if (h_next[0] == 0) break;
     }
     }
-    SSS_TRY(sss_launch(ctx, "ls_fix_seams", k_fix_seams, dim3(std::min((n + 255) / 256, 4096u)), dim3(256), 0,
-                       (const uint8_t*)B.fixmark, n, in.chars, in.offs, in.lens, (const uint32_t*)perm, lcp));
+    // (over the sorted range only; its first position keeps lcp 0)
+    SSS_TRY(sss_launch(ctx, "ls_fix_seams", k_fix_seams, dim3(std::min((nr + 255) / 256, 4096u)), dim3(256), 0,
+                       (const uint8_t*)(B.fixmark + q0), nr, in.chars, in.offs, in.lens,
+                       (const uint32_t*)(perm + q0), lcp + q0));
     return SSS_OK;
 }
 
@@ -1182,6 +1192,72 @@ sss_status impl_finish_segments(sss_ctx* ctx, const Seg* tiny, uint32_t ntiny, c
                        finish_smem(MED_CAP), med, (const uint32_t*)nullptr, nmed, work + 1, in.chars, in.offs, in.lens,
                        perm, lcp, ctx->d_err));
     return SSS_OK;
+}
+
+// Smallest offset and largest end of every partition's strings: blocks of
+// 4096 positions over the whole grid, each block reducing within one partition
+// and folding its result into out[2i] (min) and out[2i+1] (max) with atomics
+// (out pre-set by k_part_extents_init).
+__global__ void k_part_extents_init(uint32_t p, unsigned long long* __restrict__ out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < p; i += gridDim.x * blockDim.x) {
+        out[2 * i] = ~0ull;
+        out[2 * i + 1] = 0ull;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_part_extents(const uint64_t* __restrict__ offs,
+                                                      const uint32_t* __restrict__ lens, uint32_t n, uint32_t p,
+                                                      unsigned long long* __restrict__ out) {
+    constexpr uint32_t SPAN = 4096;
+    __shared__ unsigned long long s_lo[8], s_hi[8];
+    for (uint64_t c = blockIdx.x; c * SPAN < n; c += gridDim.x) {
+        const uint32_t a = (uint32_t)(c * SPAN);
+        const uint32_t b = (uint32_t)min((uint64_t)n, (uint64_t)a + SPAN);
+        // partitions are contiguous: handle the part of [a, b) in each partition it touches
+        uint32_t i = (uint32_t)(((uint64_t)a * p) / n);
+        while (i + 1 < p && part_lo(n, p, i + 1) <= a) ++i;
+        for (uint32_t q0 = a; q0 < b; ++i) {
+            const uint32_t q1 = min(b, part_lo(n, p, i + 1));
+            unsigned long long lo = ~0ull, hi = 0ull;
+            for (uint32_t q = q0 + threadIdx.x; q < q1; q += 256) {
+                const unsigned long long o = offs[q];
+                lo = o < lo ? o : lo;
+                const unsigned long long e = o + lens[q];
+                hi = e > hi ? e : hi;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ol = __shfl_xor_sync(SSS_FULL, lo, o), oh = __shfl_xor_sync(SSS_FULL, hi, o);
+                lo = ol < lo ? ol : lo;
+                hi = oh > hi ? oh : hi;
+            }
+            if ((threadIdx.x & 31) == 0) {
+                s_lo[threadIdx.x >> 5] = lo;
+                s_hi[threadIdx.x >> 5] = hi;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int w = 1; w < 8; ++w) {
+                    lo = s_lo[w] < lo ? s_lo[w] : lo;
+                    hi = s_hi[w] > hi ? s_hi[w] : hi;
+                }
+                if (q1 > q0) {
+                    atomicMin(&out[2 * i], lo);
+                    atomicMax(&out[2 * i + 1], hi);
+                }
+            }
+            __syncthreads();
+            q0 = q1;
+        }
+    }
+}
+
+sss_status impl_part_extents(sss_ctx* ctx, const StrIn& in, uint32_t p, unsigned long long* out) {
+    const uint32_t sm = (uint32_t)std::max(1, ctx->sm_count);
+    SSS_TRY(sss_launch(ctx, "part_extents", k_part_extents_init, dim3((p + 255) / 256), dim3(256), 0, p, out));
+    const uint32_t blocks = std::min((in.n + 4095u) / 4096u, sm * 8);
+    return sss_launch(ctx, "part_extents", k_part_extents, dim3(blocks), dim3(256), 0, in.offs, in.lens, in.n, p,
+                      out);
 }
 
 uint32_t finish_cap_tiny() { return TINY_CAP; }
