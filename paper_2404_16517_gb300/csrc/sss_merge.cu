@@ -24,6 +24,7 @@
 namespace {
 
 constexpr uint32_t MINF = 0xFFFFFFFFu;  // "minus infinity" splitter
+constexpr uint32_t PINF = 0xFFFFFFFEu;  // no upper splitter: "plus infinity"
 constexpr uint32_t MS_DEFAULT = 32;      // merge segment sample spacing (default)
 
 // ---------------------------------------------------------------------------
@@ -685,7 +686,8 @@ struct BucketInfo {
     uint32_t nsb;    // sub-buckets
     uint32_t ss0;    // first global sub-splitter
     uint32_t fref;   // the bucket's lower splitter (MINF: none)
-    uint32_t pad[2];
+    uint32_t uref;   // the bucket's upper splitter (PINF: none)
+    uint32_t pad;
 };
 
 __device__ __forceinline__ uint32_t last_le(const uint32_t* a, uint32_t n, uint32_t g, uint32_t stride, uint32_t off) {
@@ -864,65 +866,139 @@ __device__ __forceinline__ uint32_t sub_ref(const BucketInfo& B, uint32_t b, con
     uint32_t k = b - B.sb0;
     return k == 0 ? B.fref : subspl[B.ss0 + k - 1];
 }
+// the upper reference string of sub-bucket b (PINF: none)
+__device__ __forceinline__ uint32_t sub_uref(const BucketInfo& B, uint32_t b, const uint32_t* subspl) {
+    uint32_t k = b - B.sb0;
+    return k + 1 < B.nsb ? subspl[B.ss0 + k] : B.uref;
+}
 
-// Decode each slice once, in order: r = LCP with the sub-bucket's reference
-// string (every string of the sub-bucket is greater than it), key = the 8
-// characters at depth r.  Uses only the stored LCPs and record characters:
-// r(e) = min(r(prev), h(e)); characters below h(e) are the predecessor's.
-__global__ void k_d2_decode(Strs S, Recs R, const BucketInfo* __restrict__ bi, uint32_t p, uint32_t nsb,
-                            const uint64_t* __restrict__ soff, const uint32_t* __restrict__ subspl,
-                            uint32_t* __restrict__ rr, uint64_t* __restrict__ rk) {
-    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+// Key sides of a sub-bucket's records (every record x lies in (L, U], L and U
+// the sub-bucket's lower and upper reference strings, c = lcp(L, U); with
+// r = lcp(x, L) and u = lcp(x, U), min(r, u) = c):
+//   0: r > c, x agrees with L past c: (r descending, the 8 characters at r)
+//   1: r = u = c:                    (the 8 characters at c)
+//   2: r = c < u, x agrees with U:    (u ascending, the 8 characters at u)
+// Side 0 members come before side 1, side 1 before side 2; members of
+// different sides have lcp c.
+
+// Decode each slice once, one warp per slice, 32 records at a time:
+//  * r = lcp with L: r(first) by a direct comparison, then r(e) = min(r(prev),
+//    h(e)) -- a prefix minimum of the stored LCPs;
+//  * the 8 characters at r: record e agrees with its predecessor below h(e) and
+//    stores its own 8 characters at h(e) (head).  Where r drops (h(e) <= r(prev))
+//    the key restarts as e's head; elsewhere e's head overwrites the key's bytes
+//    from h(e) - r on.  "Later head overwrites the bytes it covers" is
+//    associative, so the keys of a chunk are a segmented scan over the warp;
+//  * u = lcp with U: u(last) by a direct comparison, then u(e) = min(h(next),
+//    u(next)) -- a suffix minimum;
+//  * side 0 / 1 / 2 from r, u and c = lcp(L, U) = min(r, u) of any record; at
+//    side 2 the characters at u are read from the string.
+// Writes rv (r, c or u), rs (side), rk (characters) per record and c per
+// sub-bucket.
+__device__ __forceinline__ uint64_t d2_mask_from(uint32_t off) { return off == 0 ? ~0ull : (~0ull >> (8 * off)); }
+
+__global__ void __launch_bounds__(256) k_d2_decode(Strs S, Recs R, const BucketInfo* __restrict__ bi, uint32_t p,
+                                                   uint32_t nsb, const uint64_t* __restrict__ soff,
+                                                   const uint32_t* __restrict__ subspl, uint32_t* __restrict__ rv,
+                                                   uint8_t* __restrict__ rs, uint64_t* __restrict__ rk,
+                                                   uint32_t* __restrict__ cb) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // the warp's slice
     if (g >= nsb * p) return;
-    uint32_t b = g / p;
-    uint32_t s0 = (uint32_t)soff[g], s1 = (uint32_t)soff[g + 1];
+    const uint32_t b = g / p;
+    const uint32_t s0 = (uint32_t)soff[g], s1 = (uint32_t)soff[g + 1];
     if (s0 >= s1) return;
-    uint32_t j = bucket_of_sub(bi, p, b);
-    uint32_t ref = sub_ref(bi[j], b, subspl);
-    uint32_t r = 0;
-    if (ref != MINF) {
-        uint32_t l;
-        uint32_t e = R.idx[s0];
-        cmp_from(S.chars + S.offs[ref], tlen(S, ref), S.chars + S.offs[e], tlen(S, e), 0, &l);
-        r = l;
-    }
-    uint32_t e0 = R.idx[s0];
-    uint64_t key = load_word_be(S.chars + S.offs[e0], R.tl[s0], r);
-    rr[s0] = r;
-    rk[s0] = key;
-    // the walk is serial, so the records are read 8 at a time ahead of it
-    const uint32_t* __restrict__ rh = R.h;
-    const uint64_t* __restrict__ rhead = R.head;
-    for (uint32_t u0 = s0 + 1; u0 < s1; u0 += 8) {
-        uint32_t hb[8];
-        uint64_t wb[8];
+    const uint32_t j = bucket_of_sub(bi, p, b);
+    const uint32_t ref = sub_ref(bi[j], b, subspl), uref = sub_uref(bi[j], b, subspl);
+    const uint32_t ef = R.idx[s0], el = R.idx[s1 - 1];
+    uint32_t r0 = 0, ul = 0;
+    if (ref != MINF) warp_cmp_from(S.chars + S.offs[ref], tlen(S, ref), S.chars + S.offs[ef], tlen(S, ef), 0, &r0);
+    if (uref != PINF && uref != MINF)
+        warp_cmp_from(S.chars + S.offs[uref], tlen(S, uref), S.chars + S.offs[el], tlen(S, el), 0, &ul);
+    const uint64_t key0 = load_word_be(S.chars + S.offs[ef], R.tl[s0], r0);
+    // forwards
+    uint32_t carry_r = 0xFFFFFFFFu;
+    uint64_t carry_key = 0;
+    for (uint32_t base = s0; base < s1; base += 32) {
+        const uint32_t t = base + lane;
+        const bool valid = t < s1;
+        const uint32_t h = valid ? (t == s0 ? r0 : R.h[t]) : 0xFFFFFFFFu;
+        const uint64_t hw = valid ? (t == s0 ? key0 : R.head[t]) : 0ull;
+        uint32_t r = h;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            hb[i] = u0 + i < s1 ? rh[u0 + i] : 0u;
-            wb[i] = u0 + i < s1 ? rhead[u0 + i] : 0ull;  // characters [h, h+8) of the string
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(SSS_FULL, r, o);
+            if (lane >= o) r = y < r ? y : r;
+        }
+        r = carry_r < r ? carry_r : r;
+        uint32_t rp = __shfl_up_sync(SSS_FULL, r, 1);  // r after the previous record
+        if (lane == 0) rp = carry_r;
+        // scan element: (segment starts here, bytes written, their values)
+        bool f = valid && h <= rp;
+        uint64_t m = 0, w = 0;
+        if (f) {
+            m = ~0ull;
+            w = hw;
+        } else if (valid && h - r < 8) {
+            m = d2_mask_from(h - r);
+            w = hw >> (8 * (h - r));
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (u0 + i >= s1) break;
-            const uint32_t h = hb[i];
-            const uint64_t hw = wb[i];
-            if (h <= r) {
-                r = h;
-                key = hw;
-            } else if (h - r < 8) {
-                uint32_t d = h - r;
-                key = (key & (~0ull << (64 - 8 * d))) | (hw >> (8 * d));
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t lf = __shfl_up_sync(SSS_FULL, (uint32_t)f, o);
+            const uint64_t lm = __shfl_up_sync(SSS_FULL, m, o), lw = __shfl_up_sync(SSS_FULL, w, o);
+            if (lane >= o && !f) {
+                w = (lw & ~m) | (w & m);
+                m |= lm;
+                f = lf != 0;
             }
-            rr[u0 + i] = r;
-            rk[u0 + i] = key;
+        }
+        const uint64_t key = f ? w : ((carry_key & ~m) | (w & m));
+        if (valid) {
+            rv[t] = r;
+            rk[t] = key;
+        }
+        carry_r = __shfl_sync(SSS_FULL, r, 31);
+        carry_key = __shfl_sync(SSS_FULL, key, 31);
+    }
+    // c = lcp(L, U) = min(r, u) of any record, here the last (whose r the last
+    // chunk's lane 31 holds: lanes past the slice's end leave the minimum alone)
+    const uint32_t c = carry_r < ul ? carry_r : ul;
+    if (lane == 0) atomicMin(&cb[b], c);  // every slice finds the same c
+    // backwards
+    uint32_t carry_u = ul;
+    const uint32_t nch = (s1 - s0 + 31) / 32;
+    for (uint32_t ci = nch; ci-- > 0;) {
+        const uint32_t t = s0 + 32 * ci + lane;
+        const bool valid = t < s1;
+        uint32_t u = valid && t + 1 < s1 ? R.h[t + 1] : 0xFFFFFFFFu;  // h of the next record
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_down_sync(SSS_FULL, u, o);
+            if (lane + o < 32) u = y < u ? y : u;
+        }
+        u = carry_u < u ? carry_u : u;
+        carry_u = __shfl_sync(SSS_FULL, u, 0);
+        if (valid) {
+            const uint32_t rt = rv[t];
+            if (rt > c) {
+                rs[t] = 0;  // rv and rk hold r and the characters at r
+            } else if (u > c) {
+                rs[t] = 2;
+                rv[t] = u;
+                const uint32_t e = R.idx[t];
+                rk[t] = load_word_be(S.chars + S.offs[e], R.tl[t], u);
+            } else {
+                rs[t] = 1;  // r = c: rk holds the characters at c
+            }
         }
     }
 }
 
-// One CTA per sub-bucket: merge its slices by (LCP with the reference desc,
-// next 8 characters, run order).  A run of equal keys whose strings go on
-// shares its first r+8 characters: it becomes a segment for the CTA finisher,
-// which orders it by the characters from r+8 on (equal strings by index).
+// One CTA per sub-bucket: merge its slices by (side, lcp value, next 8
+// characters, run order).  A run of equal keys whose strings go on shares their
+// first v+8 characters: it becomes a segment for the CTA finisher, which orders
+// it from there (equal strings by index).
 struct TieLists {
     Seg* tiny;
     Seg* med;
@@ -930,8 +1006,27 @@ struct TieLists {
     uint32_t cap_tiny, cap_med, lim_tiny;
 };
 
+// 128-bit merge key: side (2 bits) | field (31) | characters (64) | position (31);
+// field = 2^31 - 1 - r at side 0 (r descending), v at sides 1 and 2
+__device__ __forceinline__ void d2_key(uint32_t side, uint32_t v, uint64_t k, uint32_t pos, uint64_t* hi,
+                                       uint64_t* lo) {
+    const uint64_t field = side == 0 ? (uint64_t)(0x7FFFFFFFu - v) : (uint64_t)v;
+    *hi = ((uint64_t)side << 62) | (field << 31) | (k >> 33);
+    *lo = (k << 31) | pos;
+}
+__device__ __forceinline__ uint32_t d2_side(uint64_t hi) { return (uint32_t)(hi >> 62); }
+__device__ __forceinline__ uint32_t d2_v(uint64_t hi) {
+    const uint32_t f = (uint32_t)(hi >> 31) & 0x7FFFFFFFu;
+    return (hi >> 62) == 0 ? 0x7FFFFFFFu - f : f;
+}
+__device__ __forceinline__ uint64_t d2_chars(uint64_t hi, uint64_t lo) { return (hi << 33) | (lo >> 31); }
+__device__ __forceinline__ bool d2_same_key(uint64_t ha, uint64_t la, uint64_t hb, uint64_t lb) {
+    return ha == hb && (la >> 31) == (lb >> 31);
+}
+
 __global__ void __launch_bounds__(D2_T) k_d2_cta(Strs S, Recs R, const uint64_t* __restrict__ soff, uint32_t p,
-                                                 const uint32_t* __restrict__ rr, const uint64_t* __restrict__ rk,
+                                                 const uint32_t* __restrict__ rv, const uint8_t* __restrict__ rs,
+                                                 const uint64_t* __restrict__ rk, const uint32_t* __restrict__ cb,
                                                  uint32_t* __restrict__ out_perm, uint32_t* __restrict__ out_lcp,
                                                  TieLists T, unsigned* err) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -941,45 +1036,45 @@ __global__ void __launch_bounds__(D2_T) k_d2_cta(Strs S, Recs R, const uint64_t*
     const uint32_t base = (uint32_t)soff[(uint64_t)b * p];
     const uint32_t m = (uint32_t)soff[(uint64_t)(b + 1) * p] - base;
     if (m == 0 || m > D2_CAP) return;
+    const uint32_t c = cb[b];
     // slice i (one sorted run of the merge) is [rb[i], rb[i+1])
     __shared__ uint32_t s_rb[D2_MAXP + 1];
     const bool runs = p <= D2_MAXP;
     if (runs)
         for (uint32_t i = threadIdx.x; i <= p; i += D2_T) s_rb[i] = (uint32_t)soff[(uint64_t)b * p + i] - base;
-    for (uint32_t u = threadIdx.x; u < m; u += D2_T) {
-        uint32_t r = rr[base + u];
-        uint64_t k = rk[base + u];
-        sHi[u] = ((uint64_t)(~r) << 32) | (k >> 32);
-        sLo[u] = (k << 32) | u;
-    }
+    for (uint32_t u = threadIdx.x; u < m; u += D2_T) d2_key(rs[base + u], rv[base + u], rk[base + u], u, &sHi[u], &sLo[u]);
     __syncthreads();
-    // every slice is ascending in these keys (r never grows along a sorted slice
-    // of strings above the reference, and at equal r the next characters do
-    // not fall), so a merge of the p slices sorts the sub-bucket
+    // every slice is ascending in these keys (along a sorted slice r never grows
+    // and u never falls, so the sides come in order 0, 1, 2; within a side the
+    // field does not fall, and at an equal field neither do the characters), so a
+    // merge of the p slices sorts the sub-bucket
     if (!runs) block_merge_sort128_fit<D2_T, D2_CAP / D2_T>(sHi, sLo, m);
     else if (m <= D2_CAP / 2) block_merge_runs128<D2_T, D2_CAP / D2_T / 2>(sHi, sLo, m, s_rb, p);
     else block_merge_runs128<D2_T, D2_CAP / D2_T>(sHi, sLo, m, s_rb, p);
     for (uint32_t t = threadIdx.x; t < m; t += D2_T) {
-        uint32_t u = (uint32_t)sLo[t];
+        const uint32_t u = (uint32_t)(sLo[t] & 0x7FFFFFFFu);
         out_perm[base + t] = R.idx[base + u];
-        uint32_t rb = ~(uint32_t)(sHi[t] >> 32);
-        uint64_t kb = ((sHi[t] & 0xFFFFFFFFull) << 32) | (sLo[t] >> 32);
-        bool tie_next = t + 1 < m && sHi[t + 1] == sHi[t] && (sLo[t + 1] >> 32) == (sLo[t] >> 32);
+        const uint64_t hb = sHi[t], lb = sLo[t];
+        const uint32_t sideb = d2_side(hb), vb = d2_v(hb);
+        const uint64_t kb = d2_chars(hb, lb);
+        const bool tie_next = t + 1 < m && d2_same_key(sHi[t + 1], sLo[t + 1], hb, lb);
         bool tie_prev = false;
         if (t > 0) {
-            uint32_t ra = ~(uint32_t)(sHi[t - 1] >> 32);
-            uint64_t ka = ((sHi[t - 1] & 0xFFFFFFFFull) << 32) | (sLo[t - 1] >> 32);
-            tie_prev = ra == rb && ka == kb;
+            const uint64_t ha = sHi[t - 1], la = sLo[t - 1];
+            tie_prev = d2_same_key(ha, la, hb, lb);
+            const uint32_t sidea = d2_side(ha), va = d2_v(ha);
+            const uint64_t ka = d2_chars(ha, la);
             uint32_t l;
-            if (ra != rb) l = ra < rb ? ra : rb;
-            else if (ka != kb) l = ra + word_lcp(ka, kb);
-            else l = word_has_zero(kb) ? R.tl[base + u] : rb + 8;  // equal strings / set by the finisher
+            if (sidea != sideb) l = c;
+            else if (va != vb) l = va < vb ? va : vb;
+            else if (ka != kb) l = va + word_lcp(ka, kb);
+            else l = word_has_zero(kb) ? R.tl[base + u] : vb + 8;  // equal strings / set by the finisher
             out_lcp[base + t] = l;  // t == 0: overwritten by k_d2_seams
         }
         if (tie_next && !tie_prev && !word_has_zero(kb)) {
             uint32_t t1 = t + 1;
-            while (t1 < m && sHi[t1] == sHi[t] && (sLo[t1] >> 32) == (sLo[t] >> 32)) ++t1;
-            Seg sg{base + t, t1 - t, rb + 8, 0};
+            while (t1 < m && d2_same_key(sHi[t1], sLo[t1], hb, lb)) ++t1;
+            Seg sg{base + t, t1 - t, vb + 8, 0};
             if (sg.size <= T.lim_tiny) {
                 uint32_t i = atomicAdd(&T.cnt[0], 1u);
                 if (i < T.cap_tiny) T.tiny[i] = sg; else atomicOr(err, ERRBIT_OVERFLOW);
@@ -1078,7 +1173,9 @@ struct MgBufs {
     uint32_t* psz;
     uint32_t* pso;
     uint32_t* rr;
+    uint8_t* rs;
     uint64_t* rk;
+    uint32_t* cb;
     Seg* tie_tiny;
     Seg* tie_med;
     Arena sub2;  // work memory for sorting the second-level samples
@@ -1157,7 +1254,9 @@ void carve_mg(Arena& ar, uint32_t n, uint32_t p, uint32_t v, uint64_t nrecchars,
     b.psz = ar.take<uint32_t>((size_t)p * p);
     b.pso = ar.take<uint32_t>((size_t)p * p + 1);
     b.rr = ar.take<uint32_t>(n);
+    b.rs = ar.take<uint8_t>(n);
     b.rk = ar.take<uint64_t>(n);
+    b.cb = ar.take<uint32_t>(b.cap_nsb);
     b.tie_tiny = ar.take<Seg>(n / 2 + 2);
     b.tie_med = ar.take<Seg>(n / 65 + 2);
     size_t sub2 = need_local_sort(b.cap_s2, 1, sss_params{});
@@ -1474,6 +1573,7 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
         bi.sb0 = NSB;
         bi.ss0 = NSS;
         bi.fref = j == 0 ? MINF : hspl[j - 1];
+        bi.uref = j + 1 < p ? hspl[j] : PINF;
         hbi[j] = bi;
         sbase += nsmp;
         NSB += bi.nsb;
@@ -1516,14 +1616,15 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
                        S, (const uint32_t*)b.bounds, (const BucketInfo*)b.binfo, (const uint32_t*)b.sb,
                        (const uint64_t*)b.soff, b.R, b.clen, ctx->d_err));
     // D2: decode, then merge every sub-bucket in one CTA
-    SSS_TRY(sss_launch(ctx, "d2_decode", k_d2_decode, dim3((nslices + 127) / 128), dim3(128), 0, S, b.R,
+    SSS_CUDA(cudaMemsetAsync(b.cb, 0xFF, sizeof(uint32_t) * NSB, ctx->stream));
+    SSS_TRY(sss_launch(ctx, "d2_decode", k_d2_decode, dim3((nslices * 32 + 255) / 256), dim3(256), 0, S, b.R,
                        (const BucketInfo*)b.binfo, p, NSB, (const uint64_t*)b.soff, (const uint32_t*)b.subspl, b.rr,
-                       b.rk));
+                       b.rs, b.rk, b.cb));
     TieLists TL{b.tie_tiny, b.tie_med, b.cnt + 1, n / 2 + 2, n / 65 + 2, finish_cap_tiny()};
     SSS_CUDA(cudaMemsetAsync(b.cnt + 1, 0, sizeof(uint32_t) * 2, ctx->stream));
     SSS_TRY(sss_launch(ctx, "d2_cta", k_d2_cta, dim3(NSB), dim3(D2_T), (size_t)D2_CAP * (8 + 8), S, b.R,
-                       (const uint64_t*)b.soff, p, (const uint32_t*)b.rr, (const uint64_t*)b.rk, out_perm, out_lcp,
-                       TL, ctx->d_err));
+                       (const uint64_t*)b.soff, p, (const uint32_t*)b.rr, (const uint8_t*)b.rs,
+                       (const uint64_t*)b.rk, (const uint32_t*)b.cb, out_perm, out_lcp, TL, ctx->d_err));
     // oversized sub-buckets (many equal strings): pairwise merge tree over their slices.
     // (the sample sort above may have grown the pinned staging: re-derive pointers)
     {
