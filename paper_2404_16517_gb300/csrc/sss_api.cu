@@ -178,8 +178,10 @@ sss_status sss_destroy(sss_ctx* ctx) {
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->d_small) cudaFree(ctx->d_small);
     if (ctx->h_small) cudaFreeHost(ctx->h_small);
-    if (ctx->ls_exec) cudaGraphExecDestroy(ctx->ls_exec);
-    if (ctx->ls_graph) cudaGraphDestroy(ctx->ls_graph);
+    for (auto& lg : ctx->ls_graphs) {
+        if (lg.exec) cudaGraphExecDestroy(lg.exec);
+        if (lg.graph) cudaGraphDestroy(lg.graph);
+    }
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     for (cudaEvent_t e : ctx->chunk_events) cudaEventDestroy(e);

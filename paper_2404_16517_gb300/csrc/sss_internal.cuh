@@ -82,13 +82,20 @@ struct sss_ctx {
     std::string timing_filter;
     std::vector<PendingTiming> pending;
     std::vector<cudaEvent_t> event_pool;
-    // graph of the local sort's round loop (SSS_FLAG_GRAPH), reused while its key
-    // (every pointer and size baked into it) is unchanged
+    // graphs of the local sort's round loop (SSS_FLAG_GRAPH and the merge's sample
+    // sorts), each reused while its key (every pointer and size baked into it) is
+    // unchanged; the least recently used of LS_GRAPHS is replaced
     bool capturing = false;
     cudaStream_t cap_stream = nullptr;
-    cudaGraph_t ls_graph = nullptr;
-    cudaGraphExec_t ls_exec = nullptr;
-    std::string ls_key;
+    struct LsGraph {
+        std::string key;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        uint64_t used = 0;
+    };
+    static constexpr int LS_GRAPHS = 4;
+    LsGraph ls_graphs[LS_GRAPHS];
+    uint64_t ls_clock = 0;
     // sss_sort_host: the stream that uploads characters while stage A runs, and
     // one event per uploaded chunk
     cudaStream_t copy_stream = nullptr;

@@ -1023,8 +1023,8 @@ __global__ void k_ls_cond(const uint32_t* __restrict__ cnt, uint32_t* rounds, ui
 }
 
 // The round loop as one graph launch: a while node whose body is one round plus
-// k_ls_cond.  Built on first use and kept in the context under a key of every
-// pointer and size its kernels take.
+// k_ls_cond.  Built on first use and kept in the context (a few graphs, least
+// recently used replaced) under a key of every pointer and size its kernels take.
 static sss_status run_rounds_graph(sss_ctx* ctx, const LsBufs& B, const LsKnobs& kn, const SegLists& L,
                                    const StrIn& in, uint32_t* perm, uint32_t* lcp, uint32_t limit) {
     char keyb[512];
@@ -1033,11 +1033,18 @@ static sss_status run_rounds_graph(sss_ctx* ctx, const LsBufs& B, const LsKnobs&
                   (void*)B.large, (void*)B.sp.plan, kn.warp_cap, kn.cta_cap, kn.direct_cap, kn.bucket_target,
                   ctx->sm_count, limit);
     uint32_t* rounds = reinterpret_cast<uint32_t*>(ctx->d_err) + 1;  // a spare word of the context
-    if (!ctx->ls_exec || ctx->ls_key != keyb) {
-        if (ctx->ls_exec) cudaGraphExecDestroy(ctx->ls_exec);
-        if (ctx->ls_graph) cudaGraphDestroy(ctx->ls_graph);
-        ctx->ls_exec = nullptr;
-        ctx->ls_graph = nullptr;
+    sss_ctx::LsGraph* slot = nullptr;
+    for (auto& lg : ctx->ls_graphs)
+        if (lg.exec && lg.key == keyb) slot = &lg;
+    if (!slot) {
+        slot = &ctx->ls_graphs[0];  // an empty entry, else the least recently used
+        for (auto& lg : ctx->ls_graphs)
+            if (!lg.exec ? slot->exec != nullptr : (slot->exec && lg.used < slot->used)) slot = &lg;
+        if (slot->exec) cudaGraphExecDestroy(slot->exec);
+        if (slot->graph) cudaGraphDestroy(slot->graph);
+        slot->exec = nullptr;
+        slot->graph = nullptr;
+        slot->key.clear();
         if (!ctx->cap_stream) SSS_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t g;
         SSS_CUDA(cudaGraphCreate(&g, 0));
@@ -1080,12 +1087,13 @@ static sss_status run_rounds_graph(sss_ctx* ctx, const LsBufs& B, const LsKnobs&
             cudaGraphDestroy(g);
             return sss_fail(ctx, SSS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
         }
-        ctx->ls_graph = g;
-        ctx->ls_exec = ex;
-        ctx->ls_key = keyb;
+        slot->graph = g;
+        slot->exec = ex;
+        slot->key = keyb;
     }
+    slot->used = ++ctx->ls_clock;
     SSS_CUDA(cudaMemsetAsync(rounds, 0, sizeof(uint32_t), ctx->stream));
-    SSS_CUDA(cudaGraphLaunch(ctx->ls_exec, ctx->stream));
+    SSS_CUDA(cudaGraphLaunch(slot->exec, ctx->stream));
     int st = sss_stat_index(ctx, "ls_graph");
     if (st >= 0) ctx->stats[st].launches++;
     return SSS_OK;

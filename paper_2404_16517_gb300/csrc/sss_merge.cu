@@ -1594,7 +1594,11 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
                            b.s2offs, b.s2lens));
         StrIn sin{in.chars, in.n_chars, b.s2offs, b.s2lens, S2};
         Arena sub = b.sub2;
-        SSS_TRY(impl_local_sort(ctx, sub, sin, 1, sss_params{}, b.s2perm, b.s2lcp));
+        // the samples' round loop as a cached graph: a sort this small is bound by
+        // the host's launches and per-round synchronisation otherwise
+        sss_params sp{};
+        sp.flags = SSS_FLAG_GRAPH;
+        SSS_TRY(impl_local_sort(ctx, sub, sin, 1, sp, b.s2perm, b.s2lcp));
     }
     if (NSS > 0) {
         SSS_TRY(sss_launch(ctx, "d2_subspl", k_d2_subspl, dim3((NSS + 255) / 256), dim3(256), 0,
