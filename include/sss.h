@@ -66,9 +66,13 @@ typedef enum sss_status {
                                   merged inside one CTA each */
 #define SSS_FLAG_GRAPH 0x40u /* local sort: run its round loop as one CUDA graph
                                   launch (a conditional while node whose body is a
-                                  device-planned round); the graph is kept in the
-                                  context and relaunched while the call's pointers
-                                  and sizes are unchanged */
+                                  device-planned round); sss_sort_batch: the whole
+                                  call (identity order, device-side classification
+                                  of the instances, first finishers, round loop,
+                                  instance-local order) is one graph launch after
+                                  the instance-table upload.  Graphs are kept in the
+                                  context (up to four) and relaunched while the
+                                  call's pointers and sizes are unchanged */
 #define SSS_FLAG_CHAR_SAMPLING 0x20u /* partition: character-based regular sampling
                                   (Section 3.1.2): about p(v+1) samples at equally
                                   spaced character positions of the runs (truncated

@@ -183,6 +183,7 @@ sss_status sss_destroy(sss_ctx* ctx) {
         if (lg.graph) cudaGraphDestroy(lg.graph);
     }
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     for (cudaEvent_t e : ctx->chunk_events) cudaEventDestroy(e);
     if (ctx->pin_event) cudaEventDestroy(ctx->pin_event);
@@ -609,6 +610,8 @@ sss_status sss_sort_batch(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, 
     SSS_TRY(sss_upload(ctx, d_inst, pin, sizeof(Seg) * m));
     size_t off = (ar.off + 255) & ~size_t(255);
     Arena sa{ws + off, need - off, 0};
+    if (prm.flags & SSS_FLAG_GRAPH)  // the whole sort as one graph launch
+        return impl_sort_batch_graph(ctx, sa, in, d_inst, m, prm, out_perm, out_lcp, out_dist);
     SSS_TRY(impl_sort_segments(ctx, sa, in, segs, prm, out_perm, out_lcp));
     return impl_batch_finish(ctx, d_inst, m, lengths, out_perm, out_lcp, out_dist);
 }

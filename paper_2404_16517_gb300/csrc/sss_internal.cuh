@@ -87,6 +87,7 @@ struct sss_ctx {
     // unchanged; the least recently used of LS_GRAPHS is replaced
     bool capturing = false;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream2 = nullptr;  // captures a graph's loop body while cap_stream captures the graph
     struct LsGraph {
         std::string key;
         cudaGraph_t graph = nullptr;
@@ -187,6 +188,9 @@ sss_status impl_part_extents(sss_ctx* ctx, const StrIn& in, uint32_t p, unsigned
 sss_status impl_suffix_views(sss_ctx* ctx, uint32_t n, uint32_t max_len, uint64_t* offs, uint32_t* lens);
 sss_status impl_batch_finish(sss_ctx* ctx, const Seg* d_inst, uint32_t m, const uint32_t* lens, uint32_t* perm,
                              const uint32_t* lcp, uint32_t* dist);
+// The batched sort of the m instances d_inst (device table) as one graph launch.
+sss_status impl_sort_batch_graph(sss_ctx* ctx, Arena& ar, const StrIn& in, const Seg* d_inst, uint32_t m,
+                                 const sss_params& prm, uint32_t* perm, uint32_t* lcp, uint32_t* dist);
 
 // Finish segments of positions whose strings share their first `depth`
 // characters (stage A's CTA finisher): perm[start..start+size) is sorted by the

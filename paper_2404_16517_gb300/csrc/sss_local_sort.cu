@@ -1187,6 +1187,153 @@ sss_status impl_sort_segments_range(sss_ctx* ctx, Arena& ar, const StrIn& in, co
     return SSS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// The batched sort as one graph launch (sss_sort_batch with SSS_FLAG_GRAPH).
+// The instances are classified into the size-class lists on the device, so no
+// step needs the host: identity order, classification, the first finishers,
+// the round loop (a conditional WHILE node around one planned round) and the
+// instance-local permutation are all nodes of one graph, kept in the context
+// under a key of every pointer and size its kernels take.
+
+// every instance of >= 2 strings becomes a segment of its size class
+__global__ void k_batch_classify(const Seg* __restrict__ inst, uint32_t m, SegLists L, unsigned* err) {
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        const Seg s = inst[k];
+        if (s.size >= 2) push_seg(L, s.start, s.size, 0, err);
+    }
+}
+
+// the round loop runs at least once only if an instance is large
+__global__ void k_ls_cond0(const uint32_t* __restrict__ cnt, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, cnt[2] > 0 ? 1u : 0u);
+}
+
+sss_status impl_sort_batch_graph(sss_ctx* ctx, Arena& ar, const StrIn& in, const Seg* d_inst, uint32_t m,
+                                 const sss_params& prm, uint32_t* perm, uint32_t* lcp, uint32_t* dist) {
+    const uint32_t n = in.n;
+    if (n == 0 || m == 0) return SSS_OK;
+    LsBufs B;
+    carve_ls(ar, n, 1, prm, B);
+    const LsKnobs kn = ls_knobs(prm);
+    SSS_TRY(set_ls_attributes(ctx));
+    const SegLists L{B.tiny, B.med, B.large, B.cnt, B.cap_tiny, B.cap_med, B.cap_large, B.warp, B.cap_warp, B.small,
+                     B.cap_small, kn.warp_cap, kn.cta_cap};
+    const uint32_t limit = 100000u;
+    char keyb[512];
+    std::snprintf(keyb, sizeof(keyb), "batch %p %p %p %u %p %p %p %p %u %p %p %p %u %u %u %u %d", (const void*)in.chars,
+                  (const void*)in.offs, (const void*)in.lens, n, (void*)perm, (void*)lcp, (void*)dist,
+                  (const void*)d_inst, m, (void*)B.K, (void*)B.large, (void*)B.sp.plan, kn.warp_cap, kn.cta_cap,
+                  kn.direct_cap, kn.bucket_target, ctx->sm_count);
+    uint32_t* rounds = reinterpret_cast<uint32_t*>(ctx->d_err) + 1;  // a spare word of the context
+    sss_ctx::LsGraph* slot = nullptr;
+    for (auto& lg : ctx->ls_graphs)
+        if (lg.exec && lg.key == keyb) slot = &lg;
+    if (!slot) {
+        slot = &ctx->ls_graphs[0];  // an empty entry, else the least recently used
+        for (auto& lg : ctx->ls_graphs)
+            if (!lg.exec ? slot->exec != nullptr : (slot->exec && lg.used < slot->used)) slot = &lg;
+        if (slot->exec) cudaGraphExecDestroy(slot->exec);
+        if (slot->graph) cudaGraphDestroy(slot->graph);
+        slot->exec = nullptr;
+        slot->graph = nullptr;
+        slot->key.clear();
+        if (!ctx->cap_stream) SSS_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        if (!ctx->cap_stream2) SSS_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
+        cudaGraph_t g;
+        SSS_CUDA(cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle h;
+        SSS_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+        const uint32_t sm = (uint32_t)std::max(1, ctx->sm_count);
+        cudaStream_t saved = ctx->stream;
+        ctx->capturing = true;
+        sss_status st = SSS_OK;
+        cudaError_t ce = cudaStreamBeginCaptureToGraph(ctx->cap_stream, g, nullptr, nullptr, 0,
+                                                       cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            ctx->stream = ctx->cap_stream;
+            // A: identity order, the instances' segments by size class, their finishers
+            ce = cudaMemsetAsync(rounds, 0, sizeof(uint32_t), ctx->stream);
+            if (ce == cudaSuccess) ce = cudaMemsetAsync(B.cnt, 0, sizeof(uint32_t) * 8, ctx->stream);
+            if (ce == cudaSuccess) ce = cudaMemsetAsync(B.work, 0, sizeof(uint32_t) * 8, ctx->stream);
+            if (ce == cudaSuccess) ce = cudaMemsetAsync(B.fixmark, 0, n, ctx->stream);
+            if (ce == cudaSuccess) {
+                st = sss_launch(ctx, "ls_init", k_init_perm, dim3((n + 255) / 256), dim3(256), 0, perm, lcp, n, 0u);
+                if (st == SSS_OK)
+                    st = sss_launch(ctx, "batch_classify", k_batch_classify, dim3(std::min((m + 255) / 256, sm * 4)),
+                                    dim3(256), 0, d_inst, m, L, ctx->d_err);
+                if (st == SSS_OK) st = run_finishers(ctx, B, B.cnt, 0, 0, 0, 0, 0, in, perm, lcp);
+                if (st == SSS_OK)
+                    st = sss_launch(ctx, "ls_cond", k_ls_cond0, dim3(1), dim3(1), 0, (const uint32_t*)B.cnt, h);
+            }
+            // B: the round loop, a while node after everything captured so far
+            cudaGraphNode_t wnode = nullptr;
+            if (st == SSS_OK && ce == cudaSuccess) {
+                cudaStreamCaptureStatus cs;
+                cudaGraph_t cg;
+                const cudaGraphNode_t* deps = nullptr;
+                size_t ndeps = 0;
+                ce = cudaStreamGetCaptureInfo(ctx->cap_stream, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
+                cudaGraphNodeParams cp{};
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = h;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                if (ce == cudaSuccess) ce = cudaGraphAddNode(&wnode, cg, deps, nullptr, ndeps, &cp);
+                if (ce == cudaSuccess)
+                    ce = cudaStreamUpdateCaptureDependencies(ctx->cap_stream, &wnode, nullptr, 1,
+                                                             cudaStreamSetCaptureDependencies);
+                if (ce == cudaSuccess) {
+                    cudaGraph_t body = cp.conditional.phGraph_out[0];
+                    ce = cudaStreamBeginCaptureToGraph(ctx->cap_stream2, body, nullptr, nullptr, 0,
+                                                       cudaStreamCaptureModeThreadLocal);
+                    if (ce == cudaSuccess) {
+                        ctx->stream = ctx->cap_stream2;
+                        st = launch_round(ctx, B, kn, L, in, perm, lcp);
+                        if (st == SSS_OK)
+                            st = sss_launch(ctx, "ls_cond", k_ls_cond, dim3(1), dim3(1), 0, (const uint32_t*)B.cnt,
+                                            rounds, limit, ctx->d_err, h);
+                        cudaGraph_t out = body;
+                        cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream2, &out);
+                        if (ce == cudaSuccess) ce = ee;
+                        ctx->stream = ctx->cap_stream;
+                    }
+                }
+            }
+            // C: LCPs across re-sorted buckets, instance-local order, dist
+            if (st == SSS_OK && ce == cudaSuccess) {
+                st = sss_launch(ctx, "ls_fix_seams", k_fix_seams, dim3(std::min((n + 255) / 256, 4096u)), dim3(256), 0,
+                                (const uint8_t*)B.fixmark, n, in.chars, in.offs, in.lens, (const uint32_t*)perm, lcp);
+                if (st == SSS_OK) st = impl_batch_finish(ctx, d_inst, m, in.lens, perm, lcp, dist);
+            }
+            cudaGraph_t out = g;
+            cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &out);
+            if (ce == cudaSuccess) ce = ee;
+        }
+        ctx->capturing = false;
+        ctx->stream = saved;
+        if (st != SSS_OK || ce != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphDestroy(g);
+            return st != SSS_OK ? st : sss_fail(ctx, SSS_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(ce));
+        }
+        cudaGraphExec_t ex;
+        ce = cudaGraphInstantiate(&ex, g, 0);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphDestroy(g);
+            return sss_fail(ctx, SSS_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(ce));
+        }
+        slot->graph = g;
+        slot->exec = ex;
+        slot->key = keyb;
+    }
+    slot->used = ++ctx->ls_clock;
+    SSS_CUDA(cudaGraphLaunch(slot->exec, ctx->stream));
+    int sidx = sss_stat_index(ctx, "batch_graph");
+    if (sidx >= 0) ctx->stats[sidx].launches++;
+    return SSS_OK;
+}
+
 sss_status impl_finish_segments(sss_ctx* ctx, const Seg* tiny, uint32_t ntiny, const Seg* med, uint32_t nmed,
                                 const StrIn& in, uint32_t* perm, uint32_t* lcp) {
     SSS_TRY(set_ls_attributes(ctx));
