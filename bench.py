@@ -758,9 +758,24 @@ def bench_suffix(args, dev, ctx):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     l64 = lcp.to(torch.int64)
-    return {"workload": "suffix_array_markov_order2_2^22_sigma64", "text_bytes": n, "ms_per_step": ms,
-            "suffixes_per_s": n / (ms / 1e3), "mean_lcp": float(l64.float().mean().item()),
-            "max_lcp": int(l64.max().item()), "steps": args.steps}
+    out = {"workload": "suffix_array_markov_order2_2^22_sigma64", "text_bytes": n, "ms_per_step": ms,
+           "suffixes_per_s": n / (ms / 1e3), "mean_lcp": float(l64.float().mean().item()),
+           "max_lcp": int(l64.max().item()), "steps": args.steps}
+    # a highly repetitive text: 2^22 copies of one character (prefix doubling over
+    # ranks; a direct string sort would read n^2/2 characters)
+    rep = torch.full((n,), ord("A"), dtype=torch.uint8, device=dev)
+    sss.sss_suffix_sort(rep, 0, None, sa, lcp, ctx=ctx)
+    torch.cuda.synchronize()
+    e0.record(st)
+    sss.sss_suffix_sort(rep, 0, None, sa, lcp, ctx=ctx)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_rep = e0.elapsed_time(e1)
+    k = torch.arange(n, device=dev, dtype=torch.int64)
+    ok = bool(torch.equal(sa.to(torch.int64), n - 1 - k) and torch.equal(lcp.to(torch.int64), k))
+    out["one_repeated_character"] = {"text_bytes": n, "ms": ms_rep, "suffixes_per_s": n / (ms_rep / 1e3),
+                                     "closed_form_ok": ok}
+    return out
 
 
 def bench_sort_config(args, dev, ctx, workload: str, chars, offs, lens, p: int, note: str, steps: int = 20):

@@ -286,10 +286,14 @@ size_t sss_batch_workspace_bytes(uint32_t n_table, uint32_t m, const sss_params*
  * paper's Section 6, "Conclusion and Future Work": the suffixes of a text sorted
  * as strings without materialising them).  String i is the view
  * text[i .. i + min(n_text - i, max_len)) (max_len 0 = whole suffixes); the
- * views take 12 bytes per suffix of work memory, the characters are never
- * copied.  The sort is stage A (p = 1), so the work grows with the total length
- * of the distinguishing prefixes: fine for texts with short repeats, slow for
- * highly repetitive ones (a text of one repeated character costs n^2/2 reads).
+ * characters are never copied.  The suffixes truncated to 64 characters are
+ * sorted as strings by stage A (p = 1); where that leaves equal truncations,
+ * prefix doubling over ranks follows: the order on the first min(2h, target)
+ * characters is the order of the pairs (rank_h(i), rank_h(i + o)), o <= h,
+ * sorted as 10-byte strings by stage A, until every rank is distinct or the
+ * target length (max_len, else the whole suffix) is reached.  A text with
+ * short repeats is done after the first sort; a text of one repeated character
+ * takes log2(n / 64) rounds.  The LCPs come from the rank levels.
  * text         : DEVICE array of n_text bytes, no 0x00 byte (checked with
  *                SSS_FLAG_CHECKED); n_text < 2^32
  * out_sa       : uint32_t[n_text]; the suffix array (start positions in sorted

@@ -618,11 +618,7 @@ sss_status sss_sort_batch(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars, 
 
 size_t sss_suffix_workspace_bytes(uint64_t n_text, const sss_params* params) {
     if (n_text > UINT32_MAX) return 0;
-    const uint32_t n = (uint32_t)n_text;
-    Arena a;
-    a.take<uint64_t>(n);
-    a.take<uint32_t>(n);
-    return a.off + 256 + need_local_sort(n, 1, resolve_params(params));
+    return need_suffix_sort((uint32_t)n_text, resolve_params(params));
 }
 
 sss_status sss_suffix_sort(sss_ctx* ctx, const uint8_t* text, uint64_t n_text, uint32_t max_len,
@@ -637,15 +633,15 @@ sss_status sss_suffix_sort(sss_ctx* ctx, const uint8_t* text, uint64_t n_text, u
     const size_t need = sss_suffix_workspace_bytes(n_text, &prm);
     char* ws;
     SSS_TRY(sss_workspace(ctx, need, &ws));
-    Arena ar{ws, need, 0};
-    uint64_t* offs = ar.take<uint64_t>(n);
-    uint32_t* lens = ar.take<uint32_t>(n);
-    size_t off = (ar.off + 255) & ~size_t(255);
-    Arena sa{ws + off, need - off, 0};
-    SSS_TRY(impl_suffix_views(ctx, n, max_len ? max_len : UINT32_MAX, offs, lens));
-    StrIn in{text, n_text, offs, lens, n};
-    if (prm.flags & SSS_FLAG_CHECKED) SSS_TRY(checked_input(ctx, in));
-    return impl_local_sort(ctx, sa, in, 1, prm, out_sa, out_lcp);
+    if (prm.flags & SSS_FLAG_CHECKED) {
+        Arena ar{ws, need, 0};
+        uint64_t* offs = ar.take<uint64_t>(n);
+        uint32_t* lens = ar.take<uint32_t>(n);
+        SSS_TRY(impl_suffix_views(ctx, n, max_len ? max_len : UINT32_MAX, offs, lens));
+        StrIn in{text, n_text, offs, lens, n};
+        SSS_TRY(checked_input(ctx, in));
+    }
+    return impl_suffix_sort(ctx, ws, need, text, n, max_len, prm, out_sa, out_lcp);
 }
 
 }  // extern "C"

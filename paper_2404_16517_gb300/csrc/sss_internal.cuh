@@ -212,6 +212,12 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
                       const uint32_t* run_perm, const uint32_t* run_lcp, uint32_t p, uint32_t v, uint32_t ms,
                       uint32_t flags, uint64_t nrecchars, uint32_t* out_perm, uint32_t* out_lcp);
 sss_status impl_sum_tlen(sss_ctx* ctx, const StrIn& in, const uint32_t* trunc, uint64_t* out);
+// exclusive sum of count u32 values into u64 (btot: count / 4096 + 4 words of scratch)
+sss_status impl_scan_u32_u64(sss_ctx* ctx, const uint32_t* in, uint32_t count, uint64_t* out, uint64_t* btot);
+// suffix array and LCP array of a text by prefix doubling over the string sort
+size_t need_suffix_sort(uint32_t n, const sss_params& prm);
+sss_status impl_suffix_sort(sss_ctx* ctx, char* ws, size_t ws_bytes, const uint8_t* text, uint32_t n,
+                            uint32_t max_len, const sss_params& prm, uint32_t* out_sa, uint32_t* out_lcp);
 
 sss_status impl_dist(sss_ctx* ctx, const uint32_t* lens, uint32_t n, const uint32_t* perm, const uint32_t* lcp,
                      uint32_t* dist);

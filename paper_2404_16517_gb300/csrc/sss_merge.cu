@@ -881,27 +881,55 @@ __device__ __forceinline__ uint32_t sub_uref(const BucketInfo& B, uint32_t b, co
 // Side 0 members come before side 1, side 1 before side 2; members of
 // different sides have lcp c.
 
+// c = lcp(L, U) of every sub-bucket (one thread each): between two sub-splitters
+// of a bucket, the minimum of the sorted samples' LCP array over the samples
+// from one to the other; next to a level-1 splitter, a direct comparison; 0
+// next to a missing splitter.
+__global__ void k_d2_cb(Strs S, const BucketInfo* __restrict__ bi, uint32_t p, uint32_t nsb,
+                        const uint32_t* __restrict__ subspl, const uint32_t* __restrict__ s2lcp,
+                        uint32_t* __restrict__ cb) {
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nsb) return;
+    const uint32_t j = bucket_of_sub(bi, p, b);
+    const BucketInfo B = bi[j];
+    const uint32_t k = b - B.sb0;
+    const uint32_t L = sub_ref(B, b, subspl), U = sub_uref(B, b, subspl);
+    uint32_t c = 0;
+    if (L == MINF || U == PINF || U == MINF) {
+        c = 0;
+    } else if (k >= 1 && k + 1 < B.nsb) {
+        // sub-splitters k-1 and k: sorted samples sbase + D2_OVS*k - 1 and sbase + D2_OVS*(k+1) - 1
+        const uint32_t t0 = B.sbase + D2_OVS * k - 1, t1 = B.sbase + D2_OVS * (k + 1) - 1;
+        c = 0xFFFFFFFFu;
+        for (uint32_t t = t0 + 1; t <= t1; ++t) c = s2lcp[t] < c ? s2lcp[t] : c;
+    } else {
+        cmp_from(S.chars + S.offs[L], tlen(S, L), S.chars + S.offs[U], tlen(S, U), 0, &c);
+    }
+    cb[b] = c;
+}
+
 // Decode each slice once, one warp per slice, 32 records at a time:
-//  * r = lcp with L: r(first) by a direct comparison, then r(e) = min(r(prev),
+//  * r = lcp with L: r(first) by a direct comparison from c = lcp(L, U) on
+//    (every record of the sub-bucket shares c characters with L and U), then r(e) = min(r(prev),
 //    h(e)) -- a prefix minimum of the stored LCPs;
 //  * the 8 characters at r: record e agrees with its predecessor below h(e) and
 //    stores its own 8 characters at h(e) (head).  Where r drops (h(e) <= r(prev))
 //    the key restarts as e's head; elsewhere e's head overwrites the key's bytes
 //    from h(e) - r on.  "Later head overwrites the bytes it covers" is
 //    associative, so the keys of a chunk are a segmented scan over the warp;
-//  * u = lcp with U: u(last) by a direct comparison, then u(e) = min(h(next),
-//    u(next)) -- a suffix minimum;
-//  * side 0 / 1 / 2 from r, u and c = lcp(L, U) = min(r, u) of any record; at
-//    side 2 the characters at u are read from the string.
-// Writes rv (r, c or u), rs (side), rk (characters) per record and c per
-// sub-bucket.
+//  * u = lcp with U: u(last) = c when r(last) > c (min(r, u) = c), else by a
+//    direct comparison from c on; then u(e) = min(h(next), u(next)) -- a
+//    suffix minimum;
+//  * side 0 / 1 / 2 from r, u and c; at side 2 the characters at u are read
+//    from the string.
+// Writes rv (r, c or u), rs (side), rk (characters) per record.
 __device__ __forceinline__ uint64_t d2_mask_from(uint32_t off) { return off == 0 ? ~0ull : (~0ull >> (8 * off)); }
 
 __global__ void __launch_bounds__(256) k_d2_decode(Strs S, Recs R, const BucketInfo* __restrict__ bi, uint32_t p,
                                                    uint32_t nsb, const uint64_t* __restrict__ soff,
                                                    const uint32_t* __restrict__ subspl, uint32_t* __restrict__ rv,
                                                    uint8_t* __restrict__ rs, uint64_t* __restrict__ rk,
-                                                   uint32_t* __restrict__ cb) {
+                                                   const uint32_t* __restrict__ cb) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // the warp's slice
     if (g >= nsb * p) return;
@@ -911,10 +939,9 @@ __global__ void __launch_bounds__(256) k_d2_decode(Strs S, Recs R, const BucketI
     const uint32_t j = bucket_of_sub(bi, p, b);
     const uint32_t ref = sub_ref(bi[j], b, subspl), uref = sub_uref(bi[j], b, subspl);
     const uint32_t ef = R.idx[s0], el = R.idx[s1 - 1];
+    const uint32_t c = cb[b];
     uint32_t r0 = 0, ul = 0;
-    if (ref != MINF) warp_cmp_from(S.chars + S.offs[ref], tlen(S, ref), S.chars + S.offs[ef], tlen(S, ef), 0, &r0);
-    if (uref != PINF && uref != MINF)
-        warp_cmp_from(S.chars + S.offs[uref], tlen(S, uref), S.chars + S.offs[el], tlen(S, el), 0, &ul);
+    if (ref != MINF) warp_cmp_from(S.chars + S.offs[ref], tlen(S, ref), S.chars + S.offs[ef], tlen(S, ef), c, &r0);
     const uint64_t key0 = load_word_be(S.chars + S.offs[ef], R.tl[s0], r0);
     // forwards
     uint32_t carry_r = 0xFFFFFFFFu;
@@ -961,10 +988,13 @@ __global__ void __launch_bounds__(256) k_d2_decode(Strs S, Recs R, const BucketI
         carry_r = __shfl_sync(SSS_FULL, r, 31);
         carry_key = __shfl_sync(SSS_FULL, key, 31);
     }
-    // c = lcp(L, U) = min(r, u) of any record, here the last (whose r the last
-    // chunk's lane 31 holds: lanes past the slice's end leave the minimum alone)
-    const uint32_t c = carry_r < ul ? carry_r : ul;
-    if (lane == 0) atomicMin(&cb[b], c);  // every slice finds the same c
+    // u of the last record: c when its r (the last chunk's lane 31 holds it:
+    // lanes past the slice's end leave the minimum alone) is larger, as
+    // min(r, u) = c; else compared from c on
+    if (uref != PINF && uref != MINF) {
+        if (carry_r > c) ul = c;
+        else warp_cmp_from(S.chars + S.offs[uref], tlen(S, uref), S.chars + S.offs[el], tlen(S, el), c, &ul);
+    }
     // backwards
     uint32_t carry_u = ul;
     const uint32_t nch = (s1 - s0 + 31) / 32;
@@ -991,6 +1021,55 @@ __global__ void __launch_bounds__(256) k_d2_decode(Strs S, Recs R, const BucketI
             } else {
                 rs[t] = 1;  // r = c: rk holds the characters at c
             }
+        }
+    }
+}
+
+// One-sided decode, one thread per slice (slices of a few records, large p):
+// r and the characters at r by the forward walk only, every record on side 0
+// (r > 0) or 1 (r = 0), as if U were missing (c = 0): keys relative to L, and
+// runs of equal keys go to the CTA finisher.
+__global__ void k_d2_decode1(Strs S, Recs R, const BucketInfo* __restrict__ bi, uint32_t p, uint32_t nsb,
+                             const uint64_t* __restrict__ soff, const uint32_t* __restrict__ subspl,
+                             uint32_t* __restrict__ rv, uint8_t* __restrict__ rs, uint64_t* __restrict__ rk) {
+    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nsb * p) return;
+    uint32_t b = g / p;
+    uint32_t s0 = (uint32_t)soff[g], s1 = (uint32_t)soff[g + 1];
+    if (s0 >= s1) return;
+    uint32_t j = bucket_of_sub(bi, p, b);
+    uint32_t ref = sub_ref(bi[j], b, subspl);
+    uint32_t r = 0;
+    uint32_t e0 = R.idx[s0];
+    if (ref != MINF) cmp_from(S.chars + S.offs[ref], tlen(S, ref), S.chars + S.offs[e0], tlen(S, e0), 0, &r);
+    uint64_t key = load_word_be(S.chars + S.offs[e0], R.tl[s0], r);
+    rv[s0] = r;
+    rk[s0] = key;
+    rs[s0] = r > 0 ? 0 : 1;
+    // the walk is serial, so the records are read 8 at a time ahead of it
+    for (uint32_t u0 = s0 + 1; u0 < s1; u0 += 8) {
+        uint32_t hb[8];
+        uint64_t wb[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            hb[i] = u0 + i < s1 ? R.h[u0 + i] : 0u;
+            wb[i] = u0 + i < s1 ? R.head[u0 + i] : 0ull;  // characters [h, h+8) of the string
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (u0 + i >= s1) break;
+            const uint32_t h = hb[i];
+            const uint64_t hw = wb[i];
+            if (h <= r) {
+                r = h;
+                key = hw;
+            } else if (h - r < 8) {
+                uint32_t d = h - r;
+                key = (key & (~0ull << (64 - 8 * d))) | (hw >> (8 * d));
+            }
+            rv[u0 + i] = r;
+            rk[u0 + i] = key;
+            rs[u0 + i] = r > 0 ? 0 : 1;
         }
     }
 }
@@ -1405,6 +1484,10 @@ static sss_status scan_u32_u64(sss_ctx* ctx, const uint32_t* in, uint32_t count,
     return SSS_OK;
 }
 
+sss_status impl_scan_u32_u64(sss_ctx* ctx, const uint32_t* in, uint32_t count, uint64_t* out, uint64_t* btot) {
+    return scan_u32_u64(ctx, in, count, out, btot);
+}
+
 // Pairwise merge tree over groups of runs: group g occupies [base_g, ...) with
 // run sizes sizes_g; every level's pairs are planned at once.
 struct TreePlan {
@@ -1620,10 +1703,22 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
                        S, (const uint32_t*)b.bounds, (const BucketInfo*)b.binfo, (const uint32_t*)b.sb,
                        (const uint64_t*)b.soff, b.R, b.clen, ctx->d_err));
     // D2: decode, then merge every sub-bucket in one CTA
-    SSS_CUDA(cudaMemsetAsync(b.cb, 0xFF, sizeof(uint32_t) * NSB, ctx->stream));
+    // Slices of 16 or more records on average: the two-sided decode, a warp per
+    // slice; shorter slices (large p): the one-sided forward walk, a thread per
+    // slice, with c = 0 for every sub-bucket.
+    const bool two_sided = (uint64_t)n >= 16ull * nslices;
+    if (!two_sided) {
+        SSS_CUDA(cudaMemsetAsync(b.cb, 0, sizeof(uint32_t) * NSB, ctx->stream));
+        SSS_TRY(sss_launch(ctx, "d2_decode", k_d2_decode1, dim3((nslices + 127) / 128), dim3(128), 0, S, b.R,
+                           (const BucketInfo*)b.binfo, p, NSB, (const uint64_t*)b.soff, (const uint32_t*)b.subspl,
+                           b.rr, b.rs, b.rk));
+    } else {
+    SSS_TRY(sss_launch(ctx, "d2_cb", k_d2_cb, dim3((NSB + 255) / 256), dim3(256), 0, S, (const BucketInfo*)b.binfo,
+                       p, NSB, (const uint32_t*)b.subspl, (const uint32_t*)b.s2lcp, b.cb));
     SSS_TRY(sss_launch(ctx, "d2_decode", k_d2_decode, dim3((nslices * 32 + 255) / 256), dim3(256), 0, S, b.R,
                        (const BucketInfo*)b.binfo, p, NSB, (const uint64_t*)b.soff, (const uint32_t*)b.subspl, b.rr,
-                       b.rs, b.rk, b.cb));
+                       b.rs, b.rk, (const uint32_t*)b.cb));
+    }
     TieLists TL{b.tie_tiny, b.tie_med, b.cnt + 1, n / 2 + 2, n / 65 + 2, finish_cap_tiny()};
     SSS_CUDA(cudaMemsetAsync(b.cnt + 1, 0, sizeof(uint32_t) * 2, ctx->stream));
     SSS_TRY(sss_launch(ctx, "d2_cta", k_d2_cta, dim3(NSB), dim3(D2_T), (size_t)D2_CAP * (8 + 8), S, b.R,
