@@ -73,6 +73,24 @@ int sss_stat_index(sss_ctx* ctx, const char* name) {
     return ctx->nstats++;
 }
 
+sss_status sss_graph_launch(sss_ctx* ctx, const char* name, cudaGraphExec_t exec) {
+    int st = sss_stat_index(ctx, name);
+    bool timed = sss_timing_on(ctx, st);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (timed) {
+        a = sss_event(ctx);
+        b = sss_event(ctx);
+        cudaEventRecord(a, ctx->stream);
+    }
+    SSS_CUDA(cudaGraphLaunch(exec, ctx->stream));
+    if (timed) {
+        cudaEventRecord(b, ctx->stream);
+        ctx->pending.push_back({st, a, b});
+    }
+    if (st >= 0) ctx->stats[st].launches++;
+    return SSS_OK;
+}
+
 bool sss_timing_on(sss_ctx* ctx, int stat) {
     if (!ctx->timing || stat < 0) return false;
     if (ctx->timing_filter.empty()) return true;

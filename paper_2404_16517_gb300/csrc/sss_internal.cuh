@@ -97,6 +97,9 @@ struct sss_ctx {
     static constexpr int LS_GRAPHS = 4;
     LsGraph ls_graphs[LS_GRAPHS];
     uint64_t ls_clock = 0;
+    // kernel-statistics name of the next round-loop graph launches (timed like a
+    // kernel when timing is on); set by a caller for its own sorts
+    const char* graph_tag = "ls_graph";
     // sss_sort_host: the stream that uploads characters while stage A runs, and
     // one event per uploaded chunk
     cudaStream_t copy_stream = nullptr;
@@ -132,6 +135,10 @@ sss_status sss_upload(sss_ctx* ctx, void* dst, const void* src, size_t bytes);
 int sss_stat_index(sss_ctx* ctx, const char* name);
 bool sss_timing_on(sss_ctx* ctx, int stat);
 cudaEvent_t sss_event(sss_ctx* ctx);
+
+// Launch an instantiated graph on the context stream, counted (and timed with
+// CUDA events when enabled) under `name` like a kernel.
+sss_status sss_graph_launch(sss_ctx* ctx, const char* name, cudaGraphExec_t exec);
 
 // Launch a kernel on the context stream, counting it (and timing it with CUDA
 // events when enabled).  Grids with zero blocks launch nothing.

@@ -1093,10 +1093,7 @@ static sss_status run_rounds_graph(sss_ctx* ctx, const LsBufs& B, const LsKnobs&
     }
     slot->used = ++ctx->ls_clock;
     SSS_CUDA(cudaMemsetAsync(rounds, 0, sizeof(uint32_t), ctx->stream));
-    SSS_CUDA(cudaGraphLaunch(slot->exec, ctx->stream));
-    int st = sss_stat_index(ctx, "ls_graph");
-    if (st >= 0) ctx->stats[st].launches++;
-    return SSS_OK;
+    return sss_graph_launch(ctx, ctx->graph_tag, slot->exec);
 }
 
 sss_status impl_sort_segments(sss_ctx* ctx, Arena& ar, const StrIn& in, const std::vector<Seg>& init,
@@ -1328,10 +1325,7 @@ sss_status impl_sort_batch_graph(sss_ctx* ctx, Arena& ar, const StrIn& in, const
         slot->key = keyb;
     }
     slot->used = ++ctx->ls_clock;
-    SSS_CUDA(cudaGraphLaunch(slot->exec, ctx->stream));
-    int sidx = sss_stat_index(ctx, "batch_graph");
-    if (sidx >= 0) ctx->stats[sidx].launches++;
-    return SSS_OK;
+    return sss_graph_launch(ctx, "batch_graph", slot->exec);
 }
 
 sss_status impl_finish_segments(sss_ctx* ctx, const Seg* tiny, uint32_t ntiny, const Seg* med, uint32_t nmed,

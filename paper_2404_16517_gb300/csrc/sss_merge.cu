@@ -1681,7 +1681,11 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
         // the host's launches and per-round synchronisation otherwise
         sss_params sp{};
         sp.flags = SSS_FLAG_GRAPH;
-        SSS_TRY(impl_local_sort(ctx, sub, sin, 1, sp, b.s2perm, b.s2lcp));
+        const char* tag = ctx->graph_tag;
+        ctx->graph_tag = "d2_sample_sort";  // stage D's time in the statistics
+        const sss_status ss = impl_local_sort(ctx, sub, sin, 1, sp, b.s2perm, b.s2lcp);
+        ctx->graph_tag = tag;
+        SSS_TRY(ss);
     }
     if (NSS > 0) {
         SSS_TRY(sss_launch(ctx, "d2_subspl", k_d2_subspl, dim3((NSS + 255) / 256), dim3(256), 0,
