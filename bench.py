@@ -256,7 +256,7 @@ def main():
     ap.add_argument("--merge-ms", type=int, default=0, help="merge segment spacing (0 = library default)")
     ap.add_argument("--p", type=int, default=P, help="partitions (profiling of smaller cases)")
     ap.add_argument("--workload", default="all",
-                    choices=["all", "pdms", "batch", "serve", "charsample", "suffix", "config1", "config3"])
+                    choices=["all", "pdms", "batch", "serve", "charsample", "suffix", "config1", "config3", "h2d"])
     ap.add_argument("--batch-instances", type=int, default=4096)
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner (default knobs)")
     ap.add_argument("--no-graph", action="store_true", help="batch: host-driven round loop only")
@@ -293,6 +293,10 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
+    if args.workload == "h2d":
+        if rank == 0:
+            print(json.dumps({"metric": "host link GB/s", "n_gpus": ws, **bench_h2d(args, dev)}), flush=True)
+        return 0
     if args.workload in ("batch", "serve", "charsample", "suffix", "config1", "config3"):
         ctx = sss.context(local)
         res = {"batch": bench_batch, "charsample": bench_charsample, "suffix": bench_suffix,
@@ -403,6 +407,9 @@ def main():
                "h2d_bytes_per_step": int(chars.numel() + 8 * n + 4 * n),
                "d2h_bytes_per_step": int(8 * n + 16 * args.p),
                "ms_per_step": ems, "result_read_back": ok}
+        if ws == 1:
+            del d_chars, d_offs, d_lens
+            e2e["host_link"] = bench_h2d(args, dev)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -782,27 +789,52 @@ def bench_sort_config(args, dev, ctx, workload: str, chars, offs, lens, p: int, 
     """Time sss_sort on one more string set (a sub-line of the JSON): L2
     flushed (a 256 MB write) before every step, each step timed by its own CUDA
     events on the context stream, the dominant kernel's roofline and the
-    stage-level efficiencies as for the headline."""
+    stage-level efficiencies as for the headline.  The local sort's round loop
+    runs host-driven and as one graph launch (SSS_FLAG_GRAPH); the faster is
+    reported, both are listed."""
     import torch
 
     import paper_2404_16517_gb300 as sss
     n = lens.numel()
     N = int(lens.to(torch.int64).sum().item())
-    prm = sss.params()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+    perm0 = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp0 = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def loop_ms(prm_, reps):
+        for _ in range(3):
+            sss.sss_sort(chars, offs, lens, p, prm_, perm0, lcp0, ctx=ctx)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda.synchronize()
+        for i in range(reps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(st)
+            sss.sss_sort(chars, offs, lens, p, prm_, perm0, lcp0, ctx=ctx)
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+    ms_host = loop_ms(sss.params(), 10)
+    ms_graph = loop_ms(sss.params(flags=sss.SSS_FLAG_GRAPH), 10)
+    prm = sss.params(flags=sss.SSS_FLAG_GRAPH) if ms_graph < ms_host else sss.params()
+    del perm0, lcp0
     perm = torch.empty(n, dtype=torch.int32, device=dev)
     lcp = torch.empty(n, dtype=torch.int32, device=dev)
     dist_t = torch.empty(n, dtype=torch.int32, device=dev)
     approx = torch.empty(n, dtype=torch.int32, device=dev) if p > 1 else None
 
-    def step():
-        sss.sss_sort(chars, offs, lens, p, prm, perm, lcp, out_dist=dist_t, out_approx=approx, ctx=ctx)
+    def step(prm_=None):
+        sss.sss_sort(chars, offs, lens, p, prm_ or prm, perm, lcp, out_dist=dist_t, out_approx=approx, ctx=ctx)
 
     for _ in range(args.warmup):
         step()
+    # per-kernel times from one host-driven pass (kernels inside a graph launch
+    # are not timed one by one)
     torch.cuda.synchronize()
     ctx.reset_stats()
     ctx.set_timing(True, "")
-    step()
+    step(sss.params())
     torch.cuda.synchronize()
     stats_all = ctx.kernel_stats()
     ctx.set_timing(False)
@@ -810,8 +842,6 @@ def bench_sort_config(args, dev, ctx, workload: str, chars, offs, lens, p: int, 
     D = int(dist_t.to(torch.int64).sum().item())
     Dapprox = int(approx.to(torch.int64).sum().item()) if approx is not None else D
     sum_lcp = int(lcp.to(torch.int64).sum().item())
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    st = torch.cuda.current_stream(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     ctx.reset_stats()
     ctx.set_timing(True, dom)
@@ -827,13 +857,20 @@ def bench_sort_config(args, dev, ctx, workload: str, chars, offs, lens, p: int, 
     ms_step = statistics.mean(a.elapsed_time(b) for a, b in ev)
     hbm, peak_kind = peaks()
     dstat = stats.get(dom, {"launches": 0, "total_ms": 0.0, "timed": 0})
+    per_step = steps
+    if dstat["timed"] == 0:  # the dominant kernel ran inside the graph: its host-driven time
+        dstat, per_step = stats_all.get(dom), 1
     avg_ms = dstat["total_ms"] / max(1, dstat["timed"])
-    algo = algorithmic_bytes(dom, n, N, D, Dapprox, dstat["launches"] / max(1, steps))
+    algo = algorithmic_bytes(dom, n, N, D, Dapprox, dstat["launches"] / max(1, per_step))
     achieved = algo / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
     launches = sum(v["launches"] for v in stats.values()) / steps
+    kernels = sum(v["launches"] for v in stats_all.values())
     return {"workload": workload, "strings": n, "chars": N, "partitions": p, "steps": steps,
             "ms_per_step": ms_step, "chars_per_s": N / (ms_step / 1e3), "strings_per_s": n / (ms_step / 1e3),
             "D_over_N": D / max(1, N), "approx_over_N": Dapprox / max(1, N), "gpu_launches_per_step": launches,
+            "kernels_per_step": kernels,
+            "round_loop": {"ms_host_loop": ms_host, "ms_graph": ms_graph,
+                           "used": "graph" if ms_graph < ms_host else "host"},
             "l2": note,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo,
@@ -862,6 +899,49 @@ def bench_config3(args, dev, ctx):
     return bench_sort_config(args, dev, ctx, "suffixes_2097152_of_markov2_2^22_sigma64_max256_p64", chars, offs,
                              lens, 64, "the 4 MiB text and the 25 MB of views fit in L2: L2 flushed by a 256 MB "
                                        "write before every step", steps=20)
+
+
+def bench_h2d(args, dev, nbytes: int = 2 << 30) -> dict:
+    """Host link: a 2 GiB copy from pinned host memory to the device split over
+    1, 2, 4 and 8 streams, and one copy back (best of three, CUDA events)."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h.fill_(65)
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = {"bytes": nbytes, "h2d_gbs": {}}
+    for ns in (1, 2, 4, 8):
+        streams = [torch.cuda.Stream(dev) for _ in range(ns)]
+        best = None
+        for _ in range(3):
+            torch.cuda.synchronize()
+            start = torch.cuda.Event(enable_timing=True)
+            start.record()
+            ends = []
+            ch = nbytes // ns
+            for i, st in enumerate(streams):
+                e1 = torch.cuda.Event(enable_timing=True)
+                st.wait_event(start)
+                with torch.cuda.stream(st):
+                    d[i * ch:(i + 1) * ch].copy_(h[i * ch:(i + 1) * ch], non_blocking=True)
+                    e1.record(st)
+                ends.append(e1)
+            torch.cuda.synchronize()
+            # from the common start to the last stream's end
+            ms = max(start.elapsed_time(e) for e in ends)
+            best = ms if best is None else min(best, ms)
+        out["h2d_gbs"][str(ns)] = nbytes / (best / 1e3) / 1e9
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = None
+    for _ in range(3):
+        torch.cuda.synchronize()
+        e0.record()
+        h.copy_(d, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    out["d2h_gbs"] = nbytes / (best / 1e3) / 1e9
+    return out
 
 
 def algorithmic_bytes(kernel: str, n: int, N: int, D: int, Dapprox: int, launches_per_step: float) -> float:
