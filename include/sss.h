@@ -73,6 +73,10 @@ typedef enum sss_status {
                                   the instance-table upload.  Graphs are kept in the
                                   context (up to four) and relaunched while the
                                   call's pointers and sizes are unchanged */
+#define SSS_FLAG_NO_CTA_ROUNDS 0x80u /* doubling: launch the per-round kernels for
+                                  every round instead of running the rounds that
+                                  test at most 4096 keys inside one CTA (hash-table
+                                  dedupe only; results are identical) */
 #define SSS_FLAG_CHAR_SAMPLING 0x20u /* partition: character-based regular sampling
                                   (Section 3.1.2): about p(v+1) samples at equally
                                   spaced character positions of the runs (truncated
@@ -172,7 +176,9 @@ sss_status sss_dist(sss_ctx* ctx, const uint32_t* lengths, uint32_t n,
  * (as from sss_local_sort); when given, strings whose L-prefix equals a local
  * neighbour's are known duplicates and one key per such group is hashed -- the
  * result is identical.  out_approx: uint32_t[n] by input index.
- * Synchronises the stream once per round. */
+ * Consecutive rounds that each test at most 4096 keys run inside one CTA (see
+ * SSS_FLAG_NO_CTA_ROUNDS).  Synchronises the stream once per round, or once per
+ * such run of rounds. */
 sss_status sss_dist_prefix(sss_ctx* ctx, const uint8_t* chars, uint64_t n_chars,
                            const uint64_t* offsets, const uint32_t* lengths, uint32_t n,
                            const uint32_t* run_perm, const uint32_t* run_lcp, uint32_t p,

@@ -29,6 +29,7 @@ SSS_FLAG_DEDUPE_SORT = 0x8
 SSS_FLAG_MERGE_TREE = 0x10
 SSS_FLAG_CHAR_SAMPLING = 0x20
 SSS_FLAG_GRAPH = 0x40
+SSS_FLAG_NO_CTA_ROUNDS = 0x80
 SSS_KMAX_AUTO = 0xFFFFFFFF
 SSS_MAX_KERNELS = 128
 

@@ -48,6 +48,7 @@ constexpr uint32_t ACTIVE = 0xFFFFFFFFu;
 constexpr int DD_T = 512, DD_CAP = 4096;  // dedupe bucket CTA
 constexpr int HB_MAX = 13;                // max top bits for bucketing (8192 buckets)
 constexpr int KBINS = 34;                 // rounds 0..33 for the per-position round buckets
+constexpr int PD_T = 256;                 // threads of the per-rep kernels
 
 __host__ __device__ __forceinline__ uint64_t smix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -105,16 +106,49 @@ __device__ __forceinline__ bool is_part_start(uint32_t q, uint32_t n, uint32_t p
     return (uint32_t)((i * n) / p) == q;
 }
 
-// warp-aggregated append of q to list[] (counter *cnt)
-__device__ __forceinline__ void warp_append(bool want, uint32_t q, uint32_t* list, uint32_t* cnt) {
-    uint32_t m = __ballot_sync(SSS_FULL, want);
-    if (!m) return;
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(m) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(cnt, (uint32_t)__popc(m));
-    base = __shfl_sync(SSS_FULL, base, leader);
-    if (want) list[base + __popc(m & ((1u << lane) - 1u))] = q;
+// Block-aggregated append of q to list[] (counter *cnt): one atomic per block
+// and call instead of one per warp, which matters when millions of positions
+// append to one counter.  Every thread of the block calls it; sh holds
+// THREADS / 32 words.
+template <int THREADS>
+__device__ __forceinline__ void block_append(bool want, uint32_t q, uint32_t* list, uint32_t* cnt, uint32_t* sh) {
+    constexpr int NW = THREADS / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned m = __ballot_sync(SSS_FULL, want);
+    if (lane == 0) sh[w] = (uint32_t)__popc(m);
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t c = lane < NW ? sh[lane] : 0u;
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(SSS_FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        const uint32_t tot = __shfl_sync(SSS_FULL, x, 31);
+        uint32_t base = 0;
+        if (lane == 0 && tot) base = atomicAdd(cnt, tot);
+        base = __shfl_sync(SSS_FULL, base, 0);
+        if (lane < NW) sh[lane] = base + x - c;
+    }
+    __syncthreads();
+    if (want) list[sh[w] + (uint32_t)__popc(m & ((1u << lane) - 1u))] = q;
+    __syncthreads();
+}
+
+// block sum of v added to *cnt with one atomic (every thread calls it)
+template <int THREADS>
+__device__ __forceinline__ void block_count(uint32_t v, uint32_t* cnt, uint32_t* sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = __reduce_add_sync(SSS_FULL, v);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int i = 0; i < THREADS / 32; ++i) t += sh[i];
+        if (t) atomicAdd(cnt, t);
+    }
+    __syncthreads();
 }
 
 // round from which q starts a group (lcp[q] < 2^k), at least kmin
@@ -220,21 +254,21 @@ __device__ __forceinline__ uint64_t fold_words(uint64_t h, const uint8_t* s, uin
     return h;
 }
 
-// B1: keys of the reps.  Horner resumes from the L/2-prefix state of the
+// B1: the key of rep q.  Horner resumes from the L/2-prefix state of the
 // previous round: the rep's own state, or (for a position that starts a group
 // only from this round on) the state of its previous group start q', which
 // shares that prefix.  Such a position also shares its first minlcp[q]
 // characters with q': the whole words among them are read from q''s string,
 // which every member of the group reads (so from L2), and only the rest from
-// its own.  States are double-buffered by round parity.
-__global__ void k_pd_hash(PdIn in, const uint32_t* __restrict__ reps, uint32_t nreps, const uint32_t* __restrict__ lpos,
-                          const uint64_t* __restrict__ hst_in, const uint32_t* __restrict__ hlen_in,
-                          uint64_t* __restrict__ hst_out, uint32_t* __restrict__ hlen_out,
-                          const uint32_t* __restrict__ prevstart, const uint32_t* __restrict__ minlcp,
-                          uint64_t* __restrict__ K, uint32_t* __restrict__ V, uint64_t L, uint64_t B) {
-    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nreps) return;
-    uint32_t q = reps[j];
+// its own.  States are double-buffered by round parity.  prevstart and minlcp
+// are optional (a new rep then hashes its prefix from the first word).
+// (The state pointers carry no __restrict__: k_pd_cta_rounds reads in one
+// round the states it wrote in the previous one, so they must not take the
+// read-only cache path.)
+__device__ __forceinline__ uint64_t pd_rep_key(const PdIn& in, uint32_t q, const uint32_t* __restrict__ lpos,
+                                               const uint64_t* hst_in, const uint32_t* hlen_in, uint64_t* hst_out,
+                                               uint32_t* hlen_out, const uint32_t* __restrict__ prevstart,
+                                               const uint32_t* __restrict__ minlcp, uint64_t L, uint64_t B) {
     uint32_t s = ord_of(in, q);
     uint32_t len = lpos[q];
     uint32_t le = L < len ? (uint32_t)L : len;
@@ -262,7 +296,18 @@ __global__ void k_pd_hash(PdIn in, const uint32_t* __restrict__ reps, uint32_t n
     h = fold_words(h, str, wsh, nw, le, B, B2);
     hst_out[q] = h;
     hlen_out[q] = le;
-    K[j] = smix64(h ^ ((uint64_t)le * GAMMA));
+    return smix64(h ^ ((uint64_t)le * GAMMA));
+}
+
+__global__ void k_pd_hash(PdIn in, const uint32_t* __restrict__ reps, uint32_t nreps, const uint32_t* __restrict__ lpos,
+                          const uint64_t* __restrict__ hst_in, const uint32_t* __restrict__ hlen_in,
+                          uint64_t* __restrict__ hst_out, uint32_t* __restrict__ hlen_out,
+                          const uint32_t* __restrict__ prevstart, const uint32_t* __restrict__ minlcp,
+                          uint64_t* __restrict__ K, uint32_t* __restrict__ V, uint64_t L, uint64_t B) {
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nreps) return;
+    uint32_t q = reps[j];
+    K[j] = pd_rep_key(in, q, lpos, hst_in, hlen_in, hst_out, hlen_out, prevstart, minlcp, L, B);
     V[j] = q;
 }
 
@@ -333,13 +378,41 @@ __global__ void __launch_bounds__(1024) k_pd_ps_tiles(PdIn in, uint32_t kprev, u
     if (threadIdx.x == 0) tagg[blockIdx.x] = sh_w[31];
 }
 
-__global__ void k_pd_ps_carry(PsPair* __restrict__ tagg, uint32_t nt) {
-    if (threadIdx.x != 0) return;
-    PsPair run{0u, ~0u};
-    for (uint32_t t = 0; t < nt; ++t) {
-        const PsPair v = tagg[t];
-        tagg[t] = run;  // exclusive: the earlier tiles
-        run = ps_then(run, v);
+// exclusive carry of the tile totals: one CTA scans them 1024 at a time
+__global__ void __launch_bounds__(1024) k_pd_ps_carry(PsPair* __restrict__ tagg, uint32_t nt) {
+    __shared__ PsPair sh_w[32];
+    __shared__ PsPair s_run;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const PsPair id{0u, ~0u};
+    if (threadIdx.x == 0) s_run = id;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < nt; c0 += 1024) {
+        const uint32_t t = c0 + threadIdx.x;
+        PsPair x = t < nt ? tagg[t] : id;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            PsPair y{__shfl_up_sync(SSS_FULL, x.s, o), __shfl_up_sync(SSS_FULL, x.m, o)};
+            if (lane >= o) x = ps_then(y, x);
+        }
+        PsPair ex{__shfl_up_sync(SSS_FULL, x.s, 1), __shfl_up_sync(SSS_FULL, x.m, 1)};
+        if (lane == 0) ex = id;
+        if (lane == 31) sh_w[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            PsPair v = sh_w[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                PsPair y{__shfl_up_sync(SSS_FULL, v.s, o), __shfl_up_sync(SSS_FULL, v.m, o)};
+                if (lane >= o) v = ps_then(y, v);
+            }
+            sh_w[lane] = v;  // inclusive over warps
+        }
+        __syncthreads();
+        const PsPair pre = w > 0 ? ps_then(s_run, sh_w[w - 1]) : s_run;
+        if (t < nt) tagg[t] = ps_then(pre, ex);  // exclusive: the earlier tiles
+        __syncthreads();
+        if (threadIdx.x == 0) s_run = ps_then(s_run, sh_w[31]);
+        __syncthreads();
     }
 }
 
@@ -531,7 +604,7 @@ __device__ __forceinline__ bool ht_dup(const unsigned long long* tab, const uint
 
 // B4: retire the reps whose group is one string with a unique key (or whose
 // length <= L); survivors stay reps next round.
-__global__ void k_pd_retire(PdIn in, const uint32_t* __restrict__ reps, uint32_t nreps,
+__global__ void __launch_bounds__(PD_T) k_pd_retire(PdIn in, const uint32_t* __restrict__ reps, uint32_t nreps,
                             const uint32_t* __restrict__ lpos, const uint64_t* __restrict__ K,
                             const uint8_t* __restrict__ dupf, const unsigned long long* __restrict__ tab,
                             const uint8_t* __restrict__ mark, uint32_t tmask, const uint32_t* __restrict__ zero_cnt,
@@ -557,14 +630,14 @@ __global__ void k_pd_retire(PdIn in, const uint32_t* __restrict__ reps, uint32_t
             keep = true;
         }
     }
-    warp_append(keep, q, reps_next, &cnt[0]);
-    uint32_t r = __reduce_add_sync(SSS_FULL, retired);
-    if ((threadIdx.x & 31) == 0 && r) atomicAdd(&cnt[1], r);
+    __shared__ uint32_t sh[PD_T / 32];
+    block_append<PD_T>(keep, q, reps_next, &cnt[0], sh);
+    block_count<PD_T>(retired, &cnt[1], sh);
 }
 
 // strings equal to their local predecessor whose whole length is tested this
 // round: duplicates that retire with approx = len
-__global__ void k_pd_retire_equal(const uint32_t* __restrict__ list, uint32_t m, const uint32_t* __restrict__ lpos,
+__global__ void __launch_bounds__(PD_T) k_pd_retire_equal(const uint32_t* __restrict__ list, uint32_t m, const uint32_t* __restrict__ lpos,
                                   uint32_t* __restrict__ apos, uint32_t* __restrict__ cnt) {
     uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t retired = 0;
@@ -575,12 +648,12 @@ __global__ void k_pd_retire_equal(const uint32_t* __restrict__ list, uint32_t m,
             retired = 1;
         }
     }
-    uint32_t r = __reduce_add_sync(SSS_FULL, retired);
-    if ((threadIdx.x & 31) == 0 && r) atomicAdd(&cnt[1], r);
+    __shared__ uint32_t sh[PD_T / 32];
+    block_count<PD_T>(retired, &cnt[1], sh);
 }
 
 // positions that start a group from the next round on become reps (if active)
-__global__ void k_pd_newreps(const uint32_t* __restrict__ list, uint32_t m, const uint32_t* __restrict__ apos,
+__global__ void __launch_bounds__(PD_T) k_pd_newreps(const uint32_t* __restrict__ list, uint32_t m, const uint32_t* __restrict__ apos,
                              uint32_t* __restrict__ reps_next, uint32_t* __restrict__ cnt) {
     uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     bool want = false;
@@ -589,7 +662,8 @@ __global__ void k_pd_newreps(const uint32_t* __restrict__ list, uint32_t m, cons
         q = list[j];
         want = apos[q] == ACTIVE;
     }
-    warp_append(want, q, reps_next, &cnt[0]);
+    __shared__ uint32_t sh[PD_T / 32];
+    block_append<PD_T>(want, q, reps_next, &cnt[0], sh);
 }
 
 __global__ void k_pd_final(PdIn in, const uint32_t* __restrict__ apos, const uint32_t* __restrict__ lpos,
@@ -598,6 +672,163 @@ __global__ void k_pd_final(PdIn in, const uint32_t* __restrict__ apos, const uin
     if (q >= in.n) return;
     uint32_t a = apos[q];
     approx[ord_of(in, q)] = a == ACTIVE ? lpos[q] : a;
+}
+
+// Offsets of the per-position round buckets (by the round a position starts a
+// group, and by the round that covers an equal string's length).
+struct PdOffs {
+    uint32_t ks[KBINS + 1];
+    uint32_t kl[KBINS + 1];
+};
+
+// Rounds k0..k1 in one CTA, for rounds whose reps number at most CR_CAP: the
+// same steps as k_pd_hash, k_pd_ht_insert, k_pd_retire, k_pd_retire_equal and
+// k_pd_newreps, with the hash table, the keys and the rep lists in shared
+// memory and __syncthreads between the steps instead of kernel boundaries and a
+// host round trip.  The host picks k1 so that no round holds more than CR_CAP
+// reps (the reps of round k are at most the reps of round k0 plus the
+// positions whose group starts in rounds k0+1..k).  On return the next round's
+// reps are in reps_out, their count in cnt[0], and cnt[1] has grown by the
+// strings retired.  States are read and written in the global double buffers
+// with the same round parity as the per-round kernels.
+constexpr int CR_T = 1024, CR_CAP = 4096;
+constexpr size_t CR_SMEM = (size_t)CR_CAP * 8 + (size_t)2 * CR_CAP * 8 + (size_t)2 * CR_CAP * 4 + (size_t)2 * CR_CAP;
+
+__global__ void __launch_bounds__(CR_T) k_pd_cta_rounds(PdIn in, const uint32_t* __restrict__ reps0, uint32_t nreps0,
+                                                         uint32_t k0, uint32_t k1, uint32_t kmin, uint32_t kmax,
+                                                         const PdOffs off, const uint32_t* __restrict__ list_ks,
+                                                         const uint32_t* __restrict__ list_kl,
+                                                         const uint32_t* __restrict__ lpos, uint64_t* hst,
+                                                         uint32_t* hlen, uint64_t* hst2, uint32_t* hlen2,
+                                                         uint32_t* apos, uint32_t* __restrict__ reps_out,
+                                                         uint32_t* __restrict__ cnt, uint64_t B, unsigned* err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* sK = reinterpret_cast<uint64_t*>(smem);                                // CR_CAP keys
+    unsigned long long* tab = reinterpret_cast<unsigned long long*>(sK + CR_CAP);    // 2 CR_CAP slots
+    uint32_t* lst0 = reinterpret_cast<uint32_t*>(tab + 2 * CR_CAP);                  // CR_CAP
+    uint32_t* lst1 = lst0 + CR_CAP;                                                  // CR_CAP
+    uint8_t* mark = reinterpret_cast<uint8_t*>(lst1 + CR_CAP);                       // 2 CR_CAP
+    __shared__ uint32_t s_n[2], s_zero, s_ret, s_ovf;
+    const uint32_t tid = threadIdx.x;
+    const uint32_t n0 = nreps0 < (uint32_t)CR_CAP ? nreps0 : (uint32_t)CR_CAP;
+    for (uint32_t i = tid; i < n0; i += CR_T) lst0[i] = reps0[i];
+    if (tid == 0) {
+        s_n[0] = n0;
+        s_ret = 0;
+        s_ovf = nreps0 > (uint32_t)CR_CAP;
+    }
+    __syncthreads();
+    uint32_t cur = 0;
+    for (uint32_t k = k0; k <= k1; ++k) {
+        const uint64_t L = 1ull << k;
+        uint32_t* lc = cur ? lst1 : lst0;
+        uint32_t* ln = cur ? lst0 : lst1;
+        const uint32_t nr = s_n[cur];
+        uint32_t T = 1024;
+        while (T < 2u * nr) T <<= 1;
+        const uint32_t tmask = T - 1;
+        for (uint32_t i = tid; i < T; i += CR_T) {
+            tab[i] = 0ull;
+            mark[i] = 0;
+        }
+        if (tid == 0) {
+            s_zero = 0;
+            s_n[cur ^ 1] = 0;
+        }
+        __syncthreads();
+        const bool odd = ((k - kmin) & 1u) != 0;
+        const uint64_t* hs_in = odd ? hst2 : hst;
+        const uint32_t* hl_in = odd ? hlen2 : hlen;
+        uint64_t* hs_out = odd ? hst : hst2;
+        uint32_t* hl_out = odd ? hlen : hlen2;
+        // keys of the reps, inserted into the table (a second copy marks its slot)
+        for (uint32_t j = tid; j < nr; j += CR_T) {
+            const uint64_t key =
+                pd_rep_key(in, lc[j], lpos, hs_in, hl_in, hs_out, hl_out, nullptr, nullptr, L, B);
+            sK[j] = key;
+            if (key == 0) {
+                atomicAdd(&s_zero, 1u);
+                continue;
+            }
+            uint32_t h = (uint32_t)key & tmask;
+            for (uint32_t i = 0; i <= tmask; ++i) {
+                const unsigned long long old = atomicCAS(&tab[h], 0ull, (unsigned long long)key);
+                if (old == 0ull) break;
+                if (old == key) {
+                    mark[h] = 1;
+                    break;
+                }
+                h = (h + 1) & tmask;
+            }
+        }
+        __syncthreads();
+        // retire the reps whose group is one string with a unique key (or whose
+        // length <= L); the others stay reps
+        for (uint32_t j = tid; j < nr; j += CR_T) {
+            const uint32_t q = lc[j];
+            const uint32_t len = lpos[q];
+            bool dup = false;
+            if (in.run_lcp) {
+                const uint32_t pe = part_end_of(q, in.n, in.p);
+                dup = q + 1 < pe && in.run_lcp[q + 1] >= L;
+            }
+            if (!dup) {
+                const uint64_t key = sK[j];
+                if (key == 0) {
+                    dup = s_zero > 1;
+                } else {
+                    uint32_t h = (uint32_t)key & tmask;
+                    for (uint32_t i = 0; i <= tmask; ++i) {
+                        const uint64_t t = tab[h];
+                        if (t == key) {
+                            dup = mark[h] != 0;
+                            break;
+                        }
+                        h = (h + 1) & tmask;
+                    }
+                }
+            }
+            if (!dup || (uint64_t)len <= L) {
+                apos[q] = (uint64_t)len < L ? len : (uint32_t)L;
+                atomicAdd(&s_ret, 1u);
+            } else {
+                const uint32_t at = atomicAdd(&s_n[cur ^ 1], 1u);
+                if (at < (uint32_t)CR_CAP) ln[at] = q;
+                else s_ovf = 1;
+            }
+        }
+        // strings equal to their local predecessor whose whole length is tested now
+        for (uint32_t j = off.kl[k] + tid; j < off.kl[k + 1]; j += CR_T) {
+            const uint32_t q = list_kl[j];
+            if (apos[q] == ACTIVE) {
+                apos[q] = lpos[q];
+                atomicAdd(&s_ret, 1u);
+            }
+        }
+        __syncthreads();
+        // positions that start a group from the next round on become reps
+        // (after the last round k1 the host appends them)
+        if (k < k1) {
+            for (uint32_t j = off.ks[k + 1] + tid; j < off.ks[k + 2]; j += CR_T) {
+                const uint32_t q = list_ks[j];
+                if (apos[q] == ACTIVE) {
+                    const uint32_t at = atomicAdd(&s_n[cur ^ 1], 1u);
+                    if (at < (uint32_t)CR_CAP) ln[at] = q;
+                    else s_ovf = 1;
+                }
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    const uint32_t nr = s_n[cur] < (uint32_t)CR_CAP ? s_n[cur] : (uint32_t)CR_CAP;
+    const uint32_t* lc = cur ? lst1 : lst0;
+    for (uint32_t j = tid; j < nr; j += CR_T) reps_out[j] = lc[j];
+    if (tid == 0) {
+        cnt[0] = nr;
+        cnt[1] += s_ret;
+        if (s_ovf) atomicOr(err, ERRBIT_OVERFLOW);
+    }
 }
 
 struct PdBufs {
@@ -668,6 +899,7 @@ size_t need_dist_prefix(uint32_t n) {
 }
 
 static bool g_pd_attr[64];
+static bool g_cr_attr[64];
 
 sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& sin, const uint32_t* run_perm,
                             const uint32_t* run_lcp, uint32_t p, const sss_params& prm, uint32_t* approx) {
@@ -724,9 +956,45 @@ sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& sin, const uin
     uint32_t nreps = ks_off[kmin + 1] - ks_off[kmin];
     uint32_t retired = 0;
     int nxt = 0;
+    PdOffs offs;
+    for (int i = 0; i <= KBINS; ++i) {
+        offs.ks[i] = ks_off[i];
+        offs.kl[i] = kl_off[i];
+    }
+    const bool cta_rounds = use_ht && !(prm.flags & SSS_FLAG_NO_CTA_ROUNDS);
     for (uint32_t k = kmin; k <= kmax && retired < n; ++k) {
         const uint64_t L = 1ull << k;
         uint32_t tmask = 0;
+        if (cta_rounds && nreps <= (uint32_t)CR_CAP) {
+            // this round and the following ones while their reps stay few: one
+            // CTA; the reps that join in the round after the last one are
+            // appended by k_pd_newreps (they may be many)
+            uint32_t k1 = k;
+            while (k1 < kmax && (uint64_t)nreps + (ks_off[k1 + 2] - ks_off[k + 1]) <= (uint64_t)CR_CAP) ++k1;
+            if (!g_cr_attr[ctx->device & 63]) {
+                SSS_CUDA(cudaFuncSetAttribute(k_pd_cta_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)CR_SMEM));
+                g_cr_attr[ctx->device & 63] = true;
+            }
+            SSS_TRY(sss_launch(ctx, "pd_cta_rounds", k_pd_cta_rounds, dim3(1), dim3(CR_T), CR_SMEM, in, reps, nreps,
+                               k, k1, kmin, kmax, offs, (const uint32_t*)B.list_ks, (const uint32_t*)B.list_kl,
+                               (const uint32_t*)B.lpos, B.hst, B.hlen, B.hst2, B.hlen2, B.apos, B.reps[nxt], cnt, Bh,
+                               ctx->d_err));
+            if (k1 < kmax) {
+                const uint32_t nn = ks_off[k1 + 2] - ks_off[k1 + 1];
+                SSS_TRY(sss_launch(ctx, "pd_newreps", k_pd_newreps, dim3((nn + PD_T - 1) / PD_T), dim3(PD_T), 0,
+                                   (const uint32_t*)(B.list_ks + ks_off[k1 + 1]), nn, (const uint32_t*)B.apos,
+                                   B.reps[nxt], cnt));
+            }
+            SSS_CUDA(cudaMemcpyAsync(h, cnt, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, ctx->stream));
+            SSS_CUDA(cudaStreamSynchronize(ctx->stream));
+            nreps = h[0];
+            retired = h[1];
+            reps = B.reps[nxt];
+            nxt ^= 1;
+            k = k1;
+            continue;
+        }
         if (nreps > 0) {
             // many positions start a group only from this round on: locate their
             // previous group start, whose L/2-prefix state they share
@@ -736,7 +1004,7 @@ sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& sin, const uin
                 uint32_t nt = (n + 4095) / 4096;
                 SSS_TRY(sss_launch(ctx, "pd_prevstart", k_pd_ps_tiles, dim3(nt), dim3(1024), 0, in, k - 1, kmin,
                                    B.prevstart, B.minlcp, B.tagg));
-                SSS_TRY(sss_launch(ctx, "pd_prevstart_carry", k_pd_ps_carry, dim3(1), dim3(32), 0, B.tagg, nt));
+                SSS_TRY(sss_launch(ctx, "pd_prevstart_carry", k_pd_ps_carry, dim3(1), dim3(1024), 0, B.tagg, nt));
                 SSS_TRY(sss_launch(ctx, "pd_prevstart_apply", k_pd_ps_apply, dim3((n + 255) / 256), dim3(256), 0, n,
                                    B.prevstart, B.minlcp, (const PsPair*)B.tagg));
                 ps = B.prevstart;
@@ -777,16 +1045,16 @@ sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& sin, const uin
             }
         }
         SSS_CUDA(cudaMemsetAsync(&cnt[0], 0, sizeof(uint32_t), ctx->stream));
-        SSS_TRY(sss_launch(ctx, "pd_retire", k_pd_retire, dim3((nreps + 255) / 256), dim3(256), 0, in, reps, nreps,
+        SSS_TRY(sss_launch(ctx, "pd_retire", k_pd_retire, dim3((nreps + PD_T - 1) / PD_T), dim3(PD_T), 0, in, reps, nreps,
                            (const uint32_t*)B.lpos, (const uint64_t*)B.K, (const uint8_t*)B.dupf,
                            (const unsigned long long*)B.tab, (const uint8_t*)B.mark, tmask,
                            (const uint32_t*)&cnt[2], B.apos, B.reps[nxt], cnt, L, (int)use_ht));
         uint32_t ne = kl_off[k + 1] - kl_off[k];
-        SSS_TRY(sss_launch(ctx, "pd_retire_equal", k_pd_retire_equal, dim3((ne + 255) / 256), dim3(256), 0,
+        SSS_TRY(sss_launch(ctx, "pd_retire_equal", k_pd_retire_equal, dim3((ne + PD_T - 1) / PD_T), dim3(PD_T), 0,
                            (const uint32_t*)(B.list_kl + kl_off[k]), ne, (const uint32_t*)B.lpos, B.apos, cnt));
         if (k < kmax) {
             uint32_t nn = ks_off[k + 2] - ks_off[k + 1];
-            SSS_TRY(sss_launch(ctx, "pd_newreps", k_pd_newreps, dim3((nn + 255) / 256), dim3(256), 0,
+            SSS_TRY(sss_launch(ctx, "pd_newreps", k_pd_newreps, dim3((nn + PD_T - 1) / PD_T), dim3(PD_T), 0,
                                (const uint32_t*)(B.list_ks + ks_off[k + 1]), nn, (const uint32_t*)B.apos,
                                B.reps[nxt], cnt));
         }

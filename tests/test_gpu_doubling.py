@@ -18,10 +18,11 @@ def sss():
     return m
 
 
-def run_gpu(ss, p, kmin, kmax, seed, use_runs, sort_dedupe=False):
+def run_gpu(ss, p, kmin, kmax, seed, use_runs, sort_dedupe=False, per_round=False):
     m = sss()
     chars, offs, lens = m.to_device(ss)
-    prm = m.params(kmin=kmin, kmax=kmax, hash_seed=seed, flags=m.SSS_FLAG_DEDUPE_SORT if sort_dedupe else 0)
+    flags = (m.SSS_FLAG_DEDUPE_SORT if sort_dedupe else 0) | (m.SSS_FLAG_NO_CTA_ROUNDS if per_round else 0)
+    prm = m.params(kmin=kmin, kmax=kmax, hash_seed=seed, flags=flags)
     if use_runs:
         rp, rl = m.sss_local_sort(chars, offs, lens, p)
         a = m.sss_dist_prefix(chars, offs, lens, rp, rl, p, prm)
@@ -35,12 +36,14 @@ def check(ss, p=1, kmin=0, kmax=None, seed=0):
     if kmax is None:
         kmax = oracle.default_kmax(ss)
     want = oracle.doubling(ss, kmin, kmax, seed)
+    # hash table with rounds of few keys inside one CTA (the default), hash table
+    # with per-round kernels only, sorted keys
     for use_runs in (False, True):
-        for sort_dedupe in (False, True):
-            got = run_gpu(ss, p, kmin, kmax, seed, use_runs, sort_dedupe)
+        for sort_dedupe, per_round in ((False, False), (False, True), (True, False)):
+            got = run_gpu(ss, p, kmin, kmax, seed, use_runs, sort_dedupe, per_round)
             bad = np.flatnonzero(got != want)
-            assert bad.size == 0, (f"use_runs={use_runs} sort_dedupe={sort_dedupe}: approx differs at {bad[:5]} "
-                                   f"got {got[bad[:5]]} want {want[bad[:5]]}")
+            assert bad.size == 0, (f"use_runs={use_runs} sort_dedupe={sort_dedupe} per_round={per_round}: approx "
+                                   f"differs at {bad[:5]} got {got[bad[:5]]} want {want[bad[:5]]}")
 
 
 def test_handworked_example():
