@@ -190,34 +190,66 @@ __global__ void k_pd_init(PdIn in, const uint32_t* __restrict__ lens, uint32_t* 
     }
 }
 
-// scatter positions into their round buckets; one global reservation per
-// (CTA, bucket) keeps the cursors uncontended
+// Reserve a slot of bin b among the lanes that call it with `active`: lanes with
+// the same bin share one shared-memory atomic (the bins of neighbouring
+// positions are mostly equal).  Every lane of the warp calls it.
+__device__ __forceinline__ uint32_t warp_bin_reserve(uint32_t* bins, uint32_t b, bool active) {
+    const unsigned am = __ballot_sync(SSS_FULL, active);
+    uint32_t r = 0;
+    if (active) {
+        const uint32_t lane = threadIdx.x & 31;
+        const unsigned peers = __match_any_sync(am, b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (lane == (uint32_t)leader) base = atomicAdd(&bins[b], (uint32_t)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        r = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    }
+    return r;
+}
+
+// scatter positions into their round buckets, PL_ITEMS positions per thread:
+// lanes with equal buckets share a shared-memory atomic, and one global
+// reservation per (CTA, bucket) keeps the cursors uncontended (the order
+// within a bucket is free: a bucket is a set)
+constexpr int PL_ITEMS = 4;
 __global__ void __launch_bounds__(256) k_pd_lists(PdIn in, const uint32_t* __restrict__ lpos,
                                                   uint32_t* __restrict__ cur_ks, uint32_t* __restrict__ cur_kl,
                                                   uint32_t* __restrict__ list_ks, uint32_t* __restrict__ list_kl,
                                                   uint32_t kmin) {
-    __shared__ uint32_t cs[KBINS], cl[KBINS], bs[KBINS], bl[KBINS];
+    __shared__ uint32_t cs[KBINS], cl[KBINS];
     for (int i = threadIdx.x; i < KBINS; i += blockDim.x) cs[i] = cl[i] = 0;
     __syncthreads();
-    uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t ks = 0, kl = 0, rs = 0, rl = 0;
-    bool valid = q < in.n, inl = false;
-    if (valid) {
-        ks = kstar_of(in, q, kmin);
-        kl = klen_of(lpos[q], kmin);
-        inl = kl < ks;
-        rs = atomicAdd(&cs[ks], 1u);
-        if (inl) rl = atomicAdd(&cl[kl], 1u);
+    uint32_t ks[PL_ITEMS], kl[PL_ITEMS], rs[PL_ITEMS], rl[PL_ITEMS];
+    const uint32_t q0 = blockIdx.x * blockDim.x * PL_ITEMS + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < PL_ITEMS; ++i) {
+        const uint32_t q = q0 + i * blockDim.x;
+        ks[i] = kl[i] = 0;
+        if (q < in.n) {
+            ks[i] = kstar_of(in, q, kmin);
+            kl[i] = klen_of(lpos[q], kmin);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PL_ITEMS; ++i) {
+        const uint32_t q = q0 + i * blockDim.x;
+        rs[i] = warp_bin_reserve(cs, ks[i], q < in.n);
+        rl[i] = warp_bin_reserve(cl, kl[i], q < in.n && kl[i] < ks[i]);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < KBINS; i += blockDim.x) {
-        bs[i] = cs[i] ? atomicAdd(&cur_ks[i], cs[i]) : 0u;
-        bl[i] = cl[i] ? atomicAdd(&cur_kl[i], cl[i]) : 0u;
+        cs[i] = cs[i] ? atomicAdd(&cur_ks[i], cs[i]) : 0u;
+        cl[i] = cl[i] ? atomicAdd(&cur_kl[i], cl[i]) : 0u;
     }
     __syncthreads();
-    if (valid) {
-        list_ks[bs[ks] + rs] = q;
-        if (inl) list_kl[bl[kl] + rl] = q;
+#pragma unroll
+    for (int i = 0; i < PL_ITEMS; ++i) {
+        const uint32_t q = q0 + i * blockDim.x;
+        if (q < in.n) {
+            list_ks[cs[ks[i]] + rs[i]] = q;
+            if (kl[i] < ks[i]) list_kl[cl[kl[i]] + rl[i]] = q;
+        }
     }
 }
 
@@ -949,8 +981,8 @@ sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& sin, const uin
         h[KBINS + i] = kl_off[i];
     }
     SSS_TRY(sss_upload(ctx, cur_ks, h, sizeof(uint32_t) * 2 * KBINS));
-    SSS_TRY(sss_launch(ctx, "pd_lists", k_pd_lists, dim3((n + 255) / 256), dim3(256), 0, in, (const uint32_t*)B.lpos,
-                       cur_ks, cur_kl, B.list_ks, B.list_kl, kmin));
+    SSS_TRY(sss_launch(ctx, "pd_lists", k_pd_lists, dim3((n + 256 * PL_ITEMS - 1) / (256 * PL_ITEMS)), dim3(256), 0,
+                       in, (const uint32_t*)B.lpos, cur_ks, cur_kl, B.list_ks, B.list_kl, kmin));
     // the first round's reps are the positions that start a group at L = 2^kmin
     const uint32_t* reps = B.list_ks + ks_off[kmin];
     uint32_t nreps = ks_off[kmin + 1] - ks_off[kmin];
