@@ -633,6 +633,148 @@ __device__ void block_merge_sort128(uint64_t* sHi, uint64_t* sLo, uint32_t count
     __syncthreads();
 }
 
+// Stable block merge sort of `count` (64-bit key, 32-bit value) pairs in shared
+// memory by the key alone: pairs with equal keys keep their input order (the
+// per-thread odd-even sort swaps only strictly smaller keys, and every merge
+// takes the first list's element on ties).  Same structure as
+// block_merge_sort128: per-thread sorts of ITEMS pairs, then log2(THREADS)
+// merge-path rounds over the swizzled layout; a third less shared-memory
+// traffic and 64-bit instead of 128-bit comparisons.  Input and output in plain
+// index order; slots past `count` are overwritten with padding.
+template <int THREADS, int ITEMS>
+__device__ void block_merge_sort_kv(uint64_t* sK, uint32_t* sV, uint32_t count) {
+    const uint32_t tid = threadIdx.x;
+    uint64_t k[ITEMS];
+    uint32_t v[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t j = tid + i * THREADS;
+        k[i] = j < count ? sK[j] : ~0ull;
+        v[i] = j < count ? sV[j] : ~0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t j = swz<ITEMS>(tid + i * THREADS);
+        sK[j] = k[i];
+        sV[j] = v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t j = swz<ITEMS>(tid * ITEMS + i);
+        k[i] = sK[j];
+        v[i] = sV[j];
+    }
+    // padding (all-ones keys) sits at the end of the thread order, so stability
+    // among real pairs is not disturbed by it
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+#pragma unroll
+        for (int i = (r & 1); i + 1 < ITEMS; i += 2) {
+            if (k[i + 1] < k[i]) {
+                const uint64_t tk = k[i];
+                const uint32_t tv = v[i];
+                k[i] = k[i + 1];
+                v[i] = v[i + 1];
+                k[i + 1] = tk;
+                v[i + 1] = tv;
+            }
+        }
+    }
+    const uint32_t used = (count + ITEMS - 1) / ITEMS;  // threads holding real pairs
+    for (uint32_t w = 1; w < used; w <<= 1) {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            uint32_t j = swz<ITEMS>(tid * ITEMS + i);
+            sK[j] = k[i];
+            sV[j] = v[i];
+        }
+        __syncthreads();
+        const uint32_t L = w * ITEMS;
+        const uint32_t g0 = (tid / (2 * w)) * (2 * L);
+        if (g0 >= count) continue;
+        const uint32_t diag = (tid % (2 * w)) * ITEMS;
+        const uint32_t A0 = g0, B0 = g0 + L;
+        uint32_t lo = diag > L ? diag - L : 0, hi = diag < L ? diag : L;
+        while (lo < hi) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (!(sK[swz<ITEMS>(B0 + diag - 1 - mid)] < sK[swz<ITEMS>(A0 + mid)])) lo = mid + 1;
+            else hi = mid;
+        }
+        uint32_t a = lo, b = diag - lo;
+        uint64_t ak = ~0ull, bk = ~0ull;
+        uint32_t av = ~0u, bv = ~0u;
+        if (a < L) {
+            const uint32_t aj = swz<ITEMS>(A0 + a);
+            ak = sK[aj];
+            av = sV[aj];
+        }
+        if (b < L) {
+            const uint32_t bj = swz<ITEMS>(B0 + b);
+            bk = sK[bj];
+            bv = sV[bj];
+        }
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const bool takeA = a < L && (b >= L || !(bk < ak));
+            k[i] = takeA ? ak : bk;
+            v[i] = takeA ? av : bv;
+            a += takeA ? 1u : 0u;
+            b += takeA ? 0u : 1u;
+            if (i + 1 < ITEMS) {
+                const uint32_t nx = takeA ? a : b;
+                uint64_t nk = ~0ull;
+                uint32_t nv = ~0u;
+                if (nx < L) {
+                    const uint32_t nj = swz<ITEMS>((takeA ? A0 : B0) + nx);
+                    nk = sK[nj];
+                    nv = sV[nj];
+                }
+                ak = takeA ? nk : ak;
+                av = takeA ? nv : av;
+                bk = takeA ? bk : nk;
+                bv = takeA ? bv : nv;
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t j = swz<ITEMS>(tid * ITEMS + i);
+        sK[j] = k[i];
+        sV[j] = v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t j = swz<ITEMS>(tid + i * THREADS);
+        k[i] = sK[j];
+        v[i] = sV[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        uint32_t j = tid + i * THREADS;
+        sK[j] = k[i];
+        sV[j] = v[i];
+    }
+    __syncthreads();
+}
+
+// block_merge_sort_kv with half the items per thread when they suffice
+template <int THREADS, int ITEMS>
+__device__ void block_merge_sort_kv_fit(uint64_t* sK, uint32_t* sV, uint32_t count) {
+    if constexpr (ITEMS >= 4) {
+        if (count <= (uint32_t)(THREADS * ITEMS / 2)) {
+            block_merge_sort_kv<THREADS, ITEMS / 2>(sK, sV, count);
+            return;
+        }
+    }
+    block_merge_sort_kv<THREADS, ITEMS>(sK, sV, count);
+}
+
 // Merge nr sorted runs of 128-bit keys held in shared memory (run k = slots
 // [rb[k], rb[k+1]), rb[0] = 0, rb[nr] = count; plain order in and out) into one
 // ascending list: ceil(log2 nr) rounds that merge adjacent pairs of runs, where a

@@ -525,6 +525,8 @@ __global__ void __launch_bounds__(32 * WF_WARPS) k_finish_group(const Seg* __res
 }
 
 constexpr size_t finish_smem(int cap) { return (size_t)cap * (8 + 8 + 4 * 7); }
+// sort_emit: keys, values (64-bit), two 32-bit arrays
+constexpr size_t emit_smem(int, int cap) { return (size_t)cap * (8 + 8 + 4 + 4); }
 
 // ---------------------------------------------------------------------------
 // Large path.
@@ -626,10 +628,24 @@ __device__ void sort_emit(unsigned char* smem, uint32_t bs, uint32_t m, uint32_t
     __shared__ uint32_t sh_warp[32];
     for (uint32_t i = threadIdx.x; i < m; i += THREADS) {
         sHi[i] = srcK[bs + i];
-        sLo[i] = srcV[bs + i];
+        sA[i] = srcV[bs + i];
     }
     __syncthreads();
-    block_merge_sort128_fit<THREADS, ITEMS>(sHi, sLo, m);
+    // A segment's members arrive in index order (every sort of an earlier round
+    // breaks ties by index, and the partition scatter keeps the order): then a
+    // stable sort by the key alone yields (key, index) order.  Checked; the
+    // 128-bit merge sort of (key, index) otherwise.
+    bool ordered = true;
+    for (uint32_t i = threadIdx.x + 1; i < m; i += THREADS) ordered = ordered && sA[i - 1] < sA[i];
+    if (__syncthreads_and(ordered)) {
+        block_merge_sort_kv_fit<THREADS, ITEMS>(sHi, sA, m);
+        for (uint32_t i = threadIdx.x; i < m; i += THREADS) sLo[i] = sA[i];
+        __syncthreads();
+    } else {
+        for (uint32_t i = threadIdx.x; i < m; i += THREADS) sLo[i] = sA[i];
+        __syncthreads();
+        block_merge_sort128_fit<THREADS, ITEMS>(sHi, sLo, m);
+    }
     for (uint32_t i = threadIdx.x; i < CAP; i += THREADS) {
         uint32_t v = 0;
         if (i < m) {
@@ -952,11 +968,11 @@ static sss_status set_ls_attributes(sss_ctx* ctx) {
         SSS_CUDA(cudaFuncSetAttribute(k_finish<SM_T, SM_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)finish_smem(SM_CAP)));
         SSS_CUDA(cudaFuncSetAttribute(k_lg_buckets<BK_T, BK_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(BK_CAP * (8 + 8 + 4 + 4))));
+                                      (int)emit_smem(BK_T, BK_CAP)));
         SSS_CUDA(cudaFuncSetAttribute(k_lg_buckets<BKS_T, BKS_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(BKS_CAP * (8 + 8 + 4 + 4))));
+                                      (int)emit_smem(BKS_T, BKS_CAP)));
         SSS_CUDA(cudaFuncSetAttribute(k_lg_direct<DIRECT_T, DIRECT_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(DIRECT_CAP * (8 + 8 + 4 + 4))));
+                                      (int)emit_smem(DIRECT_T, DIRECT_CAP)));
         g_attr_done[ctx->device & 63] = true;
     }
     return SSS_OK;
@@ -990,12 +1006,12 @@ static sss_status launch_round(sss_ctx* ctx, const LsBufs& B, const LsKnobs& kn,
                       "ls_lg_scatter"));
     if (kn.bucket_target <= (uint32_t)BKS_CAP / 2) {
         SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets<BKS_T, BKS_CAP>, dim3(sm * 4), dim3(BKS_T),
-                           (size_t)BKS_CAP * (8 + 8 + 4 + 4), (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info,
+                           emit_smem(BKS_T, BKS_CAP), (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info,
                            (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt, (const uint64_t*)B.tK,
                            (const uint32_t*)B.tV, in.lens, B.K, perm, lcp, L, ctx->d_err, B.fixmark, B.work + 3));
     } else {
         SSS_TRY(sss_launch(ctx, "ls_lg_buckets", k_lg_buckets<BK_T, BK_CAP>, dim3(sm * 2), dim3(BK_T),
-                           (size_t)BK_CAP * (8 + 8 + 4 + 4), (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info,
+                           emit_smem(BK_T, BK_CAP), (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info,
                            (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt, (const uint64_t*)B.tK,
                            (const uint32_t*)B.tV, in.lens, B.K, perm, lcp, L, ctx->d_err, B.fixmark, B.work + 3));
     }
@@ -1003,7 +1019,7 @@ static sss_status launch_round(sss_ctx* ctx, const LsBufs& B, const LsKnobs& kn,
                        (const LgSegInfo*)B.sp.info, (const uint32_t*)B.sp.bst, (const uint32_t*)B.segfmt,
                        (const uint64_t*)B.K, lcp));
     SSS_TRY(sss_launch(ctx, "ls_lg_direct", k_lg_direct<DIRECT_T, DIRECT_CAP>, dim3(sm), dim3(DIRECT_T),
-                       (size_t)DIRECT_CAP * (8 + 8 + 4 + 4), (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info,
+                       emit_smem(DIRECT_T, DIRECT_CAP), (const LsPlan*)B.sp.plan, (const LgSegInfo*)B.sp.info,
                        (const uint32_t*)B.segfmt, in.lens, B.K, perm, lcp, L, ctx->d_err, B.work + 5, 0u));
     return run_finishers(ctx, B, B.cnt, 0, 0, 0, 0, 0, in, perm, lcp);
 }
