@@ -732,42 +732,60 @@ __global__ void k_d2_subspl(const BucketInfo* __restrict__ bi, uint32_t p, uint3
     subspl[m] = smp[sperm[bi[j].sbase + D2_OVS * (k + 1) - 1]];
 }
 
-// sb[m*p+i] = number of strings of piece (bucket of m, i) that are <= subspl[m]
-// (one warp per search, warp-wide comparisons).  A bucket's sub-splitters are
-// sorted, so their bounds in a piece are too: phase 0 searches the whole piece
-// for every D2_BSTRIDE-th sub-splitter of the bucket (the anchors), phase 1
-// searches for the others only between the bounds of the anchors around them.
-constexpr uint32_t D2_BSTRIDE = 16;
+// Sorted rank of every second-level sample: srank[sperm[x]] = x.
+__global__ void k_d2_srank(const uint32_t* __restrict__ sperm, uint32_t S2, uint32_t* __restrict__ srank) {
+    const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < S2) srank[sperm[x]] = x;
+}
 
+// sb[m*p+i] = number of strings of piece (bucket of m, i) that are <= subspl[m],
+// one warp per (sub-splitter, piece).  Sub-splitter m is the sorted sample at
+// rank R of its bucket; the piece's own samples sit at piece positions
+// (t+1)*step - 1 in string order, and the sample sort (ties by sample index)
+// keeps them in that order.  So with a = the number of the piece's samples
+// ranked at or before R_end (R extended over the following samples equal to
+// the sub-splitter, which are <= it too), sample a - 1 is <= the sub-splitter
+// and sample a is larger: the count lies in [a*step, (a+1)*step - 1] (or up to
+// the piece's end past its last sample).  A binary search over the samples'
+// ranks finds a, then a binary search of at most 2*step positions, with
+// warp-wide comparisons carrying the LCP with both window ends, the count.
 __global__ void k_d2_bounds(const uint32_t* __restrict__ run_perm, Strs S, const BucketInfo* __restrict__ bi,
                             uint32_t p, uint32_t nss, const uint32_t* __restrict__ pstart,
-                            const uint32_t* __restrict__ psz, const uint32_t* __restrict__ subspl,
-                            uint32_t* __restrict__ sb, uint32_t phase) {
+                            const uint32_t* __restrict__ psz, const uint32_t* __restrict__ pso,
+                            const uint32_t* __restrict__ subspl, const uint32_t* __restrict__ sperm,
+                            const uint32_t* __restrict__ srank, const uint32_t* __restrict__ s2lcp,
+                            const uint32_t* __restrict__ s2lens, uint32_t step, uint32_t* __restrict__ sb) {
     uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (g >= nss * p) return;
     uint32_t m = g / p, i = g % p;
     uint32_t j = last_le(&bi[0].ss0, p, m, sizeof(BucketInfo) / 4, 0);
     while (j + 1 < p && bi[j + 1].ss0 <= m) ++j;
-    const uint32_t k = m - bi[j].ss0, nk = bi[j].nsb - 1;  // index among the bucket's nk sub-splitters
-    const bool anchor = (k + 1) % D2_BSTRIDE == 0;
-    if (anchor != (phase == 0)) return;
-    uint32_t a = 0, b = psz[j * p + i], la = 0, lb = 0;
-    if (!anchor) {
-        const uint32_t blk = (k + 1) / D2_BSTRIDE;
-        if (blk > 0) a = sb[(bi[j].ss0 + blk * D2_BSTRIDE - 1) * p + i];
-        const uint32_t kb = (blk + 1) * D2_BSTRIDE - 1;
-        if (kb < nk) b = sb[(bi[j].ss0 + kb) * p + i];
-    }
-    uint32_t f = subspl[m];
+    const BucketInfo B = bi[j];
+    const uint32_t k = m - B.ss0;
+    const uint32_t f = subspl[m];
     const uint8_t* fs = S.chars + S.offs[f];
-    uint32_t fl = tlen(S, f);
-    uint32_t q0 = pstart[j * p + i];
+    const uint32_t fl = tlen(S, f);
+    // R_end: the sub-splitter's sorted rank, past the samples equal to it
+    uint32_t rend = B.sbase + D2_OVS * (k + 1) - 1;
+    const uint32_t rlim = B.sbase + B.nsmp;
+    while (rend + 1 < rlim && s2lcp[rend + 1] >= fl && s2lens[sperm[rend + 1]] == fl) ++rend;
+    // a: the piece's samples ranked <= R_end (their ranks grow with their positions)
+    const uint32_t g0 = pso[j * p + i], c = pso[j * p + i + 1] - g0;
+    uint32_t ka = 0, kb = c;
+    while (ka < kb) {
+        const uint32_t mid = (ka + kb) >> 1;
+        if (srank[g0 + mid] <= rend) ka = mid + 1; else kb = mid;
+    }
+    const uint32_t n_i = psz[j * p + i];
+    uint32_t a = ka * step, b = ka < c ? (ka + 1) * step - 1 : n_i;
+    uint32_t la = 0, lb = 0;
+    const uint32_t q0 = pstart[j * p + i];
     while (a < b) {
         uint32_t mid = (a + b) >> 1;
         uint32_t e = run_perm[q0 + mid];
         uint32_t d = la < lb ? la : lb, l;
-        int c = warp_cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, d, &l);
-        if (c <= 0) {
+        int cmp = warp_cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, d, &l);
+        if (cmp <= 0) {
             a = mid + 1;
             la = l;
         } else {
@@ -1242,6 +1260,7 @@ struct MgBufs {
     uint32_t* s2lens;
     uint32_t* s2perm;
     uint32_t* s2lcp;
+    uint32_t* s2rank;  // sorted rank of every second-level sample
     uint32_t* subspl;
     uint32_t* sb;
     uint32_t* ssz;
@@ -1323,6 +1342,7 @@ void carve_mg(Arena& ar, uint32_t n, uint32_t p, uint32_t v, uint64_t nrecchars,
     b.s2lens = ar.take<uint32_t>(b.cap_s2);
     b.s2perm = ar.take<uint32_t>(b.cap_s2);
     b.s2lcp = ar.take<uint32_t>(b.cap_s2);
+    b.s2rank = ar.take<uint32_t>(b.cap_s2);
     b.subspl = ar.take<uint32_t>(b.cap_nsb);
     b.sb = ar.take<uint32_t>(nslices);
     b.ssz = ar.take<uint32_t>(nslices);
@@ -1691,10 +1711,13 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
         SSS_TRY(sss_launch(ctx, "d2_subspl", k_d2_subspl, dim3((NSS + 255) / 256), dim3(256), 0,
                            (const BucketInfo*)b.binfo, p, NSS, (const uint32_t*)b.smp2, (const uint32_t*)b.s2perm,
                            b.subspl));
-        for (uint32_t phase = 0; phase < 2; ++phase)
-            SSS_TRY(sss_launch(ctx, "d2_bounds", k_d2_bounds, dim3((NSS * p * 32 + 127) / 128), dim3(128), 0,
-                               run_perm, S, (const BucketInfo*)b.binfo, p, NSS, (const uint32_t*)b.pstart,
-                               (const uint32_t*)b.psz, (const uint32_t*)b.subspl, b.sb, phase));
+        SSS_TRY(sss_launch(ctx, "d2_srank", k_d2_srank, dim3((S2 + 255) / 256), dim3(256), 0,
+                           (const uint32_t*)b.s2perm, S2, b.s2rank));
+        SSS_TRY(sss_launch(ctx, "d2_bounds", k_d2_bounds, dim3((NSS * p * 32 + 127) / 128), dim3(128), 0, run_perm,
+                           S, (const BucketInfo*)b.binfo, p, NSS, (const uint32_t*)b.pstart, (const uint32_t*)b.psz,
+                           (const uint32_t*)b.pso, (const uint32_t*)b.subspl, (const uint32_t*)b.s2perm,
+                           (const uint32_t*)b.s2rank, (const uint32_t*)b.s2lcp, (const uint32_t*)b.s2lens, step,
+                           b.sb));
     }
     SSS_TRY(sss_launch(ctx, "d2_slices", k_d2_slices, dim3((nslices + 255) / 256), dim3(256), 0,
                        (const BucketInfo*)b.binfo, p, NSB, (const uint32_t*)b.sb, (const uint32_t*)b.psz, b.ssz));
