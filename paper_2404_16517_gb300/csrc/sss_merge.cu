@@ -943,37 +943,77 @@ __global__ void k_d2_cb(Strs S, const BucketInfo* __restrict__ bi, uint32_t p, u
 // Writes rv (r, c or u), rs (side), rk (characters) per record.
 __device__ __forceinline__ uint64_t d2_mask_from(uint32_t off) { return off == 0 ? ~0ull : (~0ull >> (8 * off)); }
 
-__global__ void __launch_bounds__(256) k_d2_decode(Strs S, Recs R, const BucketInfo* __restrict__ bi, uint32_t p,
-                                                   uint32_t nsb, const uint64_t* __restrict__ soff,
-                                                   const uint32_t* __restrict__ subspl, uint32_t* __restrict__ rv,
-                                                   uint8_t* __restrict__ rs, uint64_t* __restrict__ rk,
-                                                   const uint32_t* __restrict__ cb) {
+// The two-sided path builds a slice's records and decodes them in one warp
+// (k_d2_recdec): the slice's positions are walked in run order (coalesced reads
+// of the run, no search for the slice, the predecessor's length by a shuffle),
+// every record is written for the merge and the fallback, and the forward walk
+// of the decode runs on the values still in registers.
+__global__ void __launch_bounds__(256) k_d2_recdec(const uint32_t* __restrict__ run_perm,
+                                                   const uint32_t* __restrict__ run_lcp, Strs S,
+                                                   const BucketInfo* __restrict__ bi, uint32_t p, uint32_t nsb,
+                                                   const uint32_t* __restrict__ pstart,
+                                                   const uint32_t* __restrict__ psz, const uint32_t* __restrict__ sb,
+                                                   const uint64_t* __restrict__ soff,
+                                                   const uint32_t* __restrict__ subspl,
+                                                   const uint32_t* __restrict__ cb, Recs R, uint32_t* clen,
+                                                   uint32_t* rv, uint8_t* rs, uint64_t* rk) {
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // the warp's slice
+    const uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // the warp's slice (b, i)
     if (g >= nsb * p) return;
-    const uint32_t b = g / p;
-    const uint32_t s0 = (uint32_t)soff[g], s1 = (uint32_t)soff[g + 1];
-    if (s0 >= s1) return;
+    const uint32_t b = g / p, i = g % p;
     const uint32_t j = bucket_of_sub(bi, p, b);
-    const uint32_t ref = sub_ref(bi[j], b, subspl), uref = sub_uref(bi[j], b, subspl);
-    const uint32_t ef = R.idx[s0], el = R.idx[s1 - 1];
+    const BucketInfo B = bi[j];
+    uint32_t lo, hi;
+    slice_range(B, b, i, p, sb, psz, j, &lo, &hi);
+    if (lo >= hi) return;
+    const uint32_t len = hi - lo;
+    const uint32_t s0 = (uint32_t)soff[g], s1 = s0 + len;
+    const uint32_t q0 = pstart[j * p + i] + lo;  // run position of the slice's first string
+    const uint32_t ref = sub_ref(B, b, subspl), uref = sub_uref(B, b, subspl);
     const uint32_t c = cb[b];
+    const uint32_t ef = run_perm[q0];
+    const uint32_t tlf = tlen(S, ef);
     uint32_t r0 = 0, ul = 0;
-    if (ref != MINF) warp_cmp_from(S.chars + S.offs[ref], tlen(S, ref), S.chars + S.offs[ef], tlen(S, ef), c, &r0);
-    const uint64_t key0 = load_word_be(S.chars + S.offs[ef], R.tl[s0], r0);
-    // forwards
-    uint32_t carry_r = 0xFFFFFFFFu;
+    if (ref != MINF) warp_cmp_from(S.chars + S.offs[ref], tlen(S, ref), S.chars + S.offs[ef], tlf, c, &r0);
+    const uint64_t key0 = load_word_be(S.chars + S.offs[ef], tlf, r0);
+    // forwards: the records, then r and the characters at r
+    uint32_t carry_r = 0xFFFFFFFFu, carry_tl = 0;
     uint64_t carry_key = 0;
-    for (uint32_t base = s0; base < s1; base += 32) {
-        const uint32_t t = base + lane;
-        const bool valid = t < s1;
-        const uint32_t h = valid ? (t == s0 ? r0 : R.h[t]) : 0xFFFFFFFFu;
-        const uint64_t hw = valid ? (t == s0 ? key0 : R.head[t]) : 0ull;
+    for (uint32_t o0 = 0; o0 < len; o0 += 32) {
+        const uint32_t o = o0 + lane;
+        const bool valid = o < len;
+        const uint32_t t = s0 + o;
+        uint32_t e = 0, tl = 0;
+        if (valid) {
+            e = run_perm[q0 + o];
+            tl = tlen(S, e);
+        }
+        uint32_t prev_tl = __shfl_up_sync(SSS_FULL, tl, 1);
+        if (lane == 0) prev_tl = carry_tl;
+        carry_tl = __shfl_sync(SSS_FULL, tl, 31);
+        uint32_t h = 0xFFFFFFFFu;
+        uint64_t hw = 0ull;
+        if (valid) {
+            uint32_t hr = 0;  // the record's LCP with its predecessor (0 for the slice's first)
+            if (o > 0) {
+                hr = run_lcp[q0 + o];
+                hr = hr < tl ? hr : tl;
+                hr = hr < prev_tl ? hr : prev_tl;
+            }
+            const uint64_t head = load_word_be(S.chars + S.offs[e], tl, hr);
+            R.idx[t] = e;
+            R.h[t] = hr;
+            R.tl[t] = tl;
+            R.head[t] = head;
+            clen[t] = tl - hr;
+            h = o == 0 ? r0 : hr;
+            hw = o == 0 ? key0 : head;
+        }
         uint32_t r = h;
 #pragma unroll
-        for (uint32_t o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(SSS_FULL, r, o);
-            if (lane >= o) r = y < r ? y : r;
+        for (uint32_t sh = 1; sh < 32; sh <<= 1) {
+            const uint32_t y = __shfl_up_sync(SSS_FULL, r, sh);
+            if (lane >= sh) r = y < r ? y : r;
         }
         r = carry_r < r ? carry_r : r;
         uint32_t rp = __shfl_up_sync(SSS_FULL, r, 1);  // r after the previous record
@@ -989,10 +1029,10 @@ __global__ void __launch_bounds__(256) k_d2_decode(Strs S, Recs R, const BucketI
             w = hw >> (8 * (h - r));
         }
 #pragma unroll
-        for (uint32_t o = 1; o < 32; o <<= 1) {
-            const uint32_t lf = __shfl_up_sync(SSS_FULL, (uint32_t)f, o);
-            const uint64_t lm = __shfl_up_sync(SSS_FULL, m, o), lw = __shfl_up_sync(SSS_FULL, w, o);
-            if (lane >= o && !f) {
+        for (uint32_t sh = 1; sh < 32; sh <<= 1) {
+            const uint32_t lf = __shfl_up_sync(SSS_FULL, (uint32_t)f, sh);
+            const uint64_t lm = __shfl_up_sync(SSS_FULL, m, sh), lw = __shfl_up_sync(SSS_FULL, w, sh);
+            if (lane >= sh && !f) {
                 w = (lw & ~m) | (w & m);
                 m |= lm;
                 f = lf != 0;
@@ -1006,6 +1046,8 @@ __global__ void __launch_bounds__(256) k_d2_decode(Strs S, Recs R, const BucketI
         carry_r = __shfl_sync(SSS_FULL, r, 31);
         carry_key = __shfl_sync(SSS_FULL, key, 31);
     }
+    __syncwarp();  // the records and r written above are read back below
+    const uint32_t el = R.idx[s1 - 1];
     // u of the last record: c when its r (the last chunk's lane 31 holds it:
     // lanes past the slice's end leave the minimum alone) is larger, as
     // min(r, u) = c; else compared from c on
@@ -1015,15 +1057,15 @@ __global__ void __launch_bounds__(256) k_d2_decode(Strs S, Recs R, const BucketI
     }
     // backwards
     uint32_t carry_u = ul;
-    const uint32_t nch = (s1 - s0 + 31) / 32;
+    const uint32_t nch = (len + 31) / 32;
     for (uint32_t ci = nch; ci-- > 0;) {
         const uint32_t t = s0 + 32 * ci + lane;
         const bool valid = t < s1;
         uint32_t u = valid && t + 1 < s1 ? R.h[t + 1] : 0xFFFFFFFFu;  // h of the next record
 #pragma unroll
-        for (uint32_t o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_down_sync(SSS_FULL, u, o);
-            if (lane + o < 32) u = y < u ? y : u;
+        for (uint32_t sh = 1; sh < 32; sh <<= 1) {
+            const uint32_t y = __shfl_down_sync(SSS_FULL, u, sh);
+            if (lane + sh < 32) u = y < u ? y : u;
         }
         u = carry_u < u ? carry_u : u;
         carry_u = __shfl_sync(SSS_FULL, u, 0);
@@ -1725,26 +1767,28 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
     SSS_CUDA(cudaMemsetAsync(b.cnt, 0, sizeof(uint32_t), ctx->stream));
     SSS_TRY(sss_launch(ctx, "d2_oversized", k_d2_oversized, dim3((NSB + 255) / 256), dim3(256), 0,
                        (const uint64_t*)b.soff, p, NSB, b.olist, b.cnt));
-    // D1: LCP-compressed records of every sub-bucket slice
-    SSS_TRY(sss_launch(ctx, "d2_records", k_d2_records, dim3((n + 255) / 256), dim3(256), 0, run_perm, run_lcp, n, p,
-                       S, (const uint32_t*)b.bounds, (const BucketInfo*)b.binfo, (const uint32_t*)b.sb,
-                       (const uint64_t*)b.soff, b.R, b.clen, ctx->d_err));
-    // D2: decode, then merge every sub-bucket in one CTA
+    // D1 (LCP-compressed records of every sub-bucket slice) and the decode of D2.
     // Slices of 16 or more records on average: the two-sided decode, a warp per
-    // slice; shorter slices (large p): the one-sided forward walk, a thread per
+    // slice, which also builds the slice's records; shorter slices (large p):
+    // the records by position, then the one-sided forward walk, a thread per
     // slice, with c = 0 for every sub-bucket.
     const bool two_sided = (uint64_t)n >= 16ull * nslices;
     if (!two_sided) {
+        SSS_TRY(sss_launch(ctx, "d2_records", k_d2_records, dim3((n + 255) / 256), dim3(256), 0, run_perm, run_lcp, n,
+                           p, S, (const uint32_t*)b.bounds, (const BucketInfo*)b.binfo, (const uint32_t*)b.sb,
+                           (const uint64_t*)b.soff, b.R, b.clen, ctx->d_err));
         SSS_CUDA(cudaMemsetAsync(b.cb, 0, sizeof(uint32_t) * NSB, ctx->stream));
         SSS_TRY(sss_launch(ctx, "d2_decode", k_d2_decode1, dim3((nslices + 127) / 128), dim3(128), 0, S, b.R,
                            (const BucketInfo*)b.binfo, p, NSB, (const uint64_t*)b.soff, (const uint32_t*)b.subspl,
                            b.rr, b.rs, b.rk));
     } else {
-    SSS_TRY(sss_launch(ctx, "d2_cb", k_d2_cb, dim3((NSB + 255) / 256), dim3(256), 0, S, (const BucketInfo*)b.binfo,
-                       p, NSB, (const uint32_t*)b.subspl, (const uint32_t*)b.s2lcp, b.cb));
-    SSS_TRY(sss_launch(ctx, "d2_decode", k_d2_decode, dim3((nslices * 32 + 255) / 256), dim3(256), 0, S, b.R,
-                       (const BucketInfo*)b.binfo, p, NSB, (const uint64_t*)b.soff, (const uint32_t*)b.subspl, b.rr,
-                       b.rs, b.rk, (const uint32_t*)b.cb));
+        SSS_TRY(sss_launch(ctx, "d2_cb", k_d2_cb, dim3((NSB + 255) / 256), dim3(256), 0, S,
+                           (const BucketInfo*)b.binfo, p, NSB, (const uint32_t*)b.subspl, (const uint32_t*)b.s2lcp,
+                           b.cb));
+        SSS_TRY(sss_launch(ctx, "d2_recdec", k_d2_recdec, dim3((nslices * 32 + 255) / 256), dim3(256), 0, run_perm,
+                           run_lcp, S, (const BucketInfo*)b.binfo, p, NSB, (const uint32_t*)b.pstart,
+                           (const uint32_t*)b.psz, (const uint32_t*)b.sb, (const uint64_t*)b.soff,
+                           (const uint32_t*)b.subspl, (const uint32_t*)b.cb, b.R, b.clen, b.rr, b.rs, b.rk));
     }
     TieLists TL{b.tie_tiny, b.tie_med, b.cnt + 1, n / 2 + 2, n / 65 + 2, finish_cap_tiny()};
     SSS_CUDA(cudaMemsetAsync(b.cnt + 1, 0, sizeof(uint32_t) * 2, ctx->stream));
