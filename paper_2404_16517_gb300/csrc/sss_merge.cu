@@ -747,8 +747,8 @@ __global__ void k_d2_srank(const uint32_t* __restrict__ sperm, uint32_t S2, uint
 // the sub-splitter, which are <= it too), sample a - 1 is <= the sub-splitter
 // and sample a is larger: the count lies in [a*step, (a+1)*step - 1] (or up to
 // the piece's end past its last sample).  A binary search over the samples'
-// ranks finds a, then a binary search of at most 2*step positions, with
-// warp-wide comparisons carrying the LCP with both window ends, the count.
+// ranks finds a; then a window of at most 32 strings is compared a lane per
+// string, a wider one searched.
 __global__ void k_d2_bounds(const uint32_t* __restrict__ run_perm, Strs S, const BucketInfo* __restrict__ bi,
                             uint32_t p, uint32_t nss, const uint32_t* __restrict__ pstart,
                             const uint32_t* __restrict__ psz, const uint32_t* __restrict__ pso,
@@ -777,23 +777,53 @@ __global__ void k_d2_bounds(const uint32_t* __restrict__ run_perm, Strs S, const
         if (srank[g0 + mid] <= rend) ka = mid + 1; else kb = mid;
     }
     const uint32_t n_i = psz[j * p + i];
-    uint32_t a = ka * step, b = ka < c ? (ka + 1) * step - 1 : n_i;
-    uint32_t la = 0, lb = 0;
+    const uint32_t wa = ka * step, wb = ka < c ? (ka + 1) * step - 1 : n_i;
     const uint32_t q0 = pstart[j * p + i];
-    while (a < b) {
-        uint32_t mid = (a + b) >> 1;
-        uint32_t e = run_perm[q0 + mid];
-        uint32_t d = la < lb ? la : lb, l;
-        int cmp = warp_cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, d, &l);
-        if (cmp <= 0) {
-            a = mid + 1;
-            la = l;
-        } else {
-            b = mid;
-            lb = l;
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t cnt = wa;
+    if (wb - wa <= 32) {
+        // a narrow window (large p: few strings between samples), one round: a
+        // lane per string, compared from the LCP that every string between the
+        // window's neighbours shares with the sub-splitter (the shorter of the
+        // neighbours' LCPs with it); the strings <= it form a prefix
+        uint32_t dl = 0, dh = 0;
+        if (wa > 0) {
+            const uint32_t e = run_perm[q0 + wa - 1];
+            warp_cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, 0, &dl);
         }
+        if (wb < n_i) {
+            const uint32_t e = run_perm[q0 + wb];
+            warp_cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, 0, &dh);
+        }
+        const uint32_t d = wa > 0 && wb < n_i ? (dl < dh ? dl : dh) : 0u;
+        const uint32_t q = wa + lane;
+        bool le = false;
+        if (q < wb) {
+            const uint32_t e = run_perm[q0 + q];
+            uint32_t l;
+            le = cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, d, &l) <= 0;
+        }
+        cnt = wa + (uint32_t)__popc(__ballot_sync(SSS_FULL, le));
+    } else {
+        // a wider window: binary search with warp-wide comparisons that carry the
+        // LCP with both ends (fewer strings fetched than a lane per string)
+        uint32_t a = wa, b = wb, la = 0, lb = 0;
+        while (a < b) {
+            const uint32_t mid = (a + b) >> 1;
+            const uint32_t e = run_perm[q0 + mid];
+            uint32_t l;
+            const int cmp = warp_cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, la < lb ? la : lb, &l);
+            if (cmp <= 0) {
+                a = mid + 1;
+                la = l;
+            } else {
+                b = mid;
+                lb = l;
+            }
+        }
+        cnt = a;
     }
-    if ((threadIdx.x & 31) == 0) sb[g] = a;
+    if (lane == 0) sb[g] = cnt;
 }
 
 __device__ __forceinline__ uint32_t bucket_of_sub(const BucketInfo* bi, uint32_t p, uint32_t b) {
