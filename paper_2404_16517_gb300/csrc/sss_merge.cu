@@ -58,6 +58,24 @@ __device__ __forceinline__ int cmp_from(const uint8_t* a, uint32_t la, const uin
     return la < lb ? -1 : (la > lb ? 1 : 0);
 }
 
+// cmp_from over at most 4 words (32 characters) from d: *dec = false when the
+// strings agree on all of them with characters of both left (undecided).
+__device__ __forceinline__ int cmp_from4(const uint8_t* a, uint32_t la, const uint8_t* b, uint32_t lb, uint32_t d,
+                                         bool* dec) {
+    const uint32_t m = la < lb ? la : lb;
+    uint32_t k = d;
+    for (int w = 0; w < 4 && k < m; ++w, k += 8) {
+        const uint64_t x = load_word_be(a, la, k), y = load_word_be(b, lb, k);
+        if (x != y) {
+            *dec = true;
+            if (k + word_lcp(x, y) >= m) return la < lb ? -1 : (la > lb ? 1 : 0);  // one ends first
+            return x < y ? -1 : 1;
+        }
+    }
+    *dec = k >= m;  // both agree up to the shorter's end: decided by the lengths
+    return la < lb ? -1 : (la > lb ? 1 : 0);
+}
+
 // The same comparison by a whole warp: lane k tests the word at d + 256*i + 8k,
 // a ballot finds the first differing word.  Every lane gets the result.
 __device__ __forceinline__ int warp_cmp_from(const uint8_t* a, uint32_t la, const uint8_t* b, uint32_t lb, uint32_t d,
@@ -769,39 +787,56 @@ __global__ void k_d2_bounds(const uint32_t* __restrict__ run_perm, Strs S, const
     uint32_t rend = B.sbase + D2_OVS * (k + 1) - 1;
     const uint32_t rlim = B.sbase + B.nsmp;
     while (rend + 1 < rlim && s2lcp[rend + 1] >= fl && s2lens[sperm[rend + 1]] == fl) ++rend;
-    // a: the piece's samples ranked <= R_end (their ranks grow with their positions)
+    // a: the piece's samples ranked <= R_end (their ranks grow with their
+    // positions): 32 evenly spaced samples per ballot narrow the range until it
+    // fits one ballot
+    const uint32_t lane = threadIdx.x & 31;
     const uint32_t g0 = pso[j * p + i], c = pso[j * p + i + 1] - g0;
-    uint32_t ka = 0, kb = c;
-    while (ka < kb) {
-        const uint32_t mid = (ka + kb) >> 1;
-        if (srank[g0 + mid] <= rend) ka = mid + 1; else kb = mid;
+    uint32_t klo = 0, khi = c;
+    while (khi - klo > 32) {
+        const uint32_t stride = (khi - klo + 31) / 32;
+        const uint32_t t = klo + lane * stride;
+        const uint32_t k = (uint32_t)__popc(__ballot_sync(SSS_FULL, t < khi && srank[g0 + t] <= rend));
+        if (k == 0) {
+            khi = klo;
+        } else {
+            const uint32_t nlo = klo + (k - 1) * stride + 1, nhi = klo + k * stride;
+            klo = nlo;
+            khi = nhi < khi ? nhi : khi;
+        }
     }
+    const uint32_t ka =
+        klo + (uint32_t)__popc(__ballot_sync(SSS_FULL, klo + lane < khi && srank[g0 + klo + lane] <= rend));
     const uint32_t n_i = psz[j * p + i];
     const uint32_t wa = ka * step, wb = ka < c ? (ka + 1) * step - 1 : n_i;
     const uint32_t q0 = pstart[j * p + i];
-    const uint32_t lane = threadIdx.x & 31;
     uint32_t cnt = wa;
     if (wb - wa <= 32) {
-        // a narrow window (large p: few strings between samples), one round: a
-        // lane per string, compared from the LCP that every string between the
-        // window's neighbours shares with the sub-splitter (the shorter of the
-        // neighbours' LCPs with it); the strings <= it form a prefix
-        uint32_t dl = 0, dh = 0;
-        if (wa > 0) {
-            const uint32_t e = run_perm[q0 + wa - 1];
-            warp_cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, 0, &dl);
-        }
-        if (wb < n_i) {
-            const uint32_t e = run_perm[q0 + wb];
-            warp_cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, 0, &dh);
-        }
-        const uint32_t d = wa > 0 && wb < n_i ? (dl < dh ? dl : dh) : 0u;
+        // a narrow window (large p: few strings between samples), a lane per
+        // string; the strings <= the sub-splitter form a prefix.  First their
+        // first 32 characters only: enough when neighbours differ early
         const uint32_t q = wa + lane;
-        bool le = false;
-        if (q < wb) {
-            const uint32_t e = run_perm[q0 + q];
-            uint32_t l;
-            le = cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, d, &l) <= 0;
+        const uint32_t e = q < wb ? run_perm[q0 + q] : 0u;
+        bool le = false, dec = true;
+        if (q < wb) le = cmp_from4(S.chars + S.offs[e], tlen(S, e), fs, fl, 0, &dec) <= 0;
+        if (__ballot_sync(SSS_FULL, !dec) != 0) {
+            // some strings share 32+ characters with the sub-splitter: compare
+            // from the LCP that every string between the window's neighbours
+            // shares with it (the shorter of the neighbours' LCPs with it)
+            uint32_t dl = 0, dh = 0;
+            if (wa > 0) {
+                const uint32_t en = run_perm[q0 + wa - 1];
+                warp_cmp_from(S.chars + S.offs[en], tlen(S, en), fs, fl, 0, &dl);
+            }
+            if (wb < n_i) {
+                const uint32_t en = run_perm[q0 + wb];
+                warp_cmp_from(S.chars + S.offs[en], tlen(S, en), fs, fl, 0, &dh);
+            }
+            const uint32_t d = wa > 0 && wb < n_i ? (dl < dh ? dl : dh) : 0u;
+            if (q < wb) {
+                uint32_t l;
+                le = cmp_from(S.chars + S.offs[e], tlen(S, e), fs, fl, d, &l) <= 0;
+            }
         }
         cnt = wa + (uint32_t)__popc(__ballot_sync(SSS_FULL, le));
     } else {
