@@ -694,6 +694,8 @@ __global__ void k_d_out(const Recs R, const uint32_t* __restrict__ Rfin, const u
 constexpr uint32_t D2_CAP = 2048;  // strings merged by one CTA (<= the stage-A CTA finisher)
 constexpr uint32_t D2_OVS = 16;    // samples per sub-bucket
 constexpr int D2_T = 512;
+constexpr int D2_T_SMALL = 128;    // CTA of the small sub-buckets
+constexpr uint32_t D2_SMALL = 512; // largest small sub-bucket
 constexpr uint32_t D2_MAXP = 256;  // slices a CTA merges as runs (more: a full sort)
 static_assert(D2_MAXP <= 2 * D2_T, "block_merge_runs128 takes at most 2*THREADS runs");
 
@@ -1228,34 +1230,38 @@ __device__ __forceinline__ bool d2_same_key(uint64_t ha, uint64_t la, uint64_t h
     return ha == hb && (la >> 31) == (lb >> 31);
 }
 
-__global__ void __launch_bounds__(D2_T) k_d2_cta(Strs S, Recs R, const uint64_t* __restrict__ soff, uint32_t p,
-                                                 const uint32_t* __restrict__ rv, const uint8_t* __restrict__ rs,
-                                                 const uint64_t* __restrict__ rk, const uint32_t* __restrict__ cb,
-                                                 uint32_t* __restrict__ out_perm, uint32_t* __restrict__ out_lcp,
-                                                 TieLists T, unsigned* err) {
+// THREADS/CAP: the CTA's size and the largest sub-bucket it takes; sub-buckets
+// of at most minsz records are left to a smaller instance.
+template <int THREADS, int CAP>
+__global__ void __launch_bounds__(THREADS) k_d2_cta(Strs S, Recs R, const uint64_t* __restrict__ soff, uint32_t p,
+                                                    const uint32_t* __restrict__ rv, const uint8_t* __restrict__ rs,
+                                                    const uint64_t* __restrict__ rk, const uint32_t* __restrict__ cb,
+                                                    uint32_t* __restrict__ out_perm, uint32_t* __restrict__ out_lcp,
+                                                    TieLists T, unsigned* err, uint32_t minsz) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* sHi = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* sLo = sHi + D2_CAP;
+    uint64_t* sLo = sHi + CAP;
     const uint32_t b = blockIdx.x;
     const uint32_t base = (uint32_t)soff[(uint64_t)b * p];
     const uint32_t m = (uint32_t)soff[(uint64_t)(b + 1) * p] - base;
-    if (m == 0 || m > D2_CAP) return;
+    if (m <= minsz || m > (uint32_t)CAP) return;
     const uint32_t c = cb[b];
     // slice i (one sorted run of the merge) is [rb[i], rb[i+1])
     __shared__ uint32_t s_rb[D2_MAXP + 1];
     const bool runs = p <= D2_MAXP;
     if (runs)
-        for (uint32_t i = threadIdx.x; i <= p; i += D2_T) s_rb[i] = (uint32_t)soff[(uint64_t)b * p + i] - base;
-    for (uint32_t u = threadIdx.x; u < m; u += D2_T) d2_key(rs[base + u], rv[base + u], rk[base + u], u, &sHi[u], &sLo[u]);
+        for (uint32_t i = threadIdx.x; i <= p; i += THREADS) s_rb[i] = (uint32_t)soff[(uint64_t)b * p + i] - base;
+    for (uint32_t u = threadIdx.x; u < m; u += THREADS)
+        d2_key(rs[base + u], rv[base + u], rk[base + u], u, &sHi[u], &sLo[u]);
     __syncthreads();
     // every slice is ascending in these keys (along a sorted slice r never grows
     // and u never falls, so the sides come in order 0, 1, 2; within a side the
     // field does not fall, and at an equal field neither do the characters), so a
     // merge of the p slices sorts the sub-bucket
-    if (!runs) block_merge_sort128_fit<D2_T, D2_CAP / D2_T>(sHi, sLo, m);
-    else if (m <= D2_CAP / 2) block_merge_runs128<D2_T, D2_CAP / D2_T / 2>(sHi, sLo, m, s_rb, p);
-    else block_merge_runs128<D2_T, D2_CAP / D2_T>(sHi, sLo, m, s_rb, p);
-    for (uint32_t t = threadIdx.x; t < m; t += D2_T) {
+    if (!runs) block_merge_sort128_fit<THREADS, CAP / THREADS>(sHi, sLo, m);
+    else if (m <= (uint32_t)CAP / 2) block_merge_runs128<THREADS, CAP / THREADS / 2>(sHi, sLo, m, s_rb, p);
+    else block_merge_runs128<THREADS, CAP / THREADS>(sHi, sLo, m, s_rb, p);
+    for (uint32_t t = threadIdx.x; t < m; t += THREADS) {
         const uint32_t u = (uint32_t)(sLo[t] & 0x7FFFFFFFu);
         out_perm[base + t] = R.idx[base + u];
         const uint64_t hb = sHi[t], lb = sLo[t];
@@ -1694,7 +1700,7 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
         return SSS_OK;
     }
     if (!g_mg_attr[ctx->device & 63]) {
-        SSS_CUDA(cudaFuncSetAttribute(k_d2_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SSS_CUDA(cudaFuncSetAttribute(k_d2_cta<D2_T, D2_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(D2_CAP * (8 + 8))));
         g_mg_attr[ctx->device & 63] = true;
     }
@@ -1857,9 +1863,18 @@ sss_status impl_merge(sss_ctx* ctx, char* ws, size_t ws_bytes, const StrIn& in, 
     }
     TieLists TL{b.tie_tiny, b.tie_med, b.cnt + 1, n / 2 + 2, n / 65 + 2, finish_cap_tiny()};
     SSS_CUDA(cudaMemsetAsync(b.cnt + 1, 0, sizeof(uint32_t) * 2, ctx->stream));
-    SSS_TRY(sss_launch(ctx, "d2_cta", k_d2_cta, dim3(NSB), dim3(D2_T), (size_t)D2_CAP * (8 + 8), S, b.R,
-                       (const uint64_t*)b.soff, p, (const uint32_t*)b.rr, (const uint8_t*)b.rs,
-                       (const uint64_t*)b.rk, (const uint32_t*)b.cb, out_perm, out_lcp, TL, ctx->d_err));
+    // when sub-buckets are small (large p: their mean is D2_OVS * step), those of
+    // at most D2_SMALL records go to 128-thread CTAs, the others to 512-thread CTAs
+    const bool small = D2_OVS * step <= D2_SMALL;
+    if (small)
+        SSS_TRY(sss_launch(ctx, "d2_cta", k_d2_cta<D2_T_SMALL, D2_SMALL>, dim3(NSB), dim3(D2_T_SMALL),
+                           (size_t)D2_SMALL * (8 + 8), S, b.R, (const uint64_t*)b.soff, p, (const uint32_t*)b.rr,
+                           (const uint8_t*)b.rs, (const uint64_t*)b.rk, (const uint32_t*)b.cb, out_perm, out_lcp, TL,
+                           ctx->d_err, 0u));
+    SSS_TRY(sss_launch(ctx, "d2_cta", k_d2_cta<D2_T, D2_CAP>, dim3(NSB), dim3(D2_T), (size_t)D2_CAP * (8 + 8), S,
+                       b.R, (const uint64_t*)b.soff, p, (const uint32_t*)b.rr, (const uint8_t*)b.rs,
+                       (const uint64_t*)b.rk, (const uint32_t*)b.cb, out_perm, out_lcp, TL, ctx->d_err,
+                       small ? D2_SMALL : 0u));
     // oversized sub-buckets (many equal strings): pairwise merge tree over their slices.
     // (the sample sort above may have grown the pinned staging: re-derive pointers)
     {
