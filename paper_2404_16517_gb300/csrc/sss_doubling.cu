@@ -331,14 +331,65 @@ __device__ __forceinline__ uint64_t pd_rep_key(const PdIn& in, uint32_t q, const
     return smix64(h ^ ((uint64_t)le * GAMMA));
 }
 
+// (a - b) mod P for a, b < P
+__device__ __forceinline__ uint64_t submod61(uint64_t a, uint64_t b) { return a >= b ? a - b : a + P61 - b; }
+
+// The hash of a new rep q from its group start's finished hash (same tested
+// length le): the two prefixes agree on their first wsh whole words, so their
+// Horner values differ by the Horner fold of the limb differences over words
+// wsh .. nw-1 alone (the polynomial is linear in the limbs, and every limb
+// keeps its power of B).
+__device__ __forceinline__ uint64_t pd_key_from_start(const uint8_t* str, const uint8_t* sstr, uint32_t le,
+                                                      uint32_t wsh, uint64_t hsrc, uint64_t B, uint64_t B2) {
+    const uint32_t nw = (le + 7) / 8;
+    uint64_t D = 0;
+    for (uint32_t w = wsh; w < nw; ++w) {
+        const uint64_t x = load_word_be(str, le, 8 * w), y = load_word_be(sstr, le, 8 * w);
+        const uint64_t dh = submod61(x >> 32, y >> 32), dl = submod61(x & 0xFFFFFFFFull, y & 0xFFFFFFFFull);
+        uint64_t t = mulmod61(D, B2) + mulmod61(dh, B);
+        t = t >= P61 ? t - P61 : t;
+        t += dl;
+        D = t >= P61 ? t - P61 : t;
+    }
+    const uint64_t h = hsrc + D;
+    return h >= P61 ? h - P61 : h;
+}
+
+// Phase 0: every rep.  When new reps resume from their group starts (prevstart
+// given), phase 1 hashes the reps that resume their own L/2 state (the group
+// starts that are still reps) and phase 2 the others; a rep of phase 2 whose
+// group start has just been hashed to the same length finishes from that hash
+// (pd_key_from_start) instead of folding the words they share.
 __global__ void k_pd_hash(PdIn in, const uint32_t* __restrict__ reps, uint32_t nreps, const uint32_t* __restrict__ lpos,
                           const uint64_t* __restrict__ hst_in, const uint32_t* __restrict__ hlen_in,
-                          uint64_t* __restrict__ hst_out, uint32_t* __restrict__ hlen_out,
-                          const uint32_t* __restrict__ prevstart, const uint32_t* __restrict__ minlcp,
-                          uint64_t* __restrict__ K, uint32_t* __restrict__ V, uint64_t L, uint64_t B) {
+                          uint64_t* hst_out, uint32_t* hlen_out, const uint32_t* __restrict__ prevstart,
+                          const uint32_t* __restrict__ minlcp, uint64_t* __restrict__ K, uint32_t* __restrict__ V,
+                          uint64_t L, uint64_t B, int phase) {
     uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nreps) return;
     uint32_t q = reps[j];
+    if (phase != 0) {
+        const bool own = L >= 16 && hlen_in[q] == (uint32_t)(L / 2);
+        if ((phase == 1) != own) return;
+        if (phase == 2 && prevstart && minlcp) {
+            const uint32_t src = prevstart[q];
+            const uint32_t len = lpos[q];
+            const uint32_t le = L < len ? (uint32_t)L : len;
+            if (src != q && hlen_out[src] == le) {
+                const uint32_t ml = minlcp[q];
+                const uint32_t wsh = (ml < le ? ml : le) / 8;
+                const uint64_t B2 = mulmod61(B, B);
+                const uint64_t h = pd_key_from_start(in.chars + in.offs[ord_of(in, q)],
+                                                     in.chars + in.offs[ord_of(in, src)], le, wsh, hst_out[src], B,
+                                                     B2);
+                hst_out[q] = h;
+                hlen_out[q] = le;
+                K[j] = smix64(h ^ ((uint64_t)le * GAMMA));
+                V[j] = q;
+                return;
+            }
+        }
+    }
     K[j] = pd_rep_key(in, q, lpos, hst_in, hlen_in, hst_out, hlen_out, prevstart, minlcp, L, B);
     V[j] = q;
 }
@@ -1046,10 +1097,13 @@ sss_status impl_dist_prefix(sss_ctx* ctx, Arena& ar, const StrIn& sin, const uin
             uint32_t* hl_in = odd ? B.hlen2 : B.hlen;
             uint64_t* hs_out = odd ? B.hst : B.hst2;
             uint32_t* hl_out = odd ? B.hlen : B.hlen2;
-            SSS_TRY(sss_launch(ctx, "pd_hash", k_pd_hash, dim3((nreps + 255) / 256), dim3(256), 0, in, reps, nreps,
-                               (const uint32_t*)B.lpos, (const uint64_t*)hs_in, (const uint32_t*)hl_in, hs_out,
-                               hl_out, ps, ps ? (const uint32_t*)B.minlcp : (const uint32_t*)nullptr, B.K, B.V, L,
-                               Bh));
+            // with previous starts: the surviving group starts first, then the new
+            // reps, which can finish from their start's hash
+            for (int phase = ps ? 1 : 0; phase <= (ps ? 2 : 0); ++phase)
+                SSS_TRY(sss_launch(ctx, "pd_hash", k_pd_hash, dim3((nreps + 255) / 256), dim3(256), 0, in, reps,
+                                   nreps, (const uint32_t*)B.lpos, (const uint64_t*)hs_in, (const uint32_t*)hl_in,
+                                   hs_out, hl_out, ps, ps ? (const uint32_t*)B.minlcp : (const uint32_t*)nullptr,
+                                   B.K, B.V, L, Bh, phase));
             if (use_ht) {
                 uint32_t T = 1024;
                 while (T < 2ull * nreps) T <<= 1;
