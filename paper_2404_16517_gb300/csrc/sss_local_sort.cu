@@ -182,6 +182,8 @@ __device__ __forceinline__ void finish_segment(const Seg sg, const uint8_t* __re
     uint32_t* sA = sGF + CAP;                            // scan buffer
     uint32_t* sC = sA + CAP;                             // compacted active positions
     __shared__ uint32_t sh_warp[32];
+    constexpr uint32_t FIN_NREF = 68;  // 64 reference words plus a 4-word block of slack
+    __shared__ uint64_t refw[FIN_NREF];
 
     const uint32_t m = sg.size;
     const int tid = threadIdx.x;
@@ -240,6 +242,14 @@ __device__ __forceinline__ void finish_segment(const Seg sg, const uint8_t* __re
             sA[pos] = best;
         }
         __syncthreads();
+        // the first iteration has one group, the whole segment: its reference's
+        // first 512 characters from the depth on go to shared memory, so that
+        // every member reads only its own string (with 16-byte loads)
+        if (iter == 0) {
+            const uint32_t r0 = sV[sA[0]], rl0 = lens[r0];
+            for (uint32_t i = tid; i < FIN_NREF; i += THREADS) refw[i] = load_word_be(chars + offs[r0], rl0, sGD[0] + 8 * i);
+            __syncthreads();
+        }
 
         // 2b. reference-split key of every member against its group's
         //     reference; pack (group, key, index)
@@ -260,9 +270,15 @@ __device__ __forceinline__ void finish_segment(const Seg sg, const uint8_t* __re
                 v = v < VCAP ? v : VCAP;
                 w = load_word_be(rs, rl, d + v);
             } else {
-                v = lcp_full_w(chars + offs[e], lens[e], rs, rl, d, &w);
+                const uint32_t le = lens[e];
+                const uint32_t mlen = le < rl ? le : rl;
+                v = (iter == 0 && mlen <= d + 8 * (FIN_NREF - 4)) ? lcp_full_w_ref(chars + offs[e], le, rl, refw, d, &w)
+                                                                  : lcp_full_w(chars + offs[e], le, rs, rl, d, &w);
             }
-            uint64_t k = ref_key(v, w, (uint32_t)(load_word_be(rs, rl, d + v) >> 56), f);
+            const uint32_t rho = (iter == 0 && (v >> 3) < FIN_NREF)
+                                     ? (uint32_t)(refw[v >> 3] >> (56 - 8 * (v & 7))) & 0xFFu
+                                     : (uint32_t)(load_word_be(rs, rl, d + v) >> 56);
+            uint64_t k = ref_key(v, w, rho, f);
             sHi[j] = ((uint64_t)g << 48) | (k >> 16);
             sLo[j] = (k << 48) | (uint64_t)e;
         }
