@@ -318,6 +318,12 @@ __global__ void __launch_bounds__(512) k_lg_offsets(const LsPlan* __restrict__ p
     }
 }
 
+// The scatter of a tile goes through shared memory: its keys are first placed
+// in bucket order (the tile's bucket counts, scanned, plus each key's rank within
+// its bucket), so that consecutive threads then write consecutive positions of
+// one bucket's range.  Written directly, the keys of a warp land in as many
+// buckets as they have, and every 8-byte key or 4-byte index costs a whole
+// sector of DRAM writes.
 __global__ void __launch_bounds__(LG_T) k_lg_scatter(const LsPlan* __restrict__ plan,
                                                      const LgTile* __restrict__ tiles, const LgSegInfo* __restrict__ info,
                                                      const uint32_t* __restrict__ hist, const uint32_t* __restrict__ bst,
@@ -325,20 +331,58 @@ __global__ void __launch_bounds__(LG_T) k_lg_scatter(const LsPlan* __restrict__ 
                                                      const uint64_t* __restrict__ K, const uint32_t* __restrict__ perm,
                                                      uint64_t* __restrict__ tK, uint32_t* __restrict__ tV,
                                                      unsigned* err) {
+    constexpr int PER = LG_TILE / LG_T;
+    static_assert(2 * LG_T >= LG_NBMAX, "two buckets per thread in the scan");
+    __shared__ uint32_t cnt[2 * LG_T];
+    __shared__ uint32_t sh_warp[32];
+    __shared__ uint64_t sK[LG_TILE];
+    __shared__ uint32_t sV[LG_TILE], sD[LG_TILE];
+    const uint32_t tid = threadIdx.x;
     const uint32_t ptiles = plan->ptiles;
     for (uint32_t g = blockIdx.x; g < ptiles; g += gridDim.x) {
-        LgTile tl = tiles[g];
-        LgSegInfo si = info[tl.s];
-        for (uint32_t q = tl.begin + threadIdx.x; q < tl.end; q += LG_T) {
-            uint32_t ri = rankinfo[q];
-            uint32_t b = ri >> 16;
-            uint32_t dst = bst[si.bst_base + b] + hist[si.hist_base + b * si.tiles + tl.t] + (ri & 0xFFFFu);
-            if (dst < si.seg.start || dst >= si.seg.start + si.seg.size) {
+        const LgTile tl = tiles[g];
+        const LgSegInfo si = info[tl.s];
+        const uint32_t nbk = 2 * si.nb - 1;
+        __syncthreads();  // the previous tile's keys have left shared memory
+        for (uint32_t i = tid; i < 2u * LG_T; i += LG_T) cnt[i] = 0;
+        __syncthreads();
+        uint32_t ri[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const uint32_t q = tl.begin + tid + u * LG_T;
+            ri[u] = q < tl.end ? rankinfo[q] : 0xFFFFFFFFu;
+            if (q < tl.end) atomicAdd(&cnt[min(ri[u] >> 16, 2u * LG_T - 1u)], 1u);  // b < nbk <= 511
+        }
+        __syncthreads();
+        // the tile's bucket offsets: exclusive scan of the counts
+        const uint32_t c0 = cnt[2 * tid], c1 = cnt[2 * tid + 1];
+        const uint32_t ex = BlockScan<LG_T>::exclusive_sum(c0 + c1, sh_warp, nullptr);
+        cnt[2 * tid] = ex;
+        cnt[2 * tid + 1] = ex + c0;
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const uint32_t q = tl.begin + tid + u * LG_T;
+            if (q >= tl.end) continue;
+            const uint32_t b = ri[u] >> 16, r = ri[u] & 0xFFFFu;
+            const uint32_t slot = cnt[min(b, 2u * LG_T - 1u)] + r;
+            uint32_t dst = bst[si.bst_base + b] + hist[si.hist_base + b * si.tiles + tl.t] + r;
+            if (b >= nbk || dst < si.seg.start || dst >= si.seg.start + si.seg.size || slot >= LG_TILE) {
                 atomicOr(err, ERRBIT_OVERFLOW);
-                continue;
+                if (slot >= LG_TILE) continue;
+                dst = 0xFFFFFFFFu;
             }
-            tK[dst] = K[q];
-            tV[dst] = perm[q];
+            sK[slot] = K[q];
+            sV[slot] = perm[q];
+            sD[slot] = dst;
+        }
+        __syncthreads();
+        const uint32_t m = tl.end - tl.begin;
+        for (uint32_t i = tid; i < m; i += LG_T) {
+            const uint32_t dst = sD[i];
+            if (dst == 0xFFFFFFFFu) continue;
+            tK[dst] = sK[i];
+            tV[dst] = sV[i];
         }
     }
 }
