@@ -11,19 +11,32 @@ __device__ __forceinline__ uint64_t bswap64(uint64_t x) {
     return ((uint64_t)__byte_perm(lo, 0, 0x0123) << 32) | (uint64_t)__byte_perm(hi, 0, 0x0123);
 }
 
+// Character loads.  STREAM = true marks a word read once from a scattered
+// string (one word per string in a pass over many strings): the load allocates
+// its lines with evict-first priority in L1 and L2 (ld.global.cs), so they give
+// way before the lines other strings' gathers still need.  Not for a window a
+// thread streams through: there the next loads use the rest of the same lines.
+template <bool STREAM>
+__device__ __forceinline__ uint64_t ld_chars8(const uint64_t* p) {
+    const unsigned long long* q = reinterpret_cast<const unsigned long long*>(p);
+    if constexpr (STREAM) return (uint64_t)__ldcs(q);
+    else return (uint64_t)__ldg(q);
+}
+
 // The 8 characters s[d .. d+8) as a big-endian word, bytes at or past `len` zero
 // (the implicit sentinel sorts below every character, so word order == string
 // order on these 8 characters).  Reads only 8-byte-aligned words that contain at
 // least one character of the string, so it never touches a page the string does
 // not touch.
+template <bool STREAM = false>
 __device__ __forceinline__ uint64_t load_word_be(const uint8_t* __restrict__ s, uint32_t len, uint32_t d) {
     if (d >= len) return 0;
     uintptr_t ai = (uintptr_t)(s + d);
     const uint64_t* base = reinterpret_cast<const uint64_t*>(ai & ~uintptr_t(7));
     uint32_t sh = (uint32_t)(ai & 7);
     uint32_t rem = len - d;
-    uint64_t x = bswap64(__ldg(base)) << (8 * sh);
-    if (sh != 0 && rem > 8 - sh) x |= bswap64(__ldg(base + 1)) >> (64 - 8 * sh);
+    uint64_t x = bswap64(ld_chars8<STREAM>(base)) << (8 * sh);
+    if (sh != 0 && rem > 8 - sh) x |= bswap64(ld_chars8<STREAM>(base + 1)) >> (64 - 8 * sh);
     if (rem < 8) x &= ~0ull << (8 * (8 - rem));
     return x;
 }

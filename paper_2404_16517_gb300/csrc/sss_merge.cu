@@ -942,7 +942,7 @@ __global__ void k_d2_records(const uint32_t* __restrict__ run_perm, const uint32
     R.idx[r] = s;
     R.h[r] = h;
     R.tl[r] = tl;
-    R.head[r] = load_word_be(S.chars + S.offs[s], tl, h);
+    R.head[r] = load_word_be<true>(S.chars + S.offs[s], tl, h);
     clen[r] = tl - h;
 }
 
@@ -1067,7 +1067,7 @@ __global__ void __launch_bounds__(256) k_d2_recdec(const uint32_t* __restrict__ 
                 hr = hr < tl ? hr : tl;
                 hr = hr < prev_tl ? hr : prev_tl;
             }
-            const uint64_t head = load_word_be(S.chars + S.offs[e], tl, hr);
+            const uint64_t head = load_word_be<true>(S.chars + S.offs[e], tl, hr);
             R.idx[t] = e;
             R.h[t] = hr;
             R.tl[t] = tl;
