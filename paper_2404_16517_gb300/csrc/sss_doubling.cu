@@ -173,15 +173,30 @@ __global__ void k_pd_init(PdIn in, const uint32_t* __restrict__ lens, uint32_t* 
     __shared__ uint32_t hs[KBINS], hl[KBINS];
     for (int i = threadIdx.x; i < KBINS; i += blockDim.x) hs[i] = hl[i] = 0;
     __syncthreads();
-    uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < in.n) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = q < in.n;
+    uint32_t ks = 0, kl = 0;
+    if (live) {
         uint32_t len = lens[ord_of(in, q)];
         apos[q] = ACTIVE;
         lpos[q] = len;
         hlen[q] = 0;
-        uint32_t ks = kstar_of(in, q, kmin), kl = klen_of(len, kmin);
-        atomicAdd(&hs[ks], 1u);
-        if (kl < ks) atomicAdd(&hl[kl], 1u);
+        ks = kstar_of(in, q, kmin);
+        kl = klen_of(len, kmin);
+    }
+    // neighbouring positions mostly share their bins: one shared atomic per
+    // (warp, bin), adding the number of lanes with that bin
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned ms = __ballot_sync(SSS_FULL, live);
+    if (live) {
+        const unsigned peers = __match_any_sync(ms, ks);
+        if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hs[ks], (uint32_t)__popc(peers));
+    }
+    const bool below = live && kl < ks;
+    const unsigned ml = __ballot_sync(SSS_FULL, below);
+    if (below) {
+        const unsigned peers = __match_any_sync(ml, kl);
+        if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hl[kl], (uint32_t)__popc(peers));
     }
     __syncthreads();
     for (int i = threadIdx.x; i < KBINS; i += blockDim.x) {

@@ -675,11 +675,11 @@ __device__ void sort_emit(unsigned char* smem, uint32_t bs, uint32_t m, uint32_t
         sA[i] = v;
     }
     __syncthreads();
-    block_inclusive_max_inplace<THREADS, ITEMS>(sA, m, sh_warp);
+    block_inclusive_max_inplace<THREADS, ITEMS>(sA, m, sh_warp);  // sA[i] = first index of i's group
+    // group sizes at the group's first index, written by the group's last member
+    // (no atomics: a group of equal keys may hold the whole segment)
     for (uint32_t i = threadIdx.x; i < m; i += THREADS)
-        if (sA[i] == i) sN[i] = 0;
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < m; i += THREADS) atomicAdd(&sN[sA[i]], 1u);
+        if (i + 1 == m || sA[i + 1] == i + 1) sN[sA[i]] = i + 1 - sA[i];
     __syncthreads();
     for (uint32_t i0 = 0; i0 < m; i0 += THREADS) {  // uniform trip count: push_seg_warp needs whole warps
         const uint32_t i = i0 + threadIdx.x;
