@@ -516,6 +516,15 @@ __device__ __forceinline__ uint32_t swz(uint32_t j) {
     return j ^ (((j / ITEMS) / PER_ROW) & (ITEMS - 1));
 }
 
+// The merge rounds' barrier: while a pair of runs spans at most 32 threads
+// (2w <= 32, runs of w threads' outputs), the pair's slots are written and read
+// by that warp alone (the swizzle permutes within blocks of ITEMS slots, and a
+// thread writes only its own block), so the warp's barrier suffices.
+__device__ __forceinline__ void merge_round_sync(uint32_t w) {
+    if (2 * w <= 32) __syncwarp();
+    else __syncthreads();
+}
+
 // Block merge sort of `count` 128-bit keys (hi, lo) held in shared memory arrays
 // of THREADS*ITEMS entries, ascending; input and output in plain index order.
 // Each thread sorts ITEMS keys in registers (odd-even transposition), then
@@ -526,6 +535,7 @@ __device__ __forceinline__ uint32_t swz(uint32_t j) {
 // padded with all-ones keys (the arrays are fully overwritten).
 template <int THREADS, int ITEMS>
 __device__ void block_merge_sort128(uint64_t* sHi, uint64_t* sLo, uint32_t count) {
+    static_assert(THREADS % 32 == 0, "whole warps: the in-warp merge rounds use the warp barrier");
     const uint32_t tid = threadIdx.x;
     uint64_t h[ITEMS], l[ITEMS];
     // plain -> swizzled, padding the tail
@@ -564,14 +574,14 @@ __device__ void block_merge_sort128(uint64_t* sHi, uint64_t* sLo, uint32_t count
     }
     const uint32_t used = (count + ITEMS - 1) / ITEMS;  // threads holding real keys
     for (uint32_t w = 1; w < used; w <<= 1) {
-        __syncthreads();
+        merge_round_sync(w);
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             uint32_t j = swz<ITEMS>(tid * ITEMS + i);
             sHi[j] = h[i];
             sLo[j] = l[i];
         }
-        __syncthreads();
+        merge_round_sync(w);
         const uint32_t L = w * ITEMS;
         const uint32_t g0 = (tid / (2 * w)) * (2 * L);
         if (g0 >= count) continue;  // a pair of padding lists stays as it is
@@ -656,6 +666,7 @@ __device__ void block_merge_sort128(uint64_t* sHi, uint64_t* sLo, uint32_t count
 // index order; slots past `count` are overwritten with padding.
 template <int THREADS, int ITEMS>
 __device__ void block_merge_sort_kv(uint64_t* sK, uint32_t* sV, uint32_t count) {
+    static_assert(THREADS % 32 == 0, "whole warps: the in-warp merge rounds use the warp barrier");
     const uint32_t tid = threadIdx.x;
     uint64_t k[ITEMS];
     uint32_t v[ITEMS];
@@ -697,14 +708,14 @@ __device__ void block_merge_sort_kv(uint64_t* sK, uint32_t* sV, uint32_t count) 
     }
     const uint32_t used = (count + ITEMS - 1) / ITEMS;  // threads holding real pairs
     for (uint32_t w = 1; w < used; w <<= 1) {
-        __syncthreads();
+        merge_round_sync(w);
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             uint32_t j = swz<ITEMS>(tid * ITEMS + i);
             sK[j] = k[i];
             sV[j] = v[i];
         }
-        __syncthreads();
+        merge_round_sync(w);
         const uint32_t L = w * ITEMS;
         const uint32_t g0 = (tid / (2 * w)) * (2 * L);
         if (g0 >= count) continue;
