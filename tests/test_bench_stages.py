@@ -1,4 +1,6 @@
-"""Stage-level algorithmic-byte efficiency in the benchmark line (host logic)."""
+"""Stage-level algorithmic-byte efficiency in the benchmark line, and the DRAM
+traffic it reports only for the library source the capture was taken on (host
+logic)."""
 import importlib.util
 import os
 
@@ -32,3 +34,22 @@ def test_stage_rooflines_groups_kernels_and_applies_the_byte_model():
     # A: 432,000 bytes in 1 ms = 0.432 GB/s against a 1000 GB/s peak
     assert st["A"]["achieved_gbs"] == pytest.approx(0.432)
     assert st["A"]["frac"] == pytest.approx(0.432 / 1000.0)
+
+
+def test_known_traffic_only_for_the_source_it_was_taken_on(tmp_path, monkeypatch):
+    b = bench()
+    csrc = tmp_path / "paper_2404_16517_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k.cu").write_text("__global__ void k() {}\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    h = b.lib_source_hash()
+    t = tmp_path / "profiles" / "traffic.json"
+    t.write_text('{"source_hash": "%s", "kernels": {"ls_lg_ext": 1234}}' % h)
+    assert b.known_traffic("ls_lg_ext") == 1234
+    assert b.known_traffic("pd_hash") is None  # not captured
+    (csrc / "k.cu").write_text("__global__ void k() { }\n")  # the source changed since the capture
+    assert b.lib_source_hash() != h
+    assert b.known_traffic("ls_lg_ext") is None
+    t.write_text("not json")
+    assert b.known_traffic("ls_lg_ext") is None
