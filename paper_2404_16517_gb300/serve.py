@@ -153,9 +153,10 @@ class Scheduler:
     """Admission and batch formation (host logic only).
 
     batch_temp(n, m) gives the arena bytes of the transient work memory of a
-    batch of m requests holding n strings in all.  The scheduler forms batches as FIFO prefixes of the queue that fit both the
-    batch limits and the arena, and frees memory when batches end and requests
-    are released."""
+    batch of m requests holding n strings in all.  The scheduler forms batches
+    as FIFO prefixes of the queue that fit both the batch limits and the arena,
+    and frees memory when batches end and requests are released.  The string
+    limit bounds joining: a request larger than it runs in a batch of its own."""
 
     def __init__(self, arena_bytes: int, batch_temp, max_batch_requests: int = 256,
                  max_batch_strings: int = 1 << 24):

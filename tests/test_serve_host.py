@@ -175,3 +175,27 @@ def test_open_loop_latency_accounting():
         assert r.t_done >= r.t_admit >= r.t_arrival
     s = summarize(reqs, t0)
     assert s["done"] == 40 and s["chars"] == sum(r.chars for r in reqs)
+
+
+def test_batches_respect_the_string_limit():
+    # requests join a batch only while the batch's string count stays within the
+    # limit; a request larger than the limit still runs, in a batch of its own
+    eng = FakeEngine()
+    srv = Server(budget_bytes=256 << 20, slots=1, engine=eng, max_batch_requests=64, max_batch_strings=1000)
+    blocker = Request(rid=0, n=50000, chars=1 << 20)  # holds the slot while the rest queue up
+    srv.submit(blocker)
+    time.sleep(0.005)
+    sizes = [400, 400, 400, 1500, 300, 300, 300, 300]
+    reqs = [Request(rid=k + 1, n=n, chars=10 * n) for k, n in enumerate(sizes)]
+    for r in reqs:
+        srv.submit(r)
+    for r in [blocker] + reqs:
+        assert r.wait(10)
+    srv.close()
+    by_rid = {r.rid: r.n for r in [blocker] + reqs}
+    batches = eng.batches[1:]
+    assert [rid for b in batches for rid in b] == list(range(1, len(sizes) + 1))  # FIFO
+    for b in batches:
+        total = sum(by_rid[rid] for rid in b)
+        assert total <= 1000 or len(b) == 1, (b, total)
+    assert [4] in batches  # the 1500-string request alone
